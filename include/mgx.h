@@ -1,0 +1,155 @@
+/*
+ * mgx — batched tree-level squared matrix elements on one GB300 (sm_103a).
+ *
+ * C ABI of the event-parallel matrix-element library.  The operation is the
+ * third step of the matrix-element generator chain of arXiv:2503.21935, Sec. 2
+ * (random numbers -> phase-space momenta -> matrix element), exposed through
+ * the multi-event interface the paper describes in Sec. 2: reentrant, stateless
+ * compute calls with well-defined input and output buffers for a whole batch
+ * of events.  For each event the library returns the spin- and colour-averaged
+ * |M|^2 summed over the non-vanishing helicities (Feynman diagrams in double
+ * precision, followed by the colour-matrix quadratic form J^dagger C J, Sec. 3),
+ * plus one helicity and one colour flow selected from per-event random numbers.
+ *
+ * Conventions
+ *   - Momenta: float64, layout [nevt][npar][4] = (E, px, py, pz) in GeV, the
+ *     particles in process-string order (two incoming partons first).
+ *   - Helicity index h in [0, 2^npar): bit (npar-1-p) of h is 1 when particle p
+ *     has helicity +1 and 0 for -1 (particle 0 varies slowest).
+ *   - Colour flows: the strings (T^{a_s1} ... T^{a_sn})_{ij} over the permutations
+ *     s of the gluon legs in lexicographic order, i the colour of the fermion line's
+ *     barred end (an outgoing quark or incoming antiquark), j of its other end.
+ *   - me = 1/(4 * Ncol_in * S) * sum_h sum_colours |M|^2, with S the product of
+ *     n! over identical final-state particles.
+ *   - selected helicity: smallest canonical h whose cumulative |M_h|^2 (canonical
+ *     order) exceeds rnd_hel * total; selected colour: smallest flow s whose
+ *     cumulative w_s exceeds rnd_col * sum(w), w_s = sum_h |J_s(h)|^2.
+ *
+ * Ownership: the caller owns every buffer passed to mgx_compute (device
+ * pointers) and the workspace; the library owns only the process handle.
+ * Errors: every call returns MGX_OK (0) or a negative mgx_status; nothing
+ * throws across the ABI.  mgx_compute is asynchronous on the given stream and
+ * performs no allocation and no host synchronisation.
+ */
+#ifndef MGX_H
+#define MGX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mgx_process mgx_process; /* opaque, library-owned */
+
+enum mgx_status {
+  MGX_OK = 0,
+  MGX_ERR_INVALID_ARGUMENT = -1,
+  MGX_ERR_UNKNOWN_PROCESS = -2,
+  MGX_ERR_CUDA = -3,
+  MGX_ERR_DEVICE_MISMATCH = -4,
+  MGX_ERR_WORKSPACE_TOO_SMALL = -5,
+  MGX_ERR_NO_GOOD_HELICITY = -6,
+  MGX_ERR_UNSUPPORTED_MODE = -7
+};
+
+/* Precision of the colour sum (Sec. 3: "mixed" computes the diagrams in double
+ * precision and the colour-matrix quadratic form in single precision).  The
+ * amplitudes are float64 in every mode; the helicity sum is float64. */
+enum mgx_mode {
+  MGX_FP64 = 0,       /* float64 colour sum */
+  MGX_MIXED_FP32 = 1  /* jamps rounded to float32, float32 quadratic form */
+};
+
+/* Standard-Model inputs.  Electroweak scheme {alpha_em(mZ), G_F, mZ}. */
+typedef struct mgx_params {
+  double mt, wt;       /* top mass and width [GeV] */
+  double mz, wz;       /* Z mass and width [GeV] */
+  double mta;          /* tau mass [GeV] */
+  double alpha_em;     /* 1/132.507 */
+  double gf;           /* Fermi constant [GeV^-2] */
+  double filter_sqrt_s;/* partonic energy of the helicity-filter events [GeV]; <= 0: 1000 */
+} mgx_params;
+
+/* Fill *p with the default parameters (mt 173, wt 1.4915, mz 91.1876,
+ * wz 2.4414, mta 1.777, alpha 1/132.507, G_F 1.16639e-5). */
+void mgx_params_default(mgx_params* p);
+
+/* Number of built-in processes and the process string of entry i (NULL if out
+ * of range).  Strings use the names e+ e- mu+ mu- ta+ ta- u u~ t t~ g. */
+int mgx_num_processes(void);
+const char* mgx_process_name(int i);
+
+/* Create a process on CUDA device `device`: resolves the couplings and masses,
+ * uploads the process's op table and colour matrix, and runs the helicity
+ * filter: all 2^npar helicities are evaluated on 16 flat phase-space events
+ * (Philox-4x32-10 keyed by filter_seed, RAMBO at params->filter_sqrt_s) and
+ * those with |M_h|^2 == 0 on every event are dropped.  Synchronous.
+ * process: e.g. "g g > t t~ g g" (whitespace-insensitive).  params may be NULL
+ * for the defaults.  On success *out receives a handle to free with
+ * mgx_process_destroy.  Errors: INVALID_ARGUMENT (NULL out, bad device),
+ * UNKNOWN_PROCESS, CUDA, NO_GOOD_HELICITY. */
+int mgx_process_create(const char* process, const mgx_params* params, int device,
+                       uint64_t filter_seed, mgx_process** out);
+
+/* Sizes of a process: particles, helicities before/after the filter, Feynman
+ * diagrams, diagram terms (one per colour structure of each four-gluon vertex)
+ * and colour flows.  Any pointer may be NULL. */
+int mgx_process_info(const mgx_process* proc, int* npar, int* nhel, int* ngood,
+                     int* ndiagrams, int* nterms, int* ncol);
+
+/* Copy the canonical indices of the good helicities (ascending) to host array
+ * out[ngood]. */
+int mgx_good_helicities(const mgx_process* proc, int32_t* out);
+
+/* Copy the float64 colour matrix to host array out[ncol*ncol] (row-major). */
+int mgx_colour_matrix(const mgx_process* proc, double* out);
+
+/* Device workspace (bytes) that mgx_compute needs for nevt events in `mode`. */
+int mgx_workspace_bytes(const mgx_process* proc, int64_t nevt, int mode, size_t* bytes);
+
+/* Compute a batch.  All arrays are DEVICE pointers on the process's device:
+ *   momenta [nevt][npar][4] f64, alpha_s [nevt] f64, rnd_hel/rnd_col [nevt] f64 in [0,1)
+ *   outputs me [nevt] f64, selhel [nevt] i32 (canonical helicity index),
+ *           selcol [nevt] i32 (colour-flow index).
+ * rnd_hel/rnd_col/selhel/selcol may all be NULL to skip selection.
+ * workspace: device buffer of at least mgx_workspace_bytes(nevt, mode) bytes
+ * (256-byte aligned); stream: a cudaStream_t (NULL = legacy default stream).
+ * Asynchronous; errors: INVALID_ARGUMENT, DEVICE_MISMATCH, WORKSPACE_TOO_SMALL,
+ * UNSUPPORTED_MODE, CUDA (launch failure). */
+int mgx_compute(mgx_process* proc, int64_t nevt, const double* momenta, const double* alpha_s,
+                const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel,
+                int32_t* selcol, int mode, void* workspace, size_t workspace_bytes, void* stream);
+
+/* As mgx_compute, with optional extra DEVICE outputs (each may be NULL):
+ *   mh   [nevt][ngood] f64: colour-summed |M_h|^2 per good helicity (not averaged)
+ *   colw [nevt][ncol]  f64: colour-selection weights w_s = sum_h |J_s(h)|^2. */
+int mgx_compute_ex(mgx_process* proc, int64_t nevt, const double* momenta, const double* alpha_s,
+                   const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel,
+                   int32_t* selcol, double* mh, double* colw, int mode, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
+/* End-to-end variant with HOST buffers (pinned memory recommended): copies the
+ * inputs to the device, computes, copies me/selhel/selcol back and
+ * synchronises the stream.  The device workspace must hold
+ * mgx_host_workspace_bytes(nevt, mode) bytes (staging + compute workspace). */
+int mgx_host_workspace_bytes(const mgx_process* proc, int64_t nevt, int mode, size_t* bytes);
+int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, const double* alpha_s,
+                     const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel,
+                     int32_t* selcol, int mode, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
+/* Number of float64 operations (add, multiply, fused multiply-add each one)
+ * the amplitude stage executes per event for this process, from the op table
+ * (used for roofline reporting). */
+double mgx_fp64_ops_per_event(const mgx_process* proc, int mode);
+
+void mgx_process_destroy(mgx_process* proc);
+const char* mgx_status_string(int status);
+int mgx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGX_H */

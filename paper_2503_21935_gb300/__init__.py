@@ -1,0 +1,184 @@
+"""mgx: GB300-native batched tree-level |M|^2 (arXiv:2503.21935 hot path).
+
+Thin Python binding over the C ABI in include/mgx.h (libmgx.so, built in-tree by
+paper_2503_21935_gb300.build).  Only argument marshalling happens here; every
+step of the matrix-element computation runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  There is no CPU fallback: importing
+the package without a built library, or calling it without a GPU, raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgx.so")
+
+MGX_OK = 0
+MGX_FP64 = 0
+MGX_MIXED_FP32 = 1
+MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32}
+
+
+class MgxError(RuntimeError):
+    pass
+
+
+class mgx_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("mt", "wt", "mz", "wz", "mta", "alpha_em", "gf", "filter_sqrt_s")]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libmgx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MgxError(f"libmgx.so is not built ({LIB_PATH}); run paper_2503_21935_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, SZ, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+        I, U64 = ctypes.c_int, ctypes.c_uint64
+        sig = {
+            "mgx_params_default": (None, [ctypes.POINTER(mgx_params)]),
+            "mgx_num_processes": (I, []),
+            "mgx_process_name": (ctypes.c_char_p, [I]),
+            "mgx_process_create": (I, [ctypes.c_char_p, ctypes.POINTER(mgx_params), I, U64, ctypes.POINTER(P)]),
+            "mgx_process_info": (I, [P] + [ctypes.POINTER(I)] * 6),
+            "mgx_good_helicities": (I, [P, P]),
+            "mgx_colour_matrix": (I, [P, P]),
+            "mgx_workspace_bytes": (I, [P, I64, I, ctypes.POINTER(SZ)]),
+            "mgx_compute": (I, [P, I64, P, P, P, P, P, P, P, I, P, SZ, P]),
+            "mgx_compute_ex": (I, [P, I64, P, P, P, P, P, P, P, P, P, I, P, SZ, P]),
+            "mgx_host_workspace_bytes": (I, [P, I64, I, ctypes.POINTER(SZ)]),
+            "mgx_compute_host": (I, [P, I64, P, P, P, P, P, P, P, I, P, SZ, P]),
+            "mgx_fp64_ops_per_event": (D, [P, I]),
+            "mgx_process_destroy": (None, [P]),
+            "mgx_status_string": (ctypes.c_char_p, [I]),
+            "mgx_version": (I, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != MGX_OK:
+        raise MgxError(f"{what}: {lib().mgx_status_string(rc).decode()} ({rc})")
+
+
+def default_params():
+    p = mgx_params()
+    lib().mgx_params_default(ctypes.byref(p))
+    return p
+
+
+def builtin_processes():
+    return [lib().mgx_process_name(i).decode() for i in range(lib().mgx_num_processes())]
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Process:
+    """A process on one CUDA device: mgx_process_create / mgx_compute / mgx_process_destroy."""
+
+    def __init__(self, process, params=None, device=0, filter_seed=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise MgxError("no CUDA device: the mgx library has no CPU path")
+        torch.cuda.init()
+        self.device = device
+        prm = default_params()
+        for k, v in (params or {}).items():
+            setattr(prm, k, float(v))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            _check(lib().mgx_process_create(process.encode(), ctypes.byref(prm), device, filter_seed,
+                                            ctypes.byref(h)), "mgx_process_create")
+        self._h = h
+        vals = [ctypes.c_int() for _ in range(6)]
+        _check(lib().mgx_process_info(h, *[ctypes.byref(v) for v in vals]), "mgx_process_info")
+        self.npar, self.nhel, self.ngood, self.ndiagrams, self.nterms, self.ncol = (v.value for v in vals)
+        g = np.zeros(self.ngood, dtype=np.int32)
+        _check(lib().mgx_good_helicities(h, g.ctypes.data_as(ctypes.c_void_p)), "mgx_good_helicities")
+        self.good_helicities = g.tolist()
+        self.process = process
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.mgx_process_destroy(h)
+            self._h = None
+
+    def colour_matrix(self):
+        C = np.zeros((self.ncol, self.ncol))
+        _check(lib().mgx_colour_matrix(self._h, C.ctypes.data_as(ctypes.c_void_p)), "mgx_colour_matrix")
+        return C
+
+    def workspace_bytes(self, nevt, mode=MGX_FP64, host=False):
+        b = ctypes.c_size_t()
+        f = lib().mgx_host_workspace_bytes if host else lib().mgx_workspace_bytes
+        _check(f(self._h, nevt, mode, ctypes.byref(b)), "workspace_bytes")
+        return b.value
+
+    def workspace(self, nevt, mode=MGX_FP64, host=False):
+        import torch
+        need = self.workspace_bytes(nevt, mode, host)
+        key = host
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+            self._ws[key] = ws
+        return ws
+
+    def fp64_ops_per_event(self, mode=MGX_FP64):
+        return lib().mgx_fp64_ops_per_event(self._h, mode)
+
+    def compute(self, momenta, alpha_s, rnd_hel=None, rnd_col=None, mode=MGX_FP64, mh=False, colw=False,
+                stream=None, out=None):
+        """Device tensors in, device tensors out (asynchronous on `stream`)."""
+        import torch
+        nevt = momenta.shape[0]
+        dev = momenta.device
+        for t in (momenta, alpha_s, rnd_hel, rnd_col):
+            if t is not None and (not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()):
+                raise MgxError("inputs must be contiguous float64 CUDA tensors")
+        if momenta.shape[1:] != (self.npar, 4):
+            raise MgxError(f"momenta must be [nevt, {self.npar}, 4]")
+        o = out or {}
+        me = o.get("me") if o.get("me") is not None else torch.empty(nevt, dtype=torch.float64, device=dev)
+        sel = rnd_hel is not None and rnd_col is not None
+        sh = (o.get("selhel") if o.get("selhel") is not None else torch.empty(nevt, dtype=torch.int32, device=dev)) if sel else None
+        sc = (o.get("selcol") if o.get("selcol") is not None else torch.empty(nevt, dtype=torch.int32, device=dev)) if sel else None
+        mh_t = torch.empty((nevt, self.ngood), dtype=torch.float64, device=dev) if mh else None
+        cw_t = torch.empty((nevt, self.ncol), dtype=torch.float64, device=dev) if colw else None
+        ws = self.workspace(nevt, mode)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        _check(lib().mgx_compute_ex(self._h, nevt, _ptr(momenta), _ptr(alpha_s), _ptr(rnd_hel), _ptr(rnd_col),
+                                    _ptr(me), _ptr(sh), _ptr(sc), _ptr(mh_t), _ptr(cw_t), mode, _ptr(ws),
+                                    ws.numel(), ctypes.c_void_p(st.cuda_stream)), "mgx_compute")
+        res = {"me": me}
+        if sel:
+            res["selhel"], res["selcol"] = sh, sc
+        if mh:
+            res["mh"] = mh_t
+        if colw:
+            res["colw"] = cw_t
+        return res
+
+    def compute_host(self, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, mode=MGX_FP64, stream=None):
+        """Host (ideally pinned) tensors in and out; copies happen inside the call."""
+        import torch
+        nevt = momenta.shape[0]
+        ws = self.workspace(nevt, mode, host=True)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _check(lib().mgx_compute_host(self._h, nevt, _ptr(momenta), _ptr(alpha_s), _ptr(rnd_hel), _ptr(rnd_col),
+                                      _ptr(me), _ptr(selhel), _ptr(selcol), mode, _ptr(ws), ws.numel(),
+                                      ctypes.c_void_p(st.cuda_stream)), "mgx_compute_host")

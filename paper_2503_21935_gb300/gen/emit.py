@@ -1,0 +1,70 @@
+"""Write the built-in process programs as a C include file for the library build."""
+import os
+
+from .program import build_program
+
+BUILTIN = [
+    "e+ e- > mu+ mu-",
+    "g g > t t~",
+    "g g > t t~ g",
+    "g g > t t~ g g",
+    "g g > t t~ g g g",
+    "g u~ > ta+ ta- g g u~",
+]
+
+_PARAM_ID = {"": 0, "mt": 1, "wt": 2, "mz": 3, "wz": 4, "mta": 5}
+_BOSON_ID = {"g": 0, "a": 1, "z": 2}
+
+
+def _arr(ctype, name, vals, per_line=16):
+    vals = list(vals)
+    body = []
+    for i in range(0, len(vals), per_line):
+        body.append("  " + ", ".join(vals[i:i + per_line]) + ",")
+    if not vals:
+        body.append("  0")
+    return f"static const {ctype} {name}[] = {{\n" + "\n".join(body) + "\n};\n"
+
+
+def emit(path):
+    from . import sm
+    out = ["/* generated by paper_2503_21935_gb300.gen.emit -- do not edit */\n"]
+    entries = []
+    for k, proc in enumerate(BUILTIN):
+        P = build_program(proc)
+        pre = f"mgx_p{k}"
+        out.append(_arr("int32_t", pre + "_ops", (str(x) for op in P.ops for x in op)))
+        out.append(_arr("int32_t", pre + "_flows", (str(x) for x in P.flows)))
+        out.append(_arr("double", pre + "_colour",
+                        (repr(float(x)) for row in P.colour for x in row), per_line=8))
+        spec = []
+        for boson, fermion in P.couplings:
+            q = sm.charge(fermion) if fermion else 0.0
+            t3 = sm.t3(fermion) if fermion else 0.0
+            spec += [str(_BOSON_ID[boson]), repr(q), repr(t3)]
+        out.append(_arr("double", pre + "_coupl", spec, per_line=9))
+        out.append(_arr("int32_t", pre + "_mass",
+                        (str(_PARAM_ID[x]) for pair in P.masses for x in pair)))
+        out.append(_arr("int32_t", pre + "_extmass", (str(x) for x in P.ext_mass)))
+        c = P.flop_counts
+        entries.append(
+            f'  {{"{P.process}", {P.npar}, {P.nin}, {P.root}, {len(P.ops)}, {pre}_ops, '
+            f'{len(P.flows) // 2}, {pre}_flows, {P.ncol}, {pre}_colour, {len(P.couplings)}, {pre}_coupl, '
+            f'{len(P.masses)}, {pre}_mass, {pre}_extmass, {P.ws_current_doubles}, {P.ndiagrams}, '
+            f'{P.nterms}, {P.average_den}, '
+            f'{{{c["var_ffv_f"]}, {c["var_ffv_fb"]}, {c["var_ffv_v"]}, {c["var_vvv"]}, {c["var_vvvv"]}, '
+            f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"]}, {c["amp"]}, {c["amp_flows"]}}}}},')
+    out.append("static const mgx_program_desc mgx_programs[] = {\n" + "\n".join(entries) + "\n};\n")
+    out.append(f"static const int mgx_num_programs = {len(BUILTIN)};\n")
+    text = "\n".join(out)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    old = open(path).read() if os.path.exists(path) else None
+    if old != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
+if __name__ == "__main__":
+    import sys
+    emit(sys.argv[1])

@@ -1,0 +1,126 @@
+"""GPU parity: the CUDA path through the C ABI against the float64 oracle, element by element.
+
+Bar (float64 path): per-event relative deviation of me, and of every per-helicity
+|M_h|^2 and colour weight relative to the event total, at most 1e-12; helicity and
+colour selection bit-exact except where a cumulative weight lies within 1e-12 of
+the random threshold.
+"""
+import numpy as np
+import pytest
+
+from phasespace import WORKLOADS, make_inputs, rambo, incoming_beams
+from oracle.matrix_element import get as oracle_get, near_tie
+
+TOL = 1e-12
+
+pytestmark = pytest.mark.gpu
+
+_procs = {}
+
+
+def _proc(name):
+    import paper_2503_21935_gb300 as pkg
+    if name not in _procs:
+        _procs[name] = pkg.Process(name, device=0)
+    return _procs[name]
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def _run(proc, mom, a, rh, rc, mode=0):
+    import torch
+    r = proc.compute(_dev(mom), _dev(a), _dev(rh), _dev(rc), mode=mode, mh=True, colw=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+CASES = [("eemumu", 300), ("ggtt", 300), ("ggttg", 260), ("ggttgg", 160), ("ggttggg", 20)]
+
+
+@pytest.mark.parametrize("name,nevt", CASES)
+def test_parity_fp64(name, nevt):
+    wl = WORKLOADS[name]
+    mom, a, rh, rc = make_inputs(wl, nevt)
+    proc = _proc(wl.process)
+    got = _run(proc, mom, a, rh, rc)
+    ref = oracle_get(wl.process).evaluate(mom, a, rh, rc)
+    rel = np.abs(got["me"] / ref["me"] - 1.0)
+    assert rel.max() <= TOL, f"me: max rel {rel.max():.3e}"
+    tot = ref["mh"].sum(axis=1, keepdims=True)
+    good = proc.good_helicities
+    assert np.abs(ref["mh"][:, [h for h in range(proc.nhel) if h not in good]]).max(initial=0.0) == 0.0
+    assert (np.abs(got["mh"] - ref["mh"][:, good]) / tot).max() <= TOL
+    ctot = ref["colw"].sum(axis=1, keepdims=True)
+    assert (np.abs(got["colw"] - ref["colw"]) / ctot).max() <= TOL
+    tie_h = near_tie(ref["mh"], rh, TOL)
+    tie_c = near_tie(ref["colw"], rc, TOL)
+    assert np.array_equal(got["selhel"][~tie_h], ref["selhel"][~tie_h])
+    assert np.array_equal(got["selcol"][~tie_c], ref["selcol"][~tie_c])
+
+
+@pytest.mark.parametrize("name", ["eemumu", "ggtt", "ggttg", "ggttgg"])
+def test_helicity_filter_matches_oracle(name):
+    wl = WORKLOADS[name]
+    proc = _proc(wl.process)
+    # the library's filter events: 16 RAMBO events at 1000 GeV, Philox key = filter seed 0, stream 0
+    po, _ = rambo(16, 1000.0, wl.final_masses(), seed=0)
+    p = np.concatenate([incoming_beams(16, 1000.0), po], axis=1)
+    assert proc.good_helicities == oracle_get(wl.process).helicity_filter(p, np.full(16, 0.118))
+
+
+@pytest.mark.parametrize("name,nevt,bound", [("ggttgg", 128, 1e-5), ("ggttggg", 12, 1e-5)])
+def test_parity_mixed_fp32_colour_sum(name, nevt, bound):
+    wl = WORKLOADS[name]
+    mom, a, rh, rc = make_inputs(wl, nevt)
+    got = _run(_proc(wl.process), mom, a, rh, rc, mode=1)
+    ref = oracle_get(wl.process).evaluate(mom, a)
+    assert np.abs(got["me"] / ref["me"] - 1.0).max() <= bound
+
+
+@pytest.mark.parametrize("nevt", [1, 127, 128, 129])
+def test_ragged_sizes(nevt):
+    wl = WORKLOADS["ggttg"]
+    mom, a, rh, rc = make_inputs(wl, nevt)
+    got = _run(_proc(wl.process), mom, a, rh, rc)
+    ref = oracle_get(wl.process).evaluate(mom, a)
+    assert np.abs(got["me"] / ref["me"] - 1.0).max() <= TOL
+
+
+def test_empty_batch_and_errors():
+    import torch
+    import paper_2503_21935_gb300 as pkg
+    proc = _proc(WORKLOADS["ggtt"].process)
+    z = torch.empty((0, 4, 4), dtype=torch.float64, device="cuda:0")
+    r = proc.compute(z, torch.empty(0, dtype=torch.float64, device="cuda:0"))
+    assert r["me"].numel() == 0
+    with pytest.raises(pkg.MgxError):
+        pkg.Process("g g > nothing", device=0)
+    with pytest.raises(pkg.MgxError):
+        proc.compute(torch.zeros((4, 5, 4), dtype=torch.float64, device="cuda:0"),
+                     torch.zeros(4, dtype=torch.float64, device="cuda:0"))
+    # too-small workspace is rejected before launch
+    import ctypes
+    m = torch.zeros((8, 4, 4), dtype=torch.float64, device="cuda:0")
+    o = torch.zeros(8, dtype=torch.float64, device="cuda:0")
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda:0")
+    rc = pkg.lib().mgx_compute(proc._h, 8, ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(o.data_ptr()), None, None,
+                               ctypes.c_void_p(o.data_ptr()), None, None, 0, ctypes.c_void_p(ws.data_ptr()), 256, None)
+    assert rc == -5
+
+
+def test_host_buffer_entry_point():
+    import torch
+    wl = WORKLOADS["ggttg"]
+    mom, a, rh, rc = make_inputs(wl, 200)
+    proc = _proc(wl.process)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    me = torch.empty(200, dtype=torch.float64).pin_memory()
+    sh = torch.empty(200, dtype=torch.int32).pin_memory()
+    sc = torch.empty(200, dtype=torch.int32).pin_memory()
+    proc.compute_host(pin(mom), pin(a), pin(rh), pin(rc), me, sh, sc)
+    dev = _run(proc, mom, a, rh, rc)
+    assert np.array_equal(me.numpy(), dev["me"])
+    assert np.array_equal(sh.numpy(), dev["selhel"]) and np.array_equal(sc.numpy(), dev["selcol"])
