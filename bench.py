@@ -1,0 +1,311 @@
+"""Throughput of the batched tree-level |M|^2 hot path on GB300.
+
+Workload: g g > t t~ g g (123 diagrams, 24 colour flows, 64 helicities), 2^20 flat
+RAMBO events per GPU at partonic sqrt(s) = 1500 GeV, m_t = 173 GeV, fixed
+alpha_s = 0.118; one step = one mgx_compute over the whole batch (momenta,
+alpha_s and random numbers already resident in HBM): external wavefunctions,
+every diagram amplitude, jamps, colour sum, helicity sum, helicity and colour
+selection.  Metric: |M|^2 evaluations per second (whole job).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|mixed_fp32] [--impl reference]
+
+Under torchrun each rank processes its own 2^20 events (weak scaling, no data
+collective); rank 0 prints one JSON line.  --impl reference times the float64
+CPU oracle on the host cores instead (bounded sample of the same workload).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ggttgg"
+NEVT = 1 << 20
+METRIC = "gg->ttgg |M|^2 evals/s (FP64)"
+# FP64 pipe: 152 SMs x 2 DFMA/clk/SM (measured: 1.20 TFLOP/s at 1995 MHz) x 2 flop x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed_fp32"])
+    ap.add_argument("--impl", default="mgx", choices=["mgx", "reference"])
+    ap.add_argument("--nevt", type=int, default=NEVT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def _oracle_worker(args):
+    wl_name, first, n = args
+    sys.path.insert(0, ROOT)
+    from phasespace import WORKLOADS, make_inputs
+    from oracle.matrix_element import get
+    wl = WORKLOADS[wl_name]
+    mom, a, rh, rc = make_inputs(wl, n, first=first)
+    me = get(wl.process)
+    me.evaluate(mom[:1], a[:1])          # warm caches / einsum paths outside the timing
+    t0 = time.perf_counter()
+    me.evaluate(mom, a, rh, rc)
+    return time.perf_counter() - t0, n
+
+
+def cpu_oracle_rate(wl_name, per_core, cores):
+    """Events/s of the float64 oracle on `cores` host processes, per_core events each."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    jobs = [(wl_name, 1000 + i * per_core, per_core) for i in range(cores)]
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    busy = max(t for t, _ in res)
+    n = sum(k for _, k in res)
+    return n / busy, n, busy, wall
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2503_21935_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_event(kernel, workload):
+    """DRAM bytes per event of `kernel` from the committed ncu summary, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d[f"{kernel}:{workload}"]
+        if e.get("source_sha") == _source_sha():
+            return e["dram_bytes_per_event"]
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    cores = _host_cores()
+    per_core = 384
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, n, busy, wall = cpu_oracle_rate(WORKLOAD, per_core, cores)
+        if i >= args.warmup:
+            rates.append((r, n, busy))
+    value = statistics.median(r for r, _, _ in rates)
+    n = rates[0][1]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(b for _, _, b in rates),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "g g > t t~ g g, flat RAMBO, sqrt(s)=1500 GeV, bounded sample per step",
+                       "nevt_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_core} events per core x {cores} spawn processes per step"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    rank, world, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    import paper_2503_21935_gb300 as pkg
+    from phasespace import WORKLOADS, make_inputs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = _host_cores()
+        per_core = 768
+        rate, n, busy, wall = cpu_oracle_rate(WORKLOAD, per_core, cores)
+        cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} events of the same workload ({per_core} per spawn process), {busy:.1f} s busy"}
+
+    wl = WORKLOADS[WORKLOAD]
+    nevt = args.nevt
+    mode = pkg.MODES[args.mode]
+    mom, a, rh, rc = make_inputs(wl, nevt, first=rank * nevt)     # each rank its own events
+    dev = torch.device(f"cuda:{local}")
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
+    proc = pkg.Process(wl.process, device=local)
+    out = {"me": torch.empty(nevt, dtype=torch.float64, device=dev),
+           "selhel": torch.empty(nevt, dtype=torch.int32, device=dev),
+           "selcol": torch.empty(nevt, dtype=torch.int32, device=dev)}
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        proc.compute(M, A, RH, RC, mode=mode, stream=stream, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for e0, e1 in evs:
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+    launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_ms = sum(launch_ms)
+    if dist is not None:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * nevt / (ms_per_step * 1e-3)
+
+    # end to end through the host-buffer entry point: pinned inputs in, results out, every step
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    hM, hA, hRH, hRC = pin(mom), pin(a), pin(rh), pin(rc)
+    hme = torch.empty(nevt, dtype=torch.float64).pin_memory()
+    hsh = torch.empty(nevt, dtype=torch.int32).pin_memory()
+    hsc = torch.empty(nevt, dtype=torch.int32).pin_memory()
+    proc.compute_host(hM, hA, hRH, hRC, hme, hsh, hsc, mode=mode, stream=stream)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        proc.compute_host(hM, hA, hRH, hRC, hme, hsh, hsc, mode=mode, stream=stream)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = sum(x.numel() * x.element_size() for x in (hM, hA, hRH, hRC))
+    d2h = sum(x.numel() * x.element_size() for x in (hme, hsh, hsc))
+
+    if rank == 0:
+        flops = 2.0 * proc.fp64_ops_per_event(mode) * nevt     # algorithmic float64 flops per launch
+        achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
+        per_evt = _traffic_per_event("me_kernel", WORKLOAD)
+        line = {"metric": METRIC if args.mode == "fp64" else METRIC.replace("FP64", "mixed FP32 colour sum"),
+                "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.mode == "fp64" else "f64+f32", "data": "synthetic",
+                "config": {"workload": f"g g > t t~ g g, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, "
+                                       "alpha_s=0.118", "process": wl.process, "nevt_per_gpu": nevt,
+                           "mode": args.mode, "ngood": proc.ngood, "ndiagrams": proc.ndiagrams,
+                           "ncol": proc.ncol, "l2": "inputs larger than L2 (192 MiB momenta, ~1 GiB workspace)"},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": achieved / FP64_PEAK_TFLOPS,
+                             "traffic": None if per_evt is None else per_evt * nevt,
+                             "kernel": "me_kernel", "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz"},
+                "e2e": {"value": world * nevt / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": args.steps,
+                "clocks": clk.summary(),
+                "cpu_baseline": cpu,
+                "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

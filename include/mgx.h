@@ -140,6 +140,18 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
                      int32_t* selcol, int mode, void* workspace, size_t workspace_bytes,
                      void* stream);
 
+/* Kernel variant (for tuning and testing).  THREAD: one thread per event, current variants
+ * and jamps in the global workspace (the default that AUTO resolves to).  CTA: one thread
+ * block per event with the event's currents in shared memory; available when the
+ * process's current store fits in shared memory and ncol <= 32.  Both give identical
+ * results up to float64 rounding. */
+enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2 };
+int mgx_process_set_kernel(mgx_process* proc, int kernel);  /* INVALID_ARGUMENT if unusable */
+int mgx_process_get_kernel(const mgx_process* proc);        /* the kernel AUTO resolves to */
+/* Thread blocks of 128 threads per SM for the thread-per-event kernel (1..16, default 4);
+ * the workspace size grows with it. */
+int mgx_process_set_blocks_per_sm(mgx_process* proc, int blocks_per_sm);
+
 /* Number of float64 operations (add, multiply, fused multiply-add each one)
  * the amplitude stage executes per event for this process, from the op table
  * (used for roofline reporting). */

@@ -18,6 +18,7 @@ MGX_OK = 0
 MGX_FP64 = 0
 MGX_MIXED_FP32 = 1
 MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32}
+MGX_KERNEL_AUTO, MGX_KERNEL_THREAD, MGX_KERNEL_CTA = 0, 1, 2
 
 
 class MgxError(RuntimeError):
@@ -54,6 +55,9 @@ def lib():
             "mgx_host_workspace_bytes": (I, [P, I64, I, ctypes.POINTER(SZ)]),
             "mgx_compute_host": (I, [P, I64, P, P, P, P, P, P, P, I, P, SZ, P]),
             "mgx_fp64_ops_per_event": (D, [P, I]),
+            "mgx_process_set_kernel": (I, [P, I]),
+            "mgx_process_get_kernel": (I, [P]),
+            "mgx_process_set_blocks_per_sm": (I, [P, I]),
             "mgx_process_destroy": (None, [P]),
             "mgx_status_string": (ctypes.c_char_p, [I]),
             "mgx_version": (I, []),
@@ -137,6 +141,18 @@ class Process:
             ws = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
             self._ws[key] = ws
         return ws
+
+    def set_kernel(self, kernel):
+        """MGX_KERNEL_AUTO / MGX_KERNEL_THREAD / MGX_KERNEL_CTA."""
+        _check(lib().mgx_process_set_kernel(self._h, kernel), "mgx_process_set_kernel")
+
+    @property
+    def kernel(self):
+        return lib().mgx_process_get_kernel(self._h)
+
+    def set_blocks_per_sm(self, n):
+        _check(lib().mgx_process_set_blocks_per_sm(self._h, n), "mgx_process_set_blocks_per_sm")
+        self._ws = {}
 
     def fp64_ops_per_event(self, mode=MGX_FP64):
         return lib().mgx_fp64_ops_per_event(self._h, mode)

@@ -29,7 +29,19 @@ struct mgx_program_desc {
   const int32_t* mass;   // (mass param, width param) per entry
   const int32_t* extmass;
   int ws_doubles, ndiag, nterm, avg_den;
-  int counts[8];         // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv; current ops; amp ops; amp flows
+  int counts[9];         // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil; current ops; amp ops; amp flows
+  struct {
+    int nops;
+    const int32_t* ops;
+    int nflows;
+    const int32_t* flows;
+    int nitems;
+    const int32_t* items;  // (op row << 8) | variant, variant 255 = header
+    int nsteps;
+    const int32_t* steps;  // (kind 0 = wave of items / 1 = amplitude rows, start, count)
+    int store;             // doubles of shared memory for one event's currents
+    int chunk;             // terms per chunk
+  } cta;
 };
 
 #include "generated/programs.inc"
@@ -41,46 +53,82 @@ using namespace mgx;
 // ------------------------------------------------------------------ kernel
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 128;        // thread-per-event kernel
+constexpr int kMaxColCta = 32;       // jamps per helicity held by one thread in the CTA kernel
+constexpr int kMaxColFp32 = 120;     // colour flows of the largest built-in process
 
-__device__ inline void colour_stage(const KParams& P, const WS& W, int mode) {
-  const int n = P.ncol;
-  for (int ih = 0; ih < P.ngood; ++ih) {
-    const int jb = P.jamp_off + 2 * n * ih;
-    double mh;
-    if (mode == MGX_MIXED_FP32) {
-      float acc = 0.0f;
-      for (int i = 0; i < n; ++i) {
-        const float ri = (float)W[jb + 2 * i], ii = (float)W[jb + 2 * i + 1];
-        const float* crow = P.colsym_f + i * n;
-        float zr = __ldg(crow + i) * ri, zi = __ldg(crow + i) * ii;
-        for (int j = i + 1; j < n; ++j) {
-          const float c = __ldg(crow + j);
-          zr = fmaf(c, (float)W[jb + 2 * j], zr);
-          zi = fmaf(c, (float)W[jb + 2 * j + 1], zi);
-        }
-        acc = fmaf(ri, zr, fmaf(ii, zi, acc));
+// |M_h|^2 = J^dagger C J with C given as C_ii on the diagonal and 2 C_ij above it.
+template <class JV>
+__device__ __forceinline__ double quad_form(const JV& J, const double* csym, const float* csym_f, int n, int mode) {
+  if (mode == MGX_MIXED_FP32) {
+    // one float64 -> float32 rounding per jamp component (conversions use the FP64 pipe)
+    float jf[2 * kMaxColFp32];
+    for (int k = 0; k < 2 * n; ++k) jf[k] = (float)J(k);
+    float acc = 0.0f;
+    for (int i = 0; i < n; ++i) {
+      const float ri = jf[2 * i], ii = jf[2 * i + 1];
+      const float* crow = csym_f + i * n;
+      float zr = __ldg(crow + i) * ri, zi = __ldg(crow + i) * ii;
+      for (int j = i + 1; j < n; ++j) {
+        const float c = __ldg(crow + j);
+        zr = fmaf(c, jf[2 * j], zr);
+        zi = fmaf(c, jf[2 * j + 1], zi);
       }
-      mh = (double)acc;
-    } else {
-      double acc = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const double ri = W[jb + 2 * i], ii = W[jb + 2 * i + 1];
-        const double* crow = P.colsym + i * n;
-        double zr = __ldg(crow + i) * ri, zi = __ldg(crow + i) * ii;
-        for (int j = i + 1; j < n; ++j) {
-          const double c = __ldg(crow + j);
-          zr = fma(c, W[jb + 2 * j], zr);
-          zi = fma(c, W[jb + 2 * j + 1], zi);
-        }
-        acc = fma(ri, zr, fma(ii, zi, acc));
-      }
-      mh = acc;
+      acc = fmaf(ri, zr, fmaf(ii, zi, acc));
     }
-    W[P.mh_off + ih] = mh;
+    return (double)acc;
+  }
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double ri = J(2 * i), ii = J(2 * i + 1);
+    const double* crow = csym + i * n;
+    double zr = __ldg(crow + i) * ri, zi = __ldg(crow + i) * ii;
+    for (int j = i + 1; j < n; ++j) {
+      const double c = __ldg(crow + j);
+      zr = fma(c, J(2 * j), zr);
+      zi = fma(c, J(2 * j + 1), zi);
+    }
+    acc = fma(ri, zr, fma(ii, zi, acc));
+  }
+  return acc;
+}
+
+// helicity sum (float64, canonical order), me and the two selections from per-helicity
+// weights mh[ngood] and colour weights colw[ncol] (any indexable storage)
+template <class A, class B>
+__device__ inline void finish_event(const KParams& P, int64_t e, const A& mh, const B& colw, const double* rhel,
+                                    const double* rcol, double* me, int32_t* selhel, int32_t* selcol) {
+  double tot = 0.0;
+  for (int ih = 0; ih < P.ngood; ++ih) tot += mh(ih);
+  me[e] = tot * P.avg;
+  if (selhel) {
+    const double target = rhel[e] * tot;
+    double acc = 0.0;
+    int sel = P.good[P.ngood - 1];
+    for (int ih = 0; ih < P.ngood; ++ih) {
+      acc += mh(ih);
+      if (acc > target) { sel = P.good[ih]; break; }
+    }
+    selhel[e] = sel;
+  }
+  if (selcol) {
+    double wt = 0.0;
+    for (int i = 0; i < P.ncol; ++i) wt += colw(i);
+    const double target = rcol[e] * wt;
+    double acc = 0.0;
+    int sel = P.ncol - 1;
+    for (int i = 0; i < P.ncol; ++i) {
+      acc += colw(i);
+      if (acc > target) { sel = i; break; }
+    }
+    selcol[e] = sel;
   }
 }
 
+// ---------------------------------------------------------------- thread-per-event kernel
+// Each thread owns one event at a time; current variants and jamps live in a per-thread
+// global workspace (offset-major so a warp's accesses coalesce).  Used for processes whose
+// per-event store does not fit in shared memory.
 __global__ void __launch_bounds__(kThreads)
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
@@ -105,25 +153,29 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = 0.0;
     for (int iop = 0; iop < P.nops; ++iop) {
       const Op o = load_op(P.ops, iop);
-      switch (o.code) {
-        case OP_EXT: op_ext(P, o, pe, W); break;
-        case OP_FFV_F: op_ffv_f(P, o, gs, W); break;
-        case OP_FFV_FB: op_ffv_fb(P, o, gs, W); break;
-        case OP_FFV_V: op_ffv_v(P, o, gs, W); break;
-        case OP_VVV: op_vvv(P, o, gs, W); break;
-        case OP_VVVV: op_vvvv(P, o, gs, W); break;
-        default: op_amp(P, o, gs, W); break;
+      if (o.code == OP_AMP) {
+        const int2* fl = P.flows + o.aux;
+        for (int ih = 0; ih < P.ngood; ++ih) {
+          const cx amp = amp_value(o, P.good[ih], W);
+          const int jb = P.jamp_off + 2 * P.ncol * ih;
+          for (int f = 0; f < o.aux2; ++f) {
+            const int2 q = __ldg(fl + f);
+            add_phase(W[jb + 2 * q.x], W[jb + 2 * q.x + 1], q.y, amp);
+          }
+        }
+        continue;
       }
+      op_header(P, o, gs, pe, W);
+      const int nv = 1 << __popc(o.mdst);
+      for (int v = 0; v < nv; ++v) op_variant(P, o, v, gs, pe, W);
     }
-    colour_stage(P, W, mode);
-    // helicity sum (float64, canonical order) and selections
-    double tot = 0.0;
-    for (int ih = 0; ih < P.ngood; ++ih) tot += W[P.mh_off + ih];
-    me[e] = tot * P.avg;
-    if (mh_out)
-      for (int ih = 0; ih < P.ngood; ++ih) mh_out[e * P.ngood + ih] = W[P.mh_off + ih];
-    const bool want_col = (selcol != nullptr) || (colw_out != nullptr);
-    if (want_col) {
+    for (int ih = 0; ih < P.ngood; ++ih) {
+      const int jb = P.jamp_off + 2 * P.ncol * ih;
+      const double mh = quad_form([&](int k) { return W[jb + k]; }, P.colsym, P.colsym_f, P.ncol, mode);
+      W[P.mh_off + ih] = mh;
+      if (mh_out) mh_out[e * P.ngood + ih] = mh;
+    }
+    if (selcol || colw_out) {
       for (int i = 0; i < P.ncol; ++i) {
         double w = 0.0;
         for (int ih = 0; ih < P.ngood; ++ih) {
@@ -134,28 +186,92 @@ __global__ void __launch_bounds__(kThreads)
         if (colw_out) colw_out[e * P.ncol + i] = w;
       }
     }
-    if (selhel) {
-      const double target = rhel[e] * tot;
-      double acc = 0.0;
-      int sel = P.good[P.ngood - 1];
-      for (int ih = 0; ih < P.ngood; ++ih) {
-        acc += W[P.mh_off + ih];
-        if (acc > target) { sel = P.good[ih]; break; }
+    finish_event(P, e, [&](int ih) { return W[P.mh_off + ih]; }, [&](int i) { return W[P.colw_off + i]; },
+                 rhel, rcol, me, selhel, selcol);
+  }
+}
+
+// ---------------------------------------------------------------- CTA-per-event kernel
+// One CTA evaluates one event at a time with the event's current store in shared memory.
+// Current waves: threads take (current, helicity-variant) items; amplitude steps: thread t
+// closes every diagram term of the step for good helicity t and keeps that helicity's
+// jamps in its own local array; then each thread forms its |M_h|^2.
+struct CtaTab {
+  const int4* ops;
+  const int2* flows;
+  const int* items;
+  const int3* steps;
+  int nsteps, store;
+};
+
+template <int T>
+__global__ void __launch_bounds__(T)
+    me_cta_kernel(const KParams P, const CtaTab C, int64_t nevt, const double* __restrict__ mom,
+                  const double* __restrict__ alphas, const double* __restrict__ rhel,
+                  const double* __restrict__ rcol, double* __restrict__ me, int32_t* __restrict__ selhel,
+                  int32_t* __restrict__ selcol, double* __restrict__ mh_out, double* __restrict__ colw_out,
+                  int mode) {
+  extern __shared__ double sm[];
+  double* store = sm;
+  double* pe = sm + C.store;
+  const SS W{store};
+  const int tid = threadIdx.x;
+  const int npar4 = 4 * P.npar;
+  const bool act = tid < P.ngood;
+  const int h = act ? P.good[tid] : 0;
+  const int ncol = P.ncol;
+  for (int64_t e = blockIdx.x; e < nevt; e += gridDim.x) {
+    for (int i = tid; i < npar4; i += T) pe[i] = __ldg(mom + e * npar4 + i);
+    __syncthreads();
+    const double gs = sqrt(4.0 * M_PI * __ldg(alphas + e));
+    double J[2 * kMaxColCta];
+#pragma unroll
+    for (int i = 0; i < 2 * kMaxColCta; ++i) J[i] = 0.0;
+    for (int s = 0; s < C.nsteps; ++s) {
+      const int3 st = C.steps[s];
+      if (st.x == 0) {
+        for (int it = tid; it < st.z; it += T) {
+          const int item = __ldg(C.items + st.y + it);
+          const Op o = load_op(C.ops, item >> 8);
+          const int v = item & 255;
+          if (v == 255) op_header(P, o, gs, pe, W);
+          else op_variant(P, o, v, gs, pe, W);
+        }
+      } else if (act) {
+        for (int a = st.y; a < st.y + st.z; ++a) {
+          const Op o = load_op(C.ops, a);
+          const cx amp = amp_value(o, h, W);
+          const int2* fl = C.flows + o.aux;
+          for (int f = 0; f < o.aux2; ++f) {
+            const int2 q = __ldg(fl + f);
+            add_phase(J[2 * q.x], J[2 * q.x + 1], q.y, amp);
+          }
+        }
       }
-      selhel[e] = sel;
+      __syncthreads();
     }
-    if (selcol) {
-      double wt = 0.0;
-      for (int i = 0; i < P.ncol; ++i) wt += W[P.colw_off + i];
-      const double target = rcol[e] * wt;
-      double acc = 0.0;
-      int sel = P.ncol - 1;
-      for (int i = 0; i < P.ncol; ++i) {
-        acc += W[P.colw_off + i];
-        if (acc > target) { sel = i; break; }
-      }
-      selcol[e] = sel;
+    // the store is dead now: reuse it for per-helicity results
+    double* mh_s = store;
+    double* cwh_s = store + P.ngood;           // [ngood][ncol] |J_i(h)|^2
+    double* colw_s = cwh_s + P.ngood * ncol;
+    if (act) {
+      const double mh = quad_form([&](int k) { return J[k]; }, P.colsym, P.colsym_f, ncol, mode);
+      mh_s[tid] = mh;
+      if (mh_out) mh_out[e * P.ngood + tid] = mh;
+      for (int i = 0; i < ncol; ++i) cwh_s[tid * ncol + i] = fma(J[2 * i], J[2 * i], J[2 * i + 1] * J[2 * i + 1]);
     }
+    __syncthreads();
+    for (int i = tid; i < ncol; i += T) {
+      double w = 0.0;
+      for (int ih = 0; ih < P.ngood; ++ih) w += cwh_s[ih * ncol + i];
+      colw_s[i] = w;
+      if (colw_out) colw_out[e * ncol + i] = w;
+    }
+    __syncthreads();
+    if (tid == 0)
+      finish_event(P, e, [&](int ih) { return mh_s[ih]; }, [&](int i) { return colw_s[i]; }, rhel, rcol, me, selhel,
+                   selcol);
+    __syncthreads();
   }
 }
 
@@ -277,7 +393,12 @@ struct mgx_process {
   int2* d_flows = nullptr;
   double* d_col = nullptr;
   float* d_colf = nullptr;
-  int blocks_per_sm = 1;
+  int4* d_cta_ops = nullptr;
+  int2* d_cta_flows = nullptr;
+  int* d_cta_items = nullptr;
+  int3* d_cta_steps = nullptr;
+  int blocks_per_sm = 4;      // thread-per-event kernel
+  int kernel = MGX_KERNEL_AUTO;
 };
 
 namespace {
@@ -298,10 +419,45 @@ void set_layout(KParams& kp, int cur_doubles, int ngood, int ncol) {
   kp.ws_doubles = kp.colw_off + ncol;
 }
 
+bool cta_usable(const mgx_process* pr, const KParams& kp) {
+  return pr->prog->cta.nops > 0 && kp.ngood <= 128 && kp.ncol <= kMaxColCta;
+}
+
+bool use_cta(const mgx_process* pr, const KParams& kp) {
+  return pr->kernel == MGX_KERNEL_CTA && cta_usable(pr, kp);
+}
+
+size_t cta_smem_bytes(const mgx_process* pr, const KParams& kp) {
+  const int results = kp.ngood + kp.ngood * kp.ncol + kp.ncol;
+  return (size_t)(std::max(pr->prog->cta.store, results) + 4 * kp.npar) * sizeof(double);
+}
+
+template <int T>
+int launch_cta(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
+               const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
+               int mode, cudaStream_t st) {
+  const size_t smem = cta_smem_bytes(pr, kp);
+  if (cudaFuncSetAttribute(me_cta_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return MGX_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_cta_kernel<T>, T, smem) != cudaSuccess || per_sm < 1)
+    return MGX_ERR_CUDA;
+  const int64_t blocks = std::min<int64_t>(nevt, (int64_t)per_sm * sm_count(pr->device));
+  CtaTab C{pr->d_cta_ops, pr->d_cta_flows, pr->d_cta_items, pr->d_cta_steps, pr->prog->cta.nsteps,
+           pr->prog->cta.store};
+  me_cta_kernel<T><<<(unsigned)blocks, T, smem, st>>>(kp, C, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
 int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
            const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
            int mode, void* ws, size_t wsb, cudaStream_t st) {
   if (nevt == 0) return MGX_OK;
+  if (use_cta(pr, kp)) {
+    if (kp.ngood <= 32) return launch_cta<32>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
+    if (kp.ngood <= 64) return launch_cta<64>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
+    return launch_cta<128>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
+  }
   const int64_t nt = grid_threads(pr, nevt);
   const size_t need = (size_t)nt * ws_doubles_per_thread(kp) * sizeof(double);
   if (wsb < need || ws == nullptr) return MGX_ERR_WORKSPACE_TOO_SMALL;
@@ -354,6 +510,10 @@ void mgx_process_destroy(mgx_process* pr) {
   cudaFree(pr->d_flows);
   cudaFree(pr->d_col);
   cudaFree(pr->d_colf);
+  cudaFree(pr->d_cta_ops);
+  cudaFree(pr->d_cta_flows);
+  cudaFree(pr->d_cta_items);
+  cudaFree(pr->d_cta_steps);
   cudaSetDevice(cur);
   delete pr;
 }
@@ -430,6 +590,17 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
        cudaMemcpy(pr->d_flows, prog->flows, sizeof(int32_t) * 2 * prog->nflows, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(pr->d_col, cs.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(pr->d_colf, csf.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  const auto& ct = prog->cta;
+  if (ok && ct.nops > 0) {
+    ok = cudaMalloc(&pr->d_cta_ops, sizeof(int32_t) * 16 * ct.nops) == cudaSuccess &&
+         cudaMalloc(&pr->d_cta_flows, sizeof(int2) * std::max(1, ct.nflows)) == cudaSuccess &&
+         cudaMalloc(&pr->d_cta_items, sizeof(int) * std::max(1, ct.nitems)) == cudaSuccess &&
+         cudaMalloc(&pr->d_cta_steps, sizeof(int3) * std::max(1, ct.nsteps)) == cudaSuccess;
+    ok = ok && cudaMemcpy(pr->d_cta_ops, ct.ops, sizeof(int32_t) * 16 * ct.nops, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(pr->d_cta_flows, ct.flows, sizeof(int32_t) * 2 * ct.nflows, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(pr->d_cta_items, ct.items, sizeof(int) * ct.nitems, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(pr->d_cta_steps, ct.steps, sizeof(int3) * ct.nsteps, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
   if (!ok) {
     mgx_process_destroy(pr);
     cudaSetDevice(cur);
@@ -514,7 +685,7 @@ int mgx_colour_matrix(const mgx_process* pr, double* out) {
 int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* bytes) {
   if (!pr || !bytes || nevt < 0) return MGX_ERR_INVALID_ARGUMENT;
   if (mode != MGX_FP64 && mode != MGX_MIXED_FP32) return MGX_ERR_UNSUPPORTED_MODE;
-  *bytes = nevt == 0 ? 0 : (size_t)grid_threads(pr, nevt) * pr->kp.ws_doubles * sizeof(double);
+  *bytes = (nevt == 0 || use_cta(pr, pr->kp)) ? 0 : (size_t)grid_threads(pr, nevt) * pr->kp.ws_doubles * sizeof(double);
   return MGX_OK;
 }
 
@@ -592,16 +763,35 @@ int mgx_compute_host(mgx_process* pr, int64_t nevt, const double* momenta, const
   return ok ? MGX_OK : MGX_ERR_CUDA;
 }
 
+int mgx_process_set_kernel(mgx_process* pr, int kernel) {
+  if (!pr || kernel < MGX_KERNEL_AUTO || kernel > MGX_KERNEL_CTA) return MGX_ERR_INVALID_ARGUMENT;
+  if (kernel == MGX_KERNEL_CTA && !cta_usable(pr, pr->kp)) return MGX_ERR_INVALID_ARGUMENT;
+  pr->kernel = kernel;
+  return MGX_OK;
+}
+
+int mgx_process_get_kernel(const mgx_process* pr) {
+  if (!pr) return MGX_ERR_INVALID_ARGUMENT;
+  return use_cta(pr, pr->kp) ? MGX_KERNEL_CTA : MGX_KERNEL_THREAD;
+}
+
+int mgx_process_set_blocks_per_sm(mgx_process* pr, int blocks_per_sm) {
+  if (!pr || blocks_per_sm < 1 || blocks_per_sm > 16) return MGX_ERR_INVALID_ARGUMENT;
+  pr->blocks_per_sm = blocks_per_sm;
+  return MGX_OK;
+}
+
 double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) {
   if (!pr) return 0.0;
-  // float64 instruction counts per variant / per good helicity of each op kind, read off the
-  // device code in mgx_ops.cuh (fma, mul and add each count as one operation)
+  // float64 instructions per variant / per good helicity of each op kind, read off the
+  // device code in mgx_ops.cuh (fma, mul and add each count as one instruction)
   const int* c = pr->prog->counts;
   const double ngood = (double)pr->good.size();
   const int n = pr->prog->ncol;
-  double ops = 96.0 * c[0] + 96.0 * c[1] + 80.0 * c[2] + 70.0 * c[3] + 60.0 * c[4];
-  ops += ngood * (60.0 * c[6] + 2.0 * c[7]);
-  if (mode == MGX_FP64) ops += ngood * (2.0 * n * (n + 1) + 2.0);
+  double ops = 92.0 * c[0] + 92.0 * c[1] + 56.0 * c[2] + 66.0 * c[3] + 52.0 * c[4] + 48.0 * c[5];
+  ops += ngood * (16.0 * c[7] + 2.0 * c[8]);
+  ops += ngood * (mode == MGX_FP64 ? (2.0 * n * (n + 1) + 2.0) : 2.0 * n);  // quadratic form / conversions
+  ops += ngood * 2.0 * n;                                                  // colour weights
   return ops;
 }
 

@@ -146,7 +146,10 @@ class Diagrams:
                 continue
             f = self.flav_in[i]
             self._new(1 << i, f, "EXT", leg=i, colour={(i,): 1} if f == "g" else {(): 1})
-        self.root_current = Current(-1, 1 << self.root, self.flav_in[self.root], "EXT", leg=self.root)
+        # the root's external wavefunction is a current too (not offered to subtree building)
+        self.root_current = Current(len(self.currents), 1 << self.root, self.flav_in[self.root], "EXT",
+                                    leg=self.root)
+        self.currents.append(self.root_current)
         full = ((1 << n) - 1) & ~(1 << self.root)
         masks = sorted((m for m in range(1, full + 1) if m & full == m), key=lambda m: (bin(m).count("1"), m))
         for S in masks:

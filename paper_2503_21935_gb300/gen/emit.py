@@ -47,13 +47,25 @@ def emit(path):
                         (str(_PARAM_ID[x]) for pair in P.masses for x in pair)))
         out.append(_arr("int32_t", pre + "_extmass", (str(x) for x in P.ext_mass)))
         c = P.flop_counts
+        cta = P.cta
+        if cta is not None:
+            out.append(_arr("int32_t", pre + "_cta_ops", (str(x) for op in cta["ops"] for x in op)))
+            out.append(_arr("int32_t", pre + "_cta_flows", (str(x) for x in cta["flows"])))
+            out.append(_arr("int32_t", pre + "_cta_items", (str(x) for x in cta["items"])))
+            out.append(_arr("int32_t", pre + "_cta_steps", (str(x) for st in cta["steps"] for x in st)))
+            cta_init = (f'{{{len(cta["ops"])}, {pre}_cta_ops, {len(cta["flows"]) // 2}, {pre}_cta_flows, '
+                        f'{len(cta["items"])}, {pre}_cta_items, {len(cta["steps"])}, {pre}_cta_steps, '
+                        f'{cta["store"]}, {cta["chunk"]}}}')
+        else:
+            cta_init = "{0, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, 0}"
         entries.append(
             f'  {{"{P.process}", {P.npar}, {P.nin}, {P.root}, {len(P.ops)}, {pre}_ops, '
             f'{len(P.flows) // 2}, {pre}_flows, {P.ncol}, {pre}_colour, {len(P.couplings)}, {pre}_coupl, '
             f'{len(P.masses)}, {pre}_mass, {pre}_extmass, {P.ws_current_doubles}, {P.ndiagrams}, '
             f'{P.nterms}, {P.average_den}, '
-            f'{{{c["var_ffv_f"]}, {c["var_ffv_fb"]}, {c["var_ffv_v"]}, {c["var_vvv"]}, {c["var_vvvv"]}, '
-            f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"]}, {c["amp"]}, {c["amp_flows"]}}}}},')
+            f'{{{c["var_ffv_f"]}, {c["var_ffv_fb"]}, {c["var_ffv_v"]}, {c["var_vvv"]}, {c["var_vvvv"]}, {c["var_bil"]}, '
+            f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"] + c["bil"]}, {c["amp"]}, {c["amp_flows"]}}}, '
+            f'{cta_init}}},')
     out.append("static const mgx_program_desc mgx_programs[] = {\n" + "\n".join(entries) + "\n};\n")
     out.append(f"static const int mgx_num_programs = {len(BUILTIN)};\n")
     text = "\n".join(out)

@@ -19,9 +19,9 @@ from fractions import Fraction
 
 from . import sm
 from .colour import colour_matrix
-from .diagrams import Diagrams
+from .diagrams import Diagrams, Current
 
-OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP = 1, 2, 3, 4, 5, 6, 7
+OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP, OP_BIL = 1, 2, 3, 4, 5, 6, 7, 8
 EXT_U, EXT_V, EXT_UBAR, EXT_VBAR, EXT_EPS_IN, EXT_EPS_OUT = 0, 1, 2, 3, 4, 5
 NFIELD = 16
 
@@ -60,38 +60,185 @@ def _bit(npar, leg):
     return 1 << (npar - 1 - leg)
 
 
-def build_program(process):
-    lhs, rhs = process.split(">")
-    inc, out = lhs.split(), rhs.split()
-    D = Diagrams(inc, out)
-    npar = D.npar
-    cur = D.currents
+HEADER = {"EXT": 4, "FFV_F": 6, "FFV_FB": 6, "FFV_V": 6, "VVV": 18, "VVVV": 6, "BIL": 6}
+SMEM_STORE_BUDGET = 64 * 1024     # bytes of shared memory for one event's current store
 
-    def hmask(m):
-        # convert a leg bitmask (bit leg) to helicity-bit positions (bit npar-1-leg)
-        return sum(_bit(npar, p) for p in range(npar) if m >> p & 1)
 
-    # ---- mass / coupling tables
-    masses = [("", "")]
-    def mass_index(flav):
+class _Allocator:
+    """First-fit allocator over a linear range of doubles; frees merge with neighbours."""
+
+    def __init__(self):
+        self.free = []
+        self.top = 0
+
+    def alloc(self, size):
+        for k, (s, z) in enumerate(self.free):
+            if z >= size:
+                if z == size:
+                    self.free.pop(k)
+                else:
+                    self.free[k] = (s + size, z - size)
+                return s
+        s = self.top
+        self.top += size
+        return s
+
+    def release(self, s, size):
+        self.free.append((s, size))
+        self.free.sort()
+        merged = []
+        for a, z in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == a:
+                merged[-1] = (merged[-1][0], merged[-1][1] + z)
+            else:
+                merged.append((a, z))
+        self.free = merged
+
+
+class _Builder:
+    """Common encoding of ops for both schedules."""
+
+    def __init__(self, D):
+        self.D = D
+        self.npar = D.npar
+        self.masses = [("", "")]
+        self.couplings = []
+        self.ext_mass = [0] * D.npar
+        self.ROOT = D.root_current.id
+        self._add_bilinears()
+
+    def _add_bilinears(self):
+        """Root bilinears Q^mu = psibar_root gamma^mu (cL PL + cR PR) psi_col, one per (column
+        current, coupling): every diagram term is then Q . V, so the fermion-line algebra at the
+        root vertex is done once per (root, column) helicity pair instead of per full helicity."""
+        D = self.D
+        key_of = {}
+        for t in D.terms:
+            col, vec = D.currents[t.col], D.currents[t.vec]
+            k = self.coupling_index(vec.flav, col.flav)
+            key = (t.col, k)
+            if key not in key_of:
+                c = Current(len(D.currents), D.root_current.mask | col.mask, "BIL", "BIL",
+                            children=(self.ROOT, t.col))
+                c.cpl = k
+                D.currents.append(c)
+                key_of[key] = c.id
+            t.bil = key_of[key]
+
+    def hmask(self, m):
+        return sum(_bit(self.npar, p) for p in range(self.npar) if m >> p & 1)
+
+    def mass_index(self, flav):
         key = (sm.mass_param(flav), sm.width_param(flav))
         if key == ("", ""):
             return 0
-        if key not in masses:
-            masses.append(key)
-        return masses.index(key)
+        if key not in self.masses:
+            self.masses.append(key)
+        return self.masses.index(key)
 
-    couplings = []
-    def coupling_index(boson, fermion):
+    def coupling_index(self, boson, fermion):
         base = fermion if not sm.is_anti(fermion) else sm.anti(fermion)
         spec = (boson, base if boson != "g" else "")
-        if spec not in couplings:
-            couplings.append(spec)
-        return couplings.index(spec)
+        if spec not in self.couplings:
+            self.couplings.append(spec)
+        return self.couplings.index(spec)
 
-    # ---- schedule: depth-first from each term
-    order = []
-    done = set()
+    def cur(self, i):
+        return self.D.currents[i]
+
+    def nvar(self, i):
+        return 1 << bin(self.cur(i).mask).count("1")
+
+    def blocksize(self, i):
+        return HEADER[self.cur(i).op] + 8 * self.nvar(i)
+
+    def varbase(self, i, offset):
+        return offset[i] + HEADER[self.cur(i).op]
+
+    def current_row(self, i, offset):
+        D = self.D
+        c = self.cur(i)
+        op = [0] * NFIELD
+        op[1] = offset[i]
+        op[5] = self.hmask(c.mask)
+        if c.op == "EXT":
+            leg = c.leg
+            f = c.flav
+            initial = leg < D.nin
+            if sm.kind(f) == "V":
+                etype = EXT_EPS_IN if initial else EXT_EPS_OUT
+            else:
+                phys = D.incoming[leg] if initial else D.outgoing[leg - D.nin]
+                anti = sm.is_anti(phys)
+                etype = ({(True, False): EXT_U, (True, True): EXT_VBAR,
+                          (False, False): EXT_UBAR, (False, True): EXT_V})[(initial, anti)]
+            mi = self.mass_index(f)
+            self.ext_mass[leg] = mi
+            op[0], op[10], op[11], op[12] = OP_EXT, mi, leg, etype
+            return op
+        ch = [D.currents[k] for k in c.children]
+        for slot, k in enumerate(c.children):
+            op[2 + slot] = offset[k]
+            op[6 + slot] = self.hmask(D.currents[k].mask)
+            op[13 + slot] = self.varbase(k, offset)
+        if c.op == "FFV_F":
+            op[0], op[9], op[10] = OP_FFV_F, self.coupling_index(ch[1].flav, ch[0].flav), self.mass_index(c.flav)
+        elif c.op == "FFV_FB":
+            op[0], op[9], op[10] = OP_FFV_FB, self.coupling_index(ch[1].flav, ch[0].flav), self.mass_index(c.flav)
+        elif c.op == "FFV_V":
+            op[0], op[9], op[10] = OP_FFV_V, self.coupling_index(c.flav, ch[1].flav), self.mass_index(c.flav)
+        elif c.op == "VVV":
+            op[0] = OP_VVV
+        elif c.op == "VVVV":
+            op[0], op[11] = OP_VVVV, c.struct
+        elif c.op == "BIL":
+            op[0], op[9] = OP_BIL, c.cpl
+        else:
+            raise ValueError(c.op)
+        return op
+
+    def amp_row(self, ti, offset, flows):
+        D = self.D
+        t = D.terms[ti]
+        bil, vec = D.currents[t.bil], D.currents[t.vec]
+        op = [0] * NFIELD
+        op[0] = OP_AMP
+        op[2], op[3] = offset[t.bil], offset[t.vec]
+        op[6], op[7] = self.hmask(bil.mask), self.hmask(vec.mask)
+        op[13], op[14] = self.varbase(t.bil, offset), self.varbase(t.vec, offset)
+        op[11] = len(flows) // 2
+        nf = 0
+        for word, coeff in sorted(t.colour.items()):
+            full = complex(coeff) * (-1j)          # M = -i * (diagram value)
+            key = complex(round(full.real), round(full.imag))
+            if abs(full - key) > 1e-12 or key not in _PHASE:
+                raise ValueError(f"unexpected colour coefficient {coeff}")
+            flows += [D_perm_index(D, word), _PHASE[key]]
+            nf += 1
+        op[12] = nf
+        return op
+
+
+def _closure(D, ti):
+    out = set()
+    st = [D.terms[ti].bil, D.terms[ti].vec]
+    while st:
+        x = st.pop()
+        if x in out:
+            continue
+        out.add(x)
+        st.extend(D.currents[x].children)
+    return out
+
+
+def _dfs_schedule(B):
+    """Thread-per-event schedule: ops in depth-first order, blocks freed after last use."""
+    D = B.D
+    cur = D.currents
+    ROOT = B.ROOT
+    order = [("C", ROOT)]
+    done = {ROOT}
+
     def emit(i):
         if i in done:
             return
@@ -100,155 +247,129 @@ def build_program(process):
         done.add(i)
         order.append(("C", i))
     for ti, t in enumerate(D.terms):
-        emit(t.col)
+        emit(t.bil)
         emit(t.vec)
         order.append(("A", ti))
-    ROOT = -1
-    order.insert(0, ("C", ROOT))
 
     def uses(item):
         kind, x = item
         if kind == "C":
-            return [] if x == ROOT else list(cur[x].children)
+            return list(cur[x].children)
         t = D.terms[x]
-        return [ROOT, t.col, t.vec]
-
+        return [t.bil, t.vec]
     last = {}
     for pos, item in enumerate(order):
         for u in uses(item):
             last[u] = pos
-
-    def nvar(i):
-        m = D.root_current.mask if i == ROOT else cur[i].mask
-        return 1 << bin(m).count("1")
-
-    # ---- first-fit allocation of current blocks
-    free = []          # list of (start, size)
-    top = 0
+    A = _Allocator()
     offset = {}
-
-    def alloc(size):
-        nonlocal top
-        for k, (s, z) in enumerate(free):
-            if z >= size:
-                if z == size:
-                    free.pop(k)
-                else:
-                    free[k] = (s + size, z - size)
-                return s
-        s = top
-        top += size
-        return s
-
-    def release(s, size):
-        free.append((s, size))
-        free.sort()
-        merged = []
-        for a, z in free:
-            if merged and merged[-1][0] + merged[-1][1] == a:
-                merged[-1] = (merged[-1][0], merged[-1][1] + z)
-            else:
-                merged.append((a, z))
-        free[:] = merged
-
-    def blocksize(i):
-        return 4 + 8 * nvar(i)
-
-    ops = []
-    flows = []
-    ext_mass = [0] * npar
-    counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, amp=0, amp_flows=0,
-                  var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0)
+    ops, flows = [], []
     for pos, item in enumerate(order):
         kind, x = item
-        op = [0] * NFIELD
         if kind == "C":
-            c = D.root_current if x == ROOT else cur[x]
-            off = alloc(blocksize(x))
-            offset[x] = off
-            op[1] = off
-            op[5] = hmask(c.mask)
-            if c.op == "EXT":
-                leg = c.leg
-                f = c.flav                      # all-incoming flavour
-                initial = leg < D.nin
-                if sm.kind(f) == "V":
-                    etype = EXT_EPS_IN if initial else EXT_EPS_OUT
-                else:
-                    phys = D.incoming[leg] if initial else D.outgoing[leg - D.nin]
-                    anti = sm.is_anti(phys)
-                    etype = ({(True, False): EXT_U, (True, True): EXT_VBAR,
-                              (False, False): EXT_UBAR, (False, True): EXT_V})[(initial, anti)]
-                mi = mass_index(f)
-                ext_mass[leg] = mi
-                op[0] = OP_EXT
-                op[10] = mi
-                op[11] = leg
-                op[12] = etype
-                counts["ext"] += 1
-            else:
-                ch = [cur[k] for k in c.children]
-                for slot, k in enumerate(c.children):
-                    op[2 + slot] = offset[k]
-                    op[6 + slot] = hmask(cur[k].mask)
-                nv = nvar(x)
-                if c.op == "FFV_F":
-                    ferm, vec = ch
-                    op[0] = OP_FFV_F
-                    op[9] = coupling_index(vec.flav, ferm.flav)
-                    op[10] = mass_index(c.flav)
-                    counts["ffv_f"] += 1
-                    counts["var_ffv_f"] += nv
-                elif c.op == "FFV_FB":
-                    ferm, vec = ch
-                    op[0] = OP_FFV_FB
-                    op[9] = coupling_index(vec.flav, ferm.flav)
-                    op[10] = mass_index(c.flav)
-                    counts["ffv_fb"] += 1
-                    counts["var_ffv_fb"] += nv
-                elif c.op == "FFV_V":
-                    row, col = ch
-                    op[0] = OP_FFV_V
-                    op[9] = coupling_index(c.flav, col.flav)
-                    op[10] = mass_index(c.flav)
-                    counts["ffv_v"] += 1
-                    counts["var_ffv_v"] += nv
-                elif c.op == "VVV":
-                    op[0] = OP_VVV
-                    counts["vvv"] += 1
-                    counts["var_vvv"] += nv
-                elif c.op == "VVVV":
-                    op[0] = OP_VVVV
-                    op[11] = c.struct
-                    counts["vvvv"] += 1
-                    counts["var_vvvv"] += nv
-                else:
-                    raise ValueError(c.op)
+            offset[x] = A.alloc(B.blocksize(x))
+            ops.append(B.current_row(x, offset))
         else:
-            t = D.terms[x]
-            col, vec = cur[t.col], cur[t.vec]
-            op[0] = OP_AMP
-            op[2], op[3], op[4] = offset[ROOT], offset[t.col], offset[t.vec]
-            op[6], op[7], op[8] = hmask(D.root_current.mask), hmask(col.mask), hmask(vec.mask)
-            op[9] = coupling_index(vec.flav, col.flav)
-            op[11] = len(flows) // 2
-            nf = 0
-            for word, coeff in sorted(t.colour.items()):
-                full = complex(coeff) * (-1j)          # M = -i * (diagram value)
-                fl = D_perm_index(D, word)
-                key = complex(round(full.real), round(full.imag))
-                if abs(full - key) > 1e-12 or key not in _PHASE:
-                    raise ValueError(f"unexpected colour coefficient {coeff}")
-                flows += [fl, _PHASE[key]]
-                nf += 1
-            op[12] = nf
-            counts["amp"] += 1
-            counts["amp_flows"] += nf
-        ops.append(op)
+            ops.append(B.amp_row(x, offset, flows))
         for u in set(uses(item)):
             if last[u] == pos:
-                release(offset[u], blocksize(u))
+                A.release(offset[u], B.blocksize(u))
+    return ops, flows, A.top
 
+
+def _wave_schedule(B, chunk):
+    """CTA-per-event schedule: terms in chunks; each chunk computes the currents it still
+    needs level by level in waves of independent (current, variant) items, then closes its
+    terms.  Returns (ops, flows, items, steps, store_doubles)."""
+    D = B.D
+    cur = D.currents
+    ROOT = B.ROOT
+    level = {}
+
+    def lv(i):
+        if i not in level:
+            c = cur[i]
+            level[i] = 0 if c.op == "EXT" else 1 + max(lv(k) for k in c.children)
+        return level[i]
+    
+    nterm = len(D.terms)
+    chunks = [list(range(i, min(i + chunk, nterm))) for i in range(0, nterm, chunk)]
+    need = [_closure(D, ti) for ti in range(nterm)]
+    last_chunk = {ROOT: len(chunks) - 1}
+    for ci, ch in enumerate(chunks):
+        for ti in ch:
+            for x in need[ti]:
+                last_chunk[x] = ci
+    A = _Allocator()
+    offset = {}
+    row_of = {}
+    ops, flows, items, steps = [], [], [], []
+    done = set()
+    live = set()
+    for ci, ch in enumerate(chunks):
+        want = set().union(*[need[ti] for ti in ch]) - done
+        if ci == 0:
+            want.add(ROOT)
+        for x in sorted(want, key=lambda i: (lv(i), i)):
+            offset[x] = A.alloc(B.blocksize(x))
+            live.add(x)
+        for x in sorted(want, key=lambda i: (lv(i), i)):
+            row_of[x] = len(ops)
+            ops.append(B.current_row(x, offset))
+        bylev = {}
+        for x in want:
+            bylev.setdefault(lv(x), []).append(x)
+        if bylev:
+            lo, hi = min(bylev), max(bylev)
+            waves = [[(row_of[x], 255) for x in sorted(bylev.get(lo, []))]]
+            for l in range(lo, hi + 1):
+                w = []
+                for x in sorted(bylev.get(l, []), key=lambda i: (cur[i].op, i)):
+                    w += [(row_of[x], v) for v in range(B.nvar(x))]
+                w += [(row_of[x], 255) for x in sorted(bylev.get(l + 1, []))]
+                waves.append(w)
+            for w in waves:
+                if w:
+                    steps.append((0, len(items), len(w)))
+                    items.extend((r << 8) | v for r, v in w)
+        done |= want
+        first = len(ops)
+        for ti in ch:
+            ops.append(B.amp_row(ti, offset, flows))
+        steps.append((1, first, len(ch)))
+        for x in list(live):
+            if last_chunk[x] == ci:
+                A.release(offset[x], B.blocksize(x))
+                live.discard(x)
+    return ops, flows, items, steps, A.top
+
+
+def build_program(process, smem_budget=SMEM_STORE_BUDGET):
+    lhs, rhs = process.split(">")
+    inc, out = lhs.split(), rhs.split()
+    D = Diagrams(inc, out)
+    npar = D.npar
+    B = _Builder(D)
+    ops, flows, top = _dfs_schedule(B)
+    counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, bil=0, amp=0, amp_flows=0,
+                  var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0)
+    name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
+            OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil"}
+    for op in ops:
+        k = name[op[0]]
+        counts[k] += 1
+        if op[0] == OP_AMP:
+            counts["amp_flows"] += op[12]
+        elif op[0] != OP_EXT:
+            counts["var_" + k] += 1 << bin(op[5]).count("1")
+    # CTA schedule: largest chunk whose store fits the shared-memory budget
+    cta = None
+    nterm = len(D.terms)
+    for chunk in sorted({min(nterm, c) for c in (8, 16, 24, 32, 48, 64, 96, 128, 192, 256, nterm)}, reverse=True):
+        res = _wave_schedule(B, chunk)   # same builder: coupling/mass indices shared
+        if res[4] * 8 <= smem_budget:
+            cta = dict(zip(("ops", "flows", "items", "steps", "store"), res), chunk=chunk)
+            break
     perms = _perms(D)
     C = colour_matrix(perms) if D.gluons or any(abs(sm.colour(f)) == 3 for f in D.flav_in) else [[Fraction(1)]]
     ncol_in = 1
@@ -257,10 +378,12 @@ def build_program(process):
     ident = 1
     for p in set(out):
         ident *= math.factorial(out.count(p))
-    return Program(process=" ".join(inc) + " > " + " ".join(out), npar=npar, nin=D.nin, root=D.root,
-                   ops=ops, flows=flows, perms=perms, colour=C, couplings=couplings, masses=masses,
-                   ext_mass=ext_mass, ws_current_doubles=top, ndiagrams=D.ndiagrams, nterms=len(D.terms),
+    prog = Program(process=" ".join(inc) + " > " + " ".join(out), npar=npar, nin=D.nin, root=D.root,
+                   ops=ops, flows=flows, perms=perms, colour=C, couplings=B.couplings, masses=B.masses,
+                   ext_mass=B.ext_mass, ws_current_doubles=top, ndiagrams=D.ndiagrams, nterms=len(D.terms),
                    average_den=4 * ncol_in * ident, flop_counts=counts)
+    prog.cta = cta
+    return prog
 
 
 def _perms(D):
