@@ -21,6 +21,8 @@ struct mgx_program_desc {
   const int32_t* ops;
   int nflows;
   const int32_t* flows;
+  int nterms_tab;
+  const int32_t* terms;  // 8 ints per diagram term of the AMP groups
   int ncol;
   const double* colour;
   int ncoupl;
@@ -29,12 +31,14 @@ struct mgx_program_desc {
   const int32_t* mass;   // (mass param, width param) per entry
   const int32_t* extmass;
   int ws_doubles, ndiag, nterm, avg_den;
-  int counts[9];         // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil; current ops; amp ops; amp flows
+  int counts[10];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil; current ops; amp terms; amp flows; amp groups
   struct {
     int nops;
     const int32_t* ops;
     int nflows;
     const int32_t* flows;
+    int nterms;
+    const int32_t* terms;
     int nitems;
     const int32_t* items;  // (op row << 8) | variant, variant 255 = header
     int nsteps;
@@ -154,11 +158,11 @@ __global__ void __launch_bounds__(kThreads)
     for (int iop = 0; iop < P.nops; ++iop) {
       const Op o = load_op(P.ops, iop);
       if (o.code == OP_AMP) {
-        const int2* fl = P.flows + o.aux;
+        const int2* fl = P.flows + o.cpl;
         for (int ih = 0; ih < P.ngood; ++ih) {
-          const cx amp = amp_value(o, P.good[ih], W);
+          const cx amp = group_amp(P.terms, o, P.good[ih], W);
           const int jb = P.jamp_off + 2 * P.ncol * ih;
-          for (int f = 0; f < o.aux2; ++f) {
+          for (int f = 0; f < o.mass; ++f) {
             const int2 q = __ldg(fl + f);
             add_phase(W[jb + 2 * q.x], W[jb + 2 * q.x + 1], q.y, amp);
           }
@@ -199,26 +203,35 @@ __global__ void __launch_bounds__(kThreads)
 struct CtaTab {
   const int4* ops;
   const int2* flows;
+  const int4* terms;
   const int* items;
   const int3* steps;
   int nsteps, store;
 };
 
-template <int T>
-__global__ void __launch_bounds__(T)
+constexpr int kCtaThreads = 128;
+
+// Threads are (term lane g, helicity slot hl): hl = t % ngp, g = t / ngp, ngp the good-helicity
+// count rounded up to 32.  In an amplitude step lane g closes groups g, g+G, ... for helicity hl;
+// lanes > 0 hand their partial jamps to lane 0 through shared memory at the end.
+__global__ void __launch_bounds__(kCtaThreads)
     me_cta_kernel(const KParams P, const CtaTab C, int64_t nevt, const double* __restrict__ mom,
                   const double* __restrict__ alphas, const double* __restrict__ rhel,
                   const double* __restrict__ rcol, double* __restrict__ me, int32_t* __restrict__ selhel,
                   int32_t* __restrict__ selcol, double* __restrict__ mh_out, double* __restrict__ colw_out,
                   int mode) {
+  constexpr int T = kCtaThreads;
   extern __shared__ double sm[];
   double* store = sm;
   double* pe = sm + C.store;
   const SS W{store};
   const int tid = threadIdx.x;
   const int npar4 = 4 * P.npar;
-  const bool act = tid < P.ngood;
-  const int h = act ? P.good[tid] : 0;
+  const int ngp = P.ngood <= 32 ? 32 : (P.ngood <= 64 ? 64 : 128);
+  const int G = T / ngp;
+  const int hl = tid % ngp, g = tid / ngp;
+  const bool act = hl < P.ngood;
+  const int h = act ? P.good[hl] : 0;
   const int ncol = P.ncol;
   for (int64_t e = blockIdx.x; e < nevt; e += gridDim.x) {
     for (int i = tid; i < npar4; i += T) pe[i] = __ldg(mom + e * npar4 + i);
@@ -238,11 +251,11 @@ __global__ void __launch_bounds__(T)
           else op_variant(P, o, v, gs, pe, W);
         }
       } else if (act) {
-        for (int a = st.y; a < st.y + st.z; ++a) {
+        for (int a = st.y + g; a < st.y + st.z; a += G) {
           const Op o = load_op(C.ops, a);
-          const cx amp = amp_value(o, h, W);
-          const int2* fl = C.flows + o.aux;
-          for (int f = 0; f < o.aux2; ++f) {
+          const cx amp = group_amp(C.terms, o, h, W);
+          const int2* fl = C.flows + o.cpl;
+          for (int f = 0; f < o.mass; ++f) {
             const int2 q = __ldg(fl + f);
             add_phase(J[2 * q.x], J[2 * q.x + 1], q.y, amp);
           }
@@ -250,15 +263,23 @@ __global__ void __launch_bounds__(T)
       }
       __syncthreads();
     }
-    // the store is dead now: reuse it for per-helicity results
+    // the store is dead now: partial jamps of lanes > 0, then per-helicity results
+    double* part = store;                               // [G-1][ngood][2 ncol]
+    if (act && g > 0)
+      for (int k = 0; k < 2 * ncol; ++k) part[((g - 1) * P.ngood + hl) * 2 * ncol + k] = J[k];
+    __syncthreads();
+    if (act && g == 0)
+      for (int gg = 1; gg < G; ++gg)
+        for (int k = 0; k < 2 * ncol; ++k) J[k] += part[((gg - 1) * P.ngood + hl) * 2 * ncol + k];
+    __syncthreads();
     double* mh_s = store;
     double* cwh_s = store + P.ngood;           // [ngood][ncol] |J_i(h)|^2
     double* colw_s = cwh_s + P.ngood * ncol;
-    if (act) {
+    if (act && g == 0) {
       const double mh = quad_form([&](int k) { return J[k]; }, P.colsym, P.colsym_f, ncol, mode);
-      mh_s[tid] = mh;
-      if (mh_out) mh_out[e * P.ngood + tid] = mh;
-      for (int i = 0; i < ncol; ++i) cwh_s[tid * ncol + i] = fma(J[2 * i], J[2 * i], J[2 * i + 1] * J[2 * i + 1]);
+      mh_s[hl] = mh;
+      if (mh_out) mh_out[e * P.ngood + hl] = mh;
+      for (int i = 0; i < ncol; ++i) cwh_s[hl * ncol + i] = fma(J[2 * i], J[2 * i], J[2 * i + 1] * J[2 * i + 1]);
     }
     __syncthreads();
     for (int i = tid; i < ncol; i += T) {
@@ -393,8 +414,10 @@ struct mgx_process {
   int2* d_flows = nullptr;
   double* d_col = nullptr;
   float* d_colf = nullptr;
+  int4* d_terms = nullptr;
   int4* d_cta_ops = nullptr;
   int2* d_cta_flows = nullptr;
+  int4* d_cta_terms = nullptr;
   int* d_cta_items = nullptr;
   int3* d_cta_steps = nullptr;
   int blocks_per_sm = 4;      // thread-per-event kernel
@@ -428,24 +451,27 @@ bool use_cta(const mgx_process* pr, const KParams& kp) {
 }
 
 size_t cta_smem_bytes(const mgx_process* pr, const KParams& kp) {
+  const int ngp = kp.ngood <= 32 ? 32 : (kp.ngood <= 64 ? 64 : 128);
+  const int G = kCtaThreads / ngp;
+  const int partials = (G - 1) * kp.ngood * 2 * kp.ncol;
   const int results = kp.ngood + kp.ngood * kp.ncol + kp.ncol;
-  return (size_t)(std::max(pr->prog->cta.store, results) + 4 * kp.npar) * sizeof(double);
+  return (size_t)(std::max({pr->prog->cta.store, results, partials}) + 4 * kp.npar) * sizeof(double);
 }
 
-template <int T>
 int launch_cta(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
                const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
                int mode, cudaStream_t st) {
   const size_t smem = cta_smem_bytes(pr, kp);
-  if (cudaFuncSetAttribute(me_cta_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(me_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return MGX_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_cta_kernel<T>, T, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, me_cta_kernel, kCtaThreads, smem) != cudaSuccess ||
+      per_sm < 1)
     return MGX_ERR_CUDA;
   const int64_t blocks = std::min<int64_t>(nevt, (int64_t)per_sm * sm_count(pr->device));
-  CtaTab C{pr->d_cta_ops, pr->d_cta_flows, pr->d_cta_items, pr->d_cta_steps, pr->prog->cta.nsteps,
-           pr->prog->cta.store};
-  me_cta_kernel<T><<<(unsigned)blocks, T, smem, st>>>(kp, C, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode);
+  CtaTab C{pr->d_cta_ops, pr->d_cta_flows, pr->d_cta_terms, pr->d_cta_items, pr->d_cta_steps,
+           pr->prog->cta.nsteps, pr->prog->cta.store};
+  me_cta_kernel<<<(unsigned)blocks, kCtaThreads, smem, st>>>(kp, C, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
@@ -453,11 +479,7 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
            const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
            int mode, void* ws, size_t wsb, cudaStream_t st) {
   if (nevt == 0) return MGX_OK;
-  if (use_cta(pr, kp)) {
-    if (kp.ngood <= 32) return launch_cta<32>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
-    if (kp.ngood <= 64) return launch_cta<64>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
-    return launch_cta<128>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
-  }
+  if (use_cta(pr, kp)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
   const int64_t nt = grid_threads(pr, nevt);
   const size_t need = (size_t)nt * ws_doubles_per_thread(kp) * sizeof(double);
   if (wsb < need || ws == nullptr) return MGX_ERR_WORKSPACE_TOO_SMALL;
@@ -510,8 +532,10 @@ void mgx_process_destroy(mgx_process* pr) {
   cudaFree(pr->d_flows);
   cudaFree(pr->d_col);
   cudaFree(pr->d_colf);
+  cudaFree(pr->d_terms);
   cudaFree(pr->d_cta_ops);
   cudaFree(pr->d_cta_flows);
+  cudaFree(pr->d_cta_terms);
   cudaFree(pr->d_cta_items);
   cudaFree(pr->d_cta_steps);
   cudaSetDevice(cur);
@@ -582,7 +606,9 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
       cs[(size_t)i * n + j] = v;
       csf[(size_t)i * n + j] = (float)v;
     }
-  bool ok = cudaMalloc(&pr->d_ops, sizeof(int32_t) * 16 * prog->nops) == cudaSuccess &&
+  bool ok = cudaMalloc(&pr->d_terms, sizeof(int4) * 2 * std::max(1, prog->nterms_tab)) == cudaSuccess &&
+            cudaMemcpy(pr->d_terms, prog->terms, sizeof(int4) * 2 * prog->nterms_tab, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMalloc(&pr->d_ops, sizeof(int32_t) * 16 * prog->nops) == cudaSuccess &&
             cudaMalloc(&pr->d_flows, sizeof(int2) * std::max(1, prog->nflows)) == cudaSuccess &&
             cudaMalloc(&pr->d_col, sizeof(double) * n * n) == cudaSuccess &&
             cudaMalloc(&pr->d_colf, sizeof(float) * n * n) == cudaSuccess;
@@ -594,10 +620,12 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
   if (ok && ct.nops > 0) {
     ok = cudaMalloc(&pr->d_cta_ops, sizeof(int32_t) * 16 * ct.nops) == cudaSuccess &&
          cudaMalloc(&pr->d_cta_flows, sizeof(int2) * std::max(1, ct.nflows)) == cudaSuccess &&
+         cudaMalloc(&pr->d_cta_terms, sizeof(int4) * 2 * std::max(1, ct.nterms)) == cudaSuccess &&
          cudaMalloc(&pr->d_cta_items, sizeof(int) * std::max(1, ct.nitems)) == cudaSuccess &&
          cudaMalloc(&pr->d_cta_steps, sizeof(int3) * std::max(1, ct.nsteps)) == cudaSuccess;
     ok = ok && cudaMemcpy(pr->d_cta_ops, ct.ops, sizeof(int32_t) * 16 * ct.nops, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(pr->d_cta_flows, ct.flows, sizeof(int32_t) * 2 * ct.nflows, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(pr->d_cta_terms, ct.terms, sizeof(int4) * 2 * ct.nterms, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(pr->d_cta_items, ct.items, sizeof(int) * ct.nitems, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(pr->d_cta_steps, ct.steps, sizeof(int3) * ct.nsteps, cudaMemcpyHostToDevice) == cudaSuccess;
   }
@@ -608,6 +636,7 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
   }
   kp.ops = pr->d_ops;
   kp.flows = pr->d_flows;
+  kp.terms = pr->d_terms;
   kp.colsym = pr->d_col;
   kp.colsym_f = pr->d_colf;
 
@@ -789,7 +818,7 @@ double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) {
   const double ngood = (double)pr->good.size();
   const int n = pr->prog->ncol;
   double ops = 92.0 * c[0] + 92.0 * c[1] + 56.0 * c[2] + 66.0 * c[3] + 52.0 * c[4] + 48.0 * c[5];
-  ops += ngood * (16.0 * c[7] + 2.0 * c[8]);
+  ops += ngood * (18.0 * c[7] + 2.0 * c[8]);   // per term: Q.V (16) + phased add (2); per flow: 2
   ops += ngood * (mode == MGX_FP64 ? (2.0 * n * (n + 1) + 2.0) : 2.0 * n);  // quadratic form / conversions
   ops += ngood * 2.0 * n;                                                  // colour weights
   return ops;

@@ -32,6 +32,7 @@ constexpr int MAXNPAR = 8;
 struct KParams {
   const int4* ops;       // 4 int4 (16 int32 fields) per op
   const int2* flows;     // (colour flow, phase code 0..3 for 1, i, -1, -i)
+  const int4* terms;     // 2 int4 per diagram term: (Q base, Q mask, V base, V mask), (phase, -, -, -)
   const double* colsym;  // ncol*ncol: C_ii on the diagonal, 2 C_ij above it
   const float* colsym_f;
   int nops, ncol, npar, nin, ngood;

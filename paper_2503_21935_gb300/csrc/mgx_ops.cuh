@@ -310,18 +310,7 @@ __device__ inline void op_variant(const KParams& P, const Op& o, int v, double g
   }
 }
 
-// ================================================================ diagram amplitude
-// amp(h) = Q(h_root, h_col) . V(h_vec): the root bilinear Q^mu = psibar gamma^mu (cL PL + cR PR) psi
-// (couplings included) contracted with the term's vector current
-template <class S>
-__device__ __forceinline__ cx amp_value(const Op& o, int h, const S& W) {
-  cx Q[4], V[4];
-  W.load4(o.va + 8 * pext(h, o.ma), Q);
-  W.load4(o.vb + 8 * pext(h, o.mb), V);
-  return mdot(Q, V);
-}
-
-// add phase(code) * amp to a jamp held as (re, im)
+// add phase(code) * a to (re, im)
 __device__ __forceinline__ void add_phase(double& jr, double& ji, int code, cx a) {
   switch (code) {
     case 0: jr += a.r; ji += a.i; break;   // +1
@@ -329,6 +318,25 @@ __device__ __forceinline__ void add_phase(double& jr, double& ji, int code, cx a
     case 2: jr -= a.r; ji -= a.i; break;   // -1
     default: jr += a.i; ji -= a.r; break;  // -i
   }
+}
+
+// ================================================================ diagram amplitudes
+// A group of diagram terms sharing one colour vector (up to a phase): sum over the group of
+// phase_t * Q_t(h) . V_t(h), where Q_t is the root bilinear psibar gamma^mu (cL PL + cR PR) psi
+// of the term's column current (couplings included) and V_t its vector current.
+// AMP op fields: aux = first term, aux2 = terms, cpl = first flow, mass = flows.
+template <class S>
+__device__ __forceinline__ cx group_amp(const int4* terms, const Op& o, int h, const S& W) {
+  cx acc{0.0, 0.0};
+  for (int t = 0; t < o.aux2; ++t) {
+    const int4 a = __ldg(terms + 2 * (o.aux + t));
+    const int ph = __ldg(terms + 2 * (o.aux + t) + 1).x;
+    cx Q[4], V[4];
+    W.load4(a.x + 8 * pext(h, a.y), Q);
+    W.load4(a.z + 8 * pext(h, a.w), V);
+    add_phase(acc.r, acc.i, ph, mdot(Q, V));
+  }
+  return acc;
 }
 
 }  // namespace mgx

@@ -35,6 +35,7 @@ def emit(path):
         pre = f"mgx_p{k}"
         out.append(_arr("int32_t", pre + "_ops", (str(x) for op in P.ops for x in op)))
         out.append(_arr("int32_t", pre + "_flows", (str(x) for x in P.flows)))
+        out.append(_arr("int32_t", pre + "_terms", (str(x) for x in P.terms)))
         out.append(_arr("double", pre + "_colour",
                         (repr(float(x)) for row in P.colour for x in row), per_line=8))
         spec = []
@@ -51,20 +52,22 @@ def emit(path):
         if cta is not None:
             out.append(_arr("int32_t", pre + "_cta_ops", (str(x) for op in cta["ops"] for x in op)))
             out.append(_arr("int32_t", pre + "_cta_flows", (str(x) for x in cta["flows"])))
+            out.append(_arr("int32_t", pre + "_cta_terms", (str(x) for x in cta["terms"])))
             out.append(_arr("int32_t", pre + "_cta_items", (str(x) for x in cta["items"])))
             out.append(_arr("int32_t", pre + "_cta_steps", (str(x) for st in cta["steps"] for x in st)))
             cta_init = (f'{{{len(cta["ops"])}, {pre}_cta_ops, {len(cta["flows"]) // 2}, {pre}_cta_flows, '
+                        f'{len(cta["terms"]) // 8}, {pre}_cta_terms, '
                         f'{len(cta["items"])}, {pre}_cta_items, {len(cta["steps"])}, {pre}_cta_steps, '
                         f'{cta["store"]}, {cta["chunk"]}}}')
         else:
-            cta_init = "{0, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, 0}"
+            cta_init = "{0, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, 0}"
         entries.append(
             f'  {{"{P.process}", {P.npar}, {P.nin}, {P.root}, {len(P.ops)}, {pre}_ops, '
-            f'{len(P.flows) // 2}, {pre}_flows, {P.ncol}, {pre}_colour, {len(P.couplings)}, {pre}_coupl, '
+            f'{len(P.flows) // 2}, {pre}_flows, {len(P.terms) // 8}, {pre}_terms, {P.ncol}, {pre}_colour, {len(P.couplings)}, {pre}_coupl, '
             f'{len(P.masses)}, {pre}_mass, {pre}_extmass, {P.ws_current_doubles}, {P.ndiagrams}, '
             f'{P.nterms}, {P.average_den}, '
             f'{{{c["var_ffv_f"]}, {c["var_ffv_fb"]}, {c["var_ffv_v"]}, {c["var_vvv"]}, {c["var_vvvv"]}, {c["var_bil"]}, '
-            f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"] + c["bil"]}, {c["amp"]}, {c["amp_flows"]}}}, '
+            f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"] + c["bil"]}, {c["amp_terms"]}, {c["amp_flows"]}, {c["amp"]}}}, '
             f'{cta_init}}},')
     out.append("static const mgx_program_desc mgx_programs[] = {\n" + "\n".join(entries) + "\n};\n")
     out.append(f"static const int mgx_num_programs = {len(BUILTIN)};\n")

@@ -39,7 +39,8 @@ class Program:
     nin: int
     root: int
     ops: list
-    flows: list                 # flattened (flow, phase code) pairs
+    flows: list                 # flattened (flow, phase code) pairs of the AMP groups
+    terms: list                 # flattened 8-int term entries of the AMP groups
     perms: list
     colour: list                # exact Fractions
     couplings: list             # (kind, fermion) specs resolved at process creation
@@ -61,7 +62,7 @@ def _bit(npar, leg):
 
 
 HEADER = {"EXT": 4, "FFV_F": 6, "FFV_FB": 6, "FFV_V": 6, "VVV": 18, "VVVV": 6, "BIL": 6}
-SMEM_STORE_BUDGET = 64 * 1024     # bytes of shared memory for one event's current store
+SMEM_STORE_BUDGET = 96 * 1024     # bytes of shared memory for one event's current store
 
 
 class _Allocator:
@@ -197,26 +198,57 @@ class _Builder:
             raise ValueError(c.op)
         return op
 
-    def amp_row(self, ti, offset, flows):
+    def amp_row(self, group, offset, flows, terms):
+        """One AMP row per term group: term table entries (bil base, bil mask, vec base, vec mask,
+        phase, 0, 0, 0) and the group's (flow, phase) list."""
         D = self.D
-        t = D.terms[ti]
-        bil, vec = D.currents[t.bil], D.currents[t.vec]
+        tis, phases, fl = group
         op = [0] * NFIELD
         op[0] = OP_AMP
-        op[2], op[3] = offset[t.bil], offset[t.vec]
-        op[6], op[7] = self.hmask(bil.mask), self.hmask(vec.mask)
-        op[13], op[14] = self.varbase(t.bil, offset), self.varbase(t.vec, offset)
-        op[11] = len(flows) // 2
-        nf = 0
-        for word, coeff in sorted(t.colour.items()):
-            full = complex(coeff) * (-1j)          # M = -i * (diagram value)
-            key = complex(round(full.real), round(full.imag))
-            if abs(full - key) > 1e-12 or key not in _PHASE:
-                raise ValueError(f"unexpected colour coefficient {coeff}")
-            flows += [D_perm_index(D, word), _PHASE[key]]
-            nf += 1
-        op[12] = nf
+        op[11] = len(terms) // 8
+        op[12] = len(tis)
+        for ti, ph in zip(tis, phases):
+            t = D.terms[ti]
+            bil, vec = D.currents[t.bil], D.currents[t.vec]
+            terms += [self.varbase(t.bil, offset), self.hmask(bil.mask), self.varbase(t.vec, offset),
+                      self.hmask(vec.mask), ph, 0, 0, 0]
+        op[9] = len(flows) // 2
+        op[10] = len(fl)
+        for f, ph in fl:
+            flows += [f, ph]
         return op
+
+
+def _term_groups(D):
+    """Group diagram terms whose colour vectors agree up to a phase in {1, i, -1, -i}: a group's
+    terms are summed with their phases first and the sum is added to the flows once.
+    Returns [(terms, [(phase code per term)], [(flow, phase code)])] in first-occurrence order."""
+    groups = {}
+    order = []
+    for ti, t in enumerate(D.terms):
+        items = sorted(t.colour.items())
+        c0 = complex(items[0][1])
+        key = tuple((w, complex(c) / c0) for w, c in items)
+        if key not in groups:
+            groups[key] = []
+            order.append(key)
+        groups[key].append((ti, c0 * (-1j)))          # M = -i * (diagram value)
+    out = []
+    for key in order:
+        phases = []
+        for ti, ph in groups[key]:
+            k = complex(round(ph.real), round(ph.imag))
+            if abs(ph - k) > 1e-12 or k not in _PHASE:
+                raise ValueError(f"unexpected colour coefficient {ph}")
+            phases.append(_PHASE[k])
+        fl = []
+        for w, r in key:
+            k = complex(round(r.real), round(r.imag))
+            if abs(r - k) > 1e-12 or k not in _PHASE:
+                raise ValueError(f"unexpected colour ratio {r}")
+            fl.append((D_perm_index(D, w), _PHASE[k]))
+        out.append(([ti for ti, _ in groups[key]], phases, fl))
+    return out
 
 
 def _closure(D, ti):
@@ -246,35 +278,39 @@ def _dfs_schedule(B):
             emit(k)
         done.add(i)
         order.append(("C", i))
-    for ti, t in enumerate(D.terms):
-        emit(t.bil)
-        emit(t.vec)
-        order.append(("A", ti))
+    groups = _term_groups(D)
+    for gi, (tis, _, _) in enumerate(groups):
+        for ti in tis:
+            emit(D.terms[ti].bil)
+            emit(D.terms[ti].vec)
+        order.append(("A", gi))
 
     def uses(item):
         kind, x = item
         if kind == "C":
             return list(cur[x].children)
-        t = D.terms[x]
-        return [t.bil, t.vec]
+        out = []
+        for ti in groups[x][0]:
+            out += [D.terms[ti].bil, D.terms[ti].vec]
+        return out
     last = {}
     for pos, item in enumerate(order):
         for u in uses(item):
             last[u] = pos
     A = _Allocator()
     offset = {}
-    ops, flows = [], []
+    ops, flows, terms = [], [], []
     for pos, item in enumerate(order):
         kind, x = item
         if kind == "C":
             offset[x] = A.alloc(B.blocksize(x))
             ops.append(B.current_row(x, offset))
         else:
-            ops.append(B.amp_row(x, offset, flows))
+            ops.append(B.amp_row(groups[x], offset, flows, terms))
         for u in set(uses(item)):
             if last[u] == pos:
                 A.release(offset[u], B.blocksize(u))
-    return ops, flows, A.top
+    return ops, flows, terms, A.top
 
 
 def _wave_schedule(B, chunk):
@@ -292,22 +328,31 @@ def _wave_schedule(B, chunk):
             level[i] = 0 if c.op == "EXT" else 1 + max(lv(k) for k in c.children)
         return level[i]
     
-    nterm = len(D.terms)
-    chunks = [list(range(i, min(i + chunk, nterm))) for i in range(0, nterm, chunk)]
-    need = [_closure(D, ti) for ti in range(nterm)]
+    groups = _term_groups(D)
+    chunks = []                       # lists of group indices holding about `chunk` terms
+    cur_chunk, nt = [], 0
+    for gi, g in enumerate(groups):
+        cur_chunk.append(gi)
+        nt += len(g[0])
+        if nt >= chunk:
+            chunks.append(cur_chunk)
+            cur_chunk, nt = [], 0
+    if cur_chunk:
+        chunks.append(cur_chunk)
+    gneed = [set().union(*[_closure(D, ti) for ti in g[0]]) for g in groups]
     last_chunk = {ROOT: len(chunks) - 1}
     for ci, ch in enumerate(chunks):
-        for ti in ch:
-            for x in need[ti]:
+        for gi in ch:
+            for x in gneed[gi]:
                 last_chunk[x] = ci
     A = _Allocator()
     offset = {}
     row_of = {}
-    ops, flows, items, steps = [], [], [], []
+    ops, flows, items, steps, terms = [], [], [], [], []
     done = set()
     live = set()
     for ci, ch in enumerate(chunks):
-        want = set().union(*[need[ti] for ti in ch]) - done
+        want = set().union(*[gneed[gi] for gi in ch]) - done
         if ci == 0:
             want.add(ROOT)
         for x in sorted(want, key=lambda i: (lv(i), i)):
@@ -334,14 +379,14 @@ def _wave_schedule(B, chunk):
                     items.extend((r << 8) | v for r, v in w)
         done |= want
         first = len(ops)
-        for ti in ch:
-            ops.append(B.amp_row(ti, offset, flows))
+        for gi in ch:
+            ops.append(B.amp_row(groups[gi], offset, flows, terms))
         steps.append((1, first, len(ch)))
         for x in list(live):
             if last_chunk[x] == ci:
                 A.release(offset[x], B.blocksize(x))
                 live.discard(x)
-    return ops, flows, items, steps, A.top
+    return ops, flows, terms, items, steps, A.top
 
 
 def build_program(process, smem_budget=SMEM_STORE_BUDGET):
@@ -350,7 +395,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     D = Diagrams(inc, out)
     npar = D.npar
     B = _Builder(D)
-    ops, flows, top = _dfs_schedule(B)
+    ops, flows, terms, top = _dfs_schedule(B)
     counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, bil=0, amp=0, amp_flows=0,
                   var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0)
     name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
@@ -359,7 +404,8 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
         k = name[op[0]]
         counts[k] += 1
         if op[0] == OP_AMP:
-            counts["amp_flows"] += op[12]
+            counts["amp_flows"] += op[10]
+            counts["amp_terms"] = counts.get("amp_terms", 0) + op[12]
         elif op[0] != OP_EXT:
             counts["var_" + k] += 1 << bin(op[5]).count("1")
     # CTA schedule: largest chunk whose store fits the shared-memory budget
@@ -367,8 +413,8 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     nterm = len(D.terms)
     for chunk in sorted({min(nterm, c) for c in (8, 16, 24, 32, 48, 64, 96, 128, 192, 256, nterm)}, reverse=True):
         res = _wave_schedule(B, chunk)   # same builder: coupling/mass indices shared
-        if res[4] * 8 <= smem_budget:
-            cta = dict(zip(("ops", "flows", "items", "steps", "store"), res), chunk=chunk)
+        if res[5] * 8 <= smem_budget:
+            cta = dict(zip(("ops", "flows", "terms", "items", "steps", "store"), res), chunk=chunk)
             break
     perms = _perms(D)
     C = colour_matrix(perms) if D.gluons or any(abs(sm.colour(f)) == 3 for f in D.flav_in) else [[Fraction(1)]]
@@ -379,7 +425,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     for p in set(out):
         ident *= math.factorial(out.count(p))
     prog = Program(process=" ".join(inc) + " > " + " ".join(out), npar=npar, nin=D.nin, root=D.root,
-                   ops=ops, flows=flows, perms=perms, colour=C, couplings=B.couplings, masses=B.masses,
+                   ops=ops, flows=flows, terms=terms, perms=perms, colour=C, couplings=B.couplings, masses=B.masses,
                    ext_mass=B.ext_mass, ws_current_doubles=top, ndiagrams=D.ndiagrams, nterms=len(D.terms),
                    average_den=4 * ncol_in * ident, flop_counts=counts)
     prog.cta = cta
