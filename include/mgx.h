@@ -157,6 +157,28 @@ int mgx_process_set_blocks_per_sm(mgx_process* proc, int blocks_per_sm);
  * (used for roofline reporting). */
 double mgx_fp64_ops_per_event(const mgx_process* proc, int mode);
 
+/* Allocation-free variant of mgx_compute.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory where they evaluate matrix elements,
+ * e.g. a Fortran event-generation loop with no CUDA allocator of its own, or a plugin inside a
+ * host framework that owns the device memory pool and forbids cudaMalloc from third-party code.
+ * Arguments are those of mgx_compute without the workspace (DEVICE pointers; the caller still
+ * passes every input and output).  The thread-per-event kernel's workspace lives in one fixed
+ * module-scope device array of mgx_noalloc_scratch_bytes() = 128 MiB, which every GPU that
+ * loads the library holds until the process exits; the grid is sized so the workspace fits.
+ * The call itself allocates nothing (no cudaMalloc/cudaFree, no allocating library call); the
+ * process handle must have been created beforehand.  Set-up: the first call on a device looks
+ * up the array's device address with that device current, so make that first call before any
+ * stream capture.  The kernel initialises everything it reads (including the jamp
+ * accumulators) for every event, so no clearing is needed between calls; but every call shares
+ * the one array, so calls whose kernels overlap on the GPU (different streams, or several
+ * threads) race and must be serialised by the caller.  Errors: as mgx_compute, plus
+ * WORKSPACE_TOO_SMALL when one 128-thread block's workspace (128 x the process's per-event
+ * workspace) exceeds the array. */
+size_t mgx_noalloc_scratch_bytes(void);
+int mgx_compute_noalloc(mgx_process* proc, int64_t nevt, const double* momenta, const double* alpha_s,
+                        const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel,
+                        int32_t* selcol, int mode, void* stream);
+
 void mgx_process_destroy(mgx_process* proc);
 const char* mgx_status_string(int status);
 int mgx_version(void);

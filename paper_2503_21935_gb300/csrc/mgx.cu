@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cctype>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -822,6 +823,66 @@ double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) {
   ops += ngood * (mode == MGX_FP64 ? (2.0 * n * (n + 1) + 2.0) : 2.0 * n);  // quadratic form / conversions
   ops += ngood * 2.0 * n;                                                  // colour weights
   return ops;
+}
+
+// ------------------------------------------------------------------ allocation-free entry point
+// Some callers cannot allocate device memory at the point where they evaluate matrix elements:
+// a Fortran event-generation loop that links this library but has no CUDA allocator of its
+// own, or a plugin running inside a host framework that owns the device memory pool and does
+// not let third-party code call cudaMalloc.  For them mgx_compute_noalloc runs the
+// thread-per-event kernel with its workspace in this fixed array instead of a caller buffer.
+// The array is module-scope device memory: every GPU that loads the library holds it until the
+// process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)128 << 20;   // 128 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch, per device ordinal
+
+// Host code must not hand the array's name to a kernel (in host code it is a host-side
+// stand-in, not a device address): look the device address up once per device, with that
+// device current.
+static int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= 256) return MGX_ERR_INVALID_ARGUMENT;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return MGX_ERR_CUDA;
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = (double*)g_noalloc_ptr[device];
+  return MGX_OK;
+}
+
+extern "C" size_t mgx_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
+
+extern "C" int mgx_compute_noalloc(mgx_process* pr, int64_t nevt, const double* momenta, const double* alpha_s,
+                                   const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel,
+                                   int32_t* selcol, int mode, void* stream) {
+  if (!pr || nevt < 0) return MGX_ERR_INVALID_ARGUMENT;
+  if (mode != MGX_FP64 && mode != MGX_MIXED_FP32) return MGX_ERR_UNSUPPORTED_MODE;
+  if (nevt == 0) return MGX_OK;
+  if (!momenta || !alpha_s || !me) return MGX_ERR_INVALID_ARGUMENT;
+  if ((selhel && !rnd_hel) || (selcol && !rnd_col)) return MGX_ERR_INVALID_ARGUMENT;
+  if (reinterpret_cast<uintptr_t>(momenta) % 16 != 0) return MGX_ERR_INVALID_ARGUMENT;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return MGX_ERR_CUDA;
+  if (cur != pr->device) return MGX_ERR_DEVICE_MISMATCH;
+  // one 128-thread block needs 128 per-event workspaces; the grid is sized to fit the array
+  const size_t per_block = (size_t)kThreads * pr->kp.ws_doubles * sizeof(double);
+  if (per_block > kNoAllocScratchBytes) return MGX_ERR_WORKSPACE_TOO_SMALL;
+  double* scratch = nullptr;
+  const int rc = noalloc_scratch(cur, &scratch);
+  if (rc != MGX_OK) return rc;
+  const int64_t fit = (int64_t)(kNoAllocScratchBytes / per_block);
+  const int64_t want = (nevt + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)sm_count(pr->device) * pr->blocks_per_sm;
+  const int64_t blocks = std::max<int64_t>(1, std::min({fit, want, cap}));
+  const int64_t nt = blocks * kThreads;
+  const size_t shm = (size_t)kThreads * 4 * pr->kp.npar * sizeof(double);
+  me_kernel<<<(unsigned)blocks, kThreads, shm, (cudaStream_t)stream>>>(
+      pr->kp, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, scratch, nt, mode);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
 }  // extern "C"
