@@ -31,6 +31,7 @@ NEVT = 1 << 20
 METRIC = "gg->ttgg |M|^2 evals/s (FP64)"
 # FP64 pipe: 152 SMs x 2 DFMA/clk/SM (measured: 1.20 TFLOP/s at 1995 MHz) x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_PEAK_GINST = 152 * 2 * 2.070e9 / 1e9       # float64 instructions per second, any of fma/mul/add
 
 
 def _args():
@@ -211,10 +212,12 @@ def run_gpu(args):
         cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} events of the same workload ({per_core} per spawn process), {busy:.1f} s busy"}
 
+    from paper_2503_21935_gb300.dist import event_range, max_over_ranks
     wl = WORKLOADS[WORKLOAD]
     nevt = args.nevt
     mode = pkg.MODES[args.mode]
-    mom, a, rh, rc = make_inputs(wl, nevt, first=rank * nevt)     # each rank its own events
+    first, _ = event_range(rank, world, nevt)
+    mom, a, rh, rc = make_inputs(wl, nevt, first=first)          # each rank its own events
     dev = torch.device(f"cuda:{local}")
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
@@ -243,11 +246,7 @@ def run_gpu(args):
         barrier()
         wall = time.perf_counter() - t0
     launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_ms = sum(launch_ms)
-    if dist is not None:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(launch_ms), device=dev)
     ms_per_step = total_ms / args.steps
     value = world * nevt / (ms_per_step * 1e-3)
 
@@ -264,17 +263,15 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         proc.compute_host(hM, hA, hRH, hRC, hme, hsh, hsc, mode=mode, stream=stream)
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, device=dev)
     h2d = sum(x.numel() * x.element_size() for x in (hM, hA, hRH, hRC))
     d2h = sum(x.numel() * x.element_size() for x in (hme, hsh, hsc))
 
     if rank == 0:
-        flops = 2.0 * proc.fp64_ops_per_event(mode) * nevt     # algorithmic float64 flops per launch
-        achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
+        flops = proc.fp64_flops_per_event(mode) * nevt         # algorithmic float64 flops per launch
+        insts = proc.fp64_ops_per_event(mode) * nevt           # float64 instructions per launch
+        launch_s = statistics.mean(launch_ms) * 1e-3
+        achieved = flops / launch_s / 1e12
         per_evt = _traffic_per_event("me_kernel", WORKLOAD)
         line = {"metric": METRIC if args.mode == "fp64" else METRIC.replace("FP64", "mixed FP32 colour sum"),
                 "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -287,7 +284,11 @@ def run_gpu(args):
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP64_PEAK_TFLOPS,
                              "traffic": None if per_evt is None else per_evt * nevt,
-                             "kernel": "me_kernel", "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz"},
+                             "kernel": "me_kernel",
+                             "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz (all-fma peak)",
+                             "fp64_inst_per_s": insts / launch_s,
+                             "pipe_frac": insts / launch_s / 1e9 / FP64_PEAK_GINST,
+                             "flops_per_event": flops / nevt},
                 "e2e": {"value": world * nevt / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": args.steps,

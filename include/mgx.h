@@ -152,10 +152,12 @@ int mgx_process_get_kernel(const mgx_process* proc);        /* the kernel AUTO r
  * the workspace size grows with it. */
 int mgx_process_set_blocks_per_sm(mgx_process* proc, int blocks_per_sm);
 
-/* Number of float64 operations (add, multiply, fused multiply-add each one)
- * the amplitude stage executes per event for this process, from the op table
- * (used for roofline reporting). */
+/* Float64 work per event of this process in `mode`, from the op table and per-op
+ * instruction counts of the device code: instructions (add, multiply and fused
+ * multiply-add each one) and flops (a fused multiply-add counted as two).  Used for
+ * roofline reporting. */
 double mgx_fp64_ops_per_event(const mgx_process* proc, int mode);
+double mgx_fp64_flops_per_event(const mgx_process* proc, int mode);
 
 /* Allocation-free variant of mgx_compute.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory where they evaluate matrix elements,

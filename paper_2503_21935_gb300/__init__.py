@@ -55,6 +55,7 @@ def lib():
             "mgx_host_workspace_bytes": (I, [P, I64, I, ctypes.POINTER(SZ)]),
             "mgx_compute_host": (I, [P, I64, P, P, P, P, P, P, P, I, P, SZ, P]),
             "mgx_fp64_ops_per_event": (D, [P, I]),
+            "mgx_fp64_flops_per_event": (D, [P, I]),
             "mgx_process_set_kernel": (I, [P, I]),
             "mgx_process_get_kernel": (I, [P]),
             "mgx_process_set_blocks_per_sm": (I, [P, I]),
@@ -155,7 +156,12 @@ class Process:
         self._ws = {}
 
     def fp64_ops_per_event(self, mode=MGX_FP64):
+        """Float64 instructions per event (fma, mul, add one each)."""
         return lib().mgx_fp64_ops_per_event(self._h, mode)
+
+    def fp64_flops_per_event(self, mode=MGX_FP64):
+        """Float64 flops per event (fma counted as two)."""
+        return lib().mgx_fp64_flops_per_event(self._h, mode)
 
     def compute(self, momenta, alpha_s, rnd_hel=None, rnd_col=None, mode=MGX_FP64, mh=False, colw=False,
                 stream=None, out=None):

@@ -32,6 +32,7 @@ struct mgx_program_desc {
   const int32_t* mass;   // (mass param, width param) per entry
   const int32_t* extmass;
   int ws_doubles, ndiag, nterm, avg_den;
+  int gs_power;          // power of g_s of every amplitude (vertices are evaluated with g_s = 1)
   int counts[10];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil; current ops; amp terms; amp flows; amp groups
   struct {
     int nops;
@@ -61,6 +62,14 @@ namespace {
 constexpr int kThreads = 128;        // thread-per-event kernel
 constexpr int kMaxColCta = 32;       // jamps per helicity held by one thread in the CTA kernel
 constexpr int kMaxColFp32 = 120;     // colour flows of the largest built-in process
+
+// g_s^(2p) = (4 pi alpha_s)^p: every amplitude carries g_s^p, the vertices use g_s = 1
+__device__ __forceinline__ double coupling_scale(const KParams& P, double alpha_s) {
+  const double g2 = 4.0 * M_PI * alpha_s;
+  double s = 1.0;
+  for (int k = 0; k < P.gs_power; ++k) s *= g2;
+  return s;
+}
 
 // |M_h|^2 = J^dagger C J with C given as C_ii on the diagonal and 2 C_ij above it.
 template <class JV>
@@ -154,7 +163,8 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t e = base + threadIdx.x;
     if (e >= nevt) continue;
     const double* pe = smem + threadIdx.x * npar4;
-    const double gs = sqrt(4.0 * M_PI * alphas[e]);
+    const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
+    const double scale = coupling_scale(P, alphas[e]);
     for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = 0.0;
     for (int iop = 0; iop < P.nops; ++iop) {
       const Op o = load_op(P.ops, iop);
@@ -176,7 +186,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     for (int ih = 0; ih < P.ngood; ++ih) {
       const int jb = P.jamp_off + 2 * P.ncol * ih;
-      const double mh = quad_form([&](int k) { return W[jb + k]; }, P.colsym, P.colsym_f, P.ncol, mode);
+      const double mh = scale * quad_form([&](int k) { return W[jb + k]; }, P.colsym, P.colsym_f, P.ncol, mode);
       W[P.mh_off + ih] = mh;
       if (mh_out) mh_out[e * P.ngood + ih] = mh;
     }
@@ -187,6 +197,7 @@ __global__ void __launch_bounds__(kThreads)
           const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
           w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
         }
+        w *= scale;
         W[P.colw_off + i] = w;
         if (colw_out) colw_out[e * P.ncol + i] = w;
       }
@@ -237,7 +248,8 @@ __global__ void __launch_bounds__(kCtaThreads)
   for (int64_t e = blockIdx.x; e < nevt; e += gridDim.x) {
     for (int i = tid; i < npar4; i += T) pe[i] = __ldg(mom + e * npar4 + i);
     __syncthreads();
-    const double gs = sqrt(4.0 * M_PI * __ldg(alphas + e));
+    const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
+    const double scale = coupling_scale(P, __ldg(alphas + e));
     double J[2 * kMaxColCta];
 #pragma unroll
     for (int i = 0; i < 2 * kMaxColCta; ++i) J[i] = 0.0;
@@ -277,10 +289,11 @@ __global__ void __launch_bounds__(kCtaThreads)
     double* cwh_s = store + P.ngood;           // [ngood][ncol] |J_i(h)|^2
     double* colw_s = cwh_s + P.ngood * ncol;
     if (act && g == 0) {
-      const double mh = quad_form([&](int k) { return J[k]; }, P.colsym, P.colsym_f, ncol, mode);
+      const double mh = scale * quad_form([&](int k) { return J[k]; }, P.colsym, P.colsym_f, ncol, mode);
       mh_s[hl] = mh;
       if (mh_out) mh_out[e * P.ngood + hl] = mh;
-      for (int i = 0; i < ncol; ++i) cwh_s[hl * ncol + i] = fma(J[2 * i], J[2 * i], J[2 * i + 1] * J[2 * i + 1]);
+      for (int i = 0; i < ncol; ++i)
+        cwh_s[hl * ncol + i] = scale * fma(J[2 * i], J[2 * i], J[2 * i + 1] * J[2 * i + 1]);
     }
     __syncthreads();
     for (int i = tid; i < ncol; i += T) {
@@ -571,6 +584,7 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
   kp.npar = prog->npar;
   kp.nin = prog->nin;
   kp.avg = 1.0 / prog->avg_den;
+  kp.gs_power = prog->gs_power;
   // couplings
   const double e = std::sqrt(4.0 * M_PI * prm.alpha_em);
   const double mz2 = prm.mz * prm.mz;
@@ -811,19 +825,30 @@ int mgx_process_set_blocks_per_sm(mgx_process* pr, int blocks_per_sm) {
   return MGX_OK;
 }
 
-double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) {
-  if (!pr) return 0.0;
-  // float64 instructions per variant / per good helicity of each op kind, read off the
-  // device code in mgx_ops.cuh (fma, mul and add each count as one instruction)
+// Float64 work per event of the amplitude program, counted from the device code in
+// mgx_ops.cuh: (fma, mul, add) instructions per variant / per good helicity of each op kind.
+// Returns instructions (flops = false) or flops with an fma counted as 2 (flops = true).
+static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   const int* c = pr->prog->counts;
   const double ngood = (double)pr->good.size();
-  const int n = pr->prog->ncol;
-  double ops = 92.0 * c[0] + 92.0 * c[1] + 56.0 * c[2] + 66.0 * c[3] + 52.0 * c[4] + 48.0 * c[5];
-  ops += ngood * (18.0 * c[7] + 2.0 * c[8]);   // per term: Q.V (16) + phased add (2); per flow: 2
-  ops += ngood * (mode == MGX_FP64 ? (2.0 * n * (n + 1) + 2.0) : 2.0 * n);  // quadratic form / conversions
-  ops += ngood * 2.0 * n;                                                  // colour weights
-  return ops;
+  const double n = pr->prog->ncol;
+  struct K { double fma, mul, add; };
+  const K ffv_f{56, 24, 10}, ffv_v{24, 24, 24}, bil{16, 16, 24}, vvv{58, 14, 0}, vvvv{52, 16, 0},
+      term{14, 2, 2}, flow{0, 0, 2};
+  auto w = [&](const K& k) { return flops ? 2 * k.fma + k.mul + k.add : k.fma + k.mul + k.add; };
+  double t = w(ffv_f) * (c[0] + c[1]) + w(ffv_v) * c[2] + w(vvv) * c[3] + w(vvvv) * c[4] + w(bil) * c[5];
+  t += ngood * (w(term) * c[7] + w(flow) * c[8]);
+  if (mode == MGX_FP64) t += ngood * (flops ? 2 * n * n + 4 * n : n * n + 3 * n);  // quadratic form
+  else if (!flops) t += ngood * 2 * n;                                              // f64 -> f32 conversions
+  t += ngood * (flops ? 4 * n : 2 * n);                                             // colour weights
+  return t;
 }
+
+double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) { return pr ? fp64_work(pr, mode, false) : 0.0; }
+
+double mgx_fp64_flops_per_event(const mgx_process* pr, int mode) { return pr ? fp64_work(pr, mode, true) : 0.0; }
+
+}  // extern "C"
 
 // ------------------------------------------------------------------ allocation-free entry point
 // Some callers cannot allocate device memory at the point where they evaluate matrix elements:
@@ -885,4 +910,4 @@ extern "C" int mgx_compute_noalloc(mgx_process* pr, int64_t nevt, const double* 
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
-}  // extern "C"
+

@@ -38,6 +38,7 @@ struct KParams {
   int nops, ncol, npar, nin, ngood;
   int cur_doubles, jamp_off, mh_off, colw_off, ws_doubles;
   double avg;            // 1 / (4 Ncol_in S)
+  int gs_power;          // |M|^2 carries (4 pi alpha_s)^gs_power; vertices use g_s = 1
   double cpl[MAXCPL][4]; // cL.re cL.im cR.re cR.im
   int cplflags[MAXCPL];
   double mass[MAXMASS], width[MAXMASS];

@@ -94,12 +94,13 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
   }
   W.storek(o.dst, k);
   if (o.code == OP_VVV) {
-    W[o.dst + 4] = -gs / msq(k);  // prefactor -i g_s/P^2 = i * this
+    // prefactor -i g_s/P^2 = i s, s folded into the momentum combinations of the vertex
+    const double s = -gs / msq(k);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      W[o.dst + 6 + j] = ka[j] - kb[j];                 // k1 - k2
-      W[o.dst + 10 + j] = fma(2.0, kb[j], ka[j]);       // k2 - k3 = k1 + 2 k2
-      W[o.dst + 14 + j] = -fma(2.0, ka[j], kb[j]);      // k3 - k1 = -(2 k1 + k2)
+      W[o.dst + 6 + j] = s * (ka[j] - kb[j]);               // s (k1 - k2)
+      W[o.dst + 10 + j] = s * fma(2.0, kb[j], ka[j]);       // s (k2 - k3) = s (k1 + 2 k2)
+      W[o.dst + 14 + j] = -s * fma(2.0, ka[j], kb[j]);      // s (k3 - k1) = -s (2 k1 + k2)
     }
     return;
   }
@@ -243,18 +244,27 @@ __device__ inline void var_ffv_v(const KParams& P, const Op& o, int v, double gs
 #pragma unroll
     for (int j = 0; j < 4; ++j) C[j] = C[j] - rmul(k[j], f);
   }
-  cx out[4] = {cmul(pref, C[0]), cmul(pref, C[1]), cmul(pref, C[2]), cmul(pref, C[3])};
+  cx out[4];
+  if (pref.r == 0.0 && pref.i == 1.0) {            // pure i (QCD root bilinear): no multiply
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = cx{-C[j].i, C[j].r};
+  } else if (pref.r == 0.0) {                        // pure imaginary
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = cx{-pref.i * C[j].i, pref.i * C[j].r};
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = cmul(pref, C[j]);
+  }
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
-// J^r = i s [ (e1.e2)(k1-k2)^r + e2^r ((k2-k3).e1) + e1^r ((k3-k1).e2) ],  s = -g_s/P^2
+// J^r = i [ (e1.e2) s(k1-k2)^r + e2^r (s(k2-k3).e1) + e1^r (s(k3-k1).e2) ],  s = -g_s/P^2
 template <class S>
 __device__ inline void var_vvv(const KParams& P, const Op& o, int v, const S& W) {
   const int hb = pdep(v, o.mdst);
   cx e1[4], e2[4];
   W.load4(o.va + 8 * pext(hb, o.ma), e1);
   W.load4(o.vb + 8 * pext(hb, o.mb), e2);
-  const double s = W[o.dst + 4];
   double d[4], q1[4], q2[4];
   W.loadk(o.dst + 6, d);
   W.loadk(o.dst + 10, q1);
@@ -266,7 +276,7 @@ __device__ inline void var_vvv(const KParams& P, const Op& o, int v, const S& W)
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const cx t = cfma(e1[j], a2, cfma(e2[j], a1, rmul(d[j], s12)));
-    out[j] = cx{-s * t.i, s * t.r};
+    out[j] = cx{-t.i, t.r};
   }
   W.store4(o.dst + 18 + 8 * v, out);
 }

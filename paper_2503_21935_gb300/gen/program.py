@@ -389,10 +389,31 @@ def _wave_schedule(B, chunk):
     return ops, flows, terms, items, steps, A.top
 
 
+def gs_power(D):
+    """Power of g_s carried by every tree amplitude of the process (one per q q g or g g g
+    vertex, two per g g g g vertex); all diagram terms of a process share it, so the kernel
+    evaluates the vertices with g_s = 1 and multiplies |M|^2 by g_s^(2p) = (4 pi alpha_s)^p."""
+    cur = D.currents
+
+    def gp(i):
+        c = cur[i]
+        if c.op == "EXT":
+            return 0
+        own = {"VVV": 1, "VVVV": 2}.get(c.op, 0)
+        if c.op in ("FFV_F", "FFV_FB", "FFV_V"):
+            own = 1 if any(cur[k].flav == "g" for k in c.children) or c.flav == "g" else 0
+        return own + sum(gp(k) for k in c.children)
+    powers = {gp(t.col) + gp(t.vec) + (1 if cur[t.vec].flav == "g" else 0) for t in D.terms}
+    if len(powers) != 1:
+        raise ValueError(f"diagram terms carry different powers of g_s: {powers}")
+    return powers.pop()
+
+
 def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     lhs, rhs = process.split(">")
     inc, out = lhs.split(), rhs.split()
     D = Diagrams(inc, out)
+    gsp = gs_power(D)
     npar = D.npar
     B = _Builder(D)
     ops, flows, terms, top = _dfs_schedule(B)
@@ -429,6 +450,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
                    ext_mass=B.ext_mass, ws_current_doubles=top, ndiagrams=D.ndiagrams, nterms=len(D.terms),
                    average_den=4 * ncol_in * ident, flop_counts=counts)
     prog.cta = cta
+    prog.gs_power = gsp
     return prog
 
 
