@@ -181,6 +181,12 @@ int mgx_compute_noalloc(mgx_process* proc, int64_t nevt, const double* momenta, 
                         const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel,
                         int32_t* selcol, int mode, void* stream);
 
+/* Measured fused-multiply-add throughput (TFLOP/s, fma = 2 flops) of the float64
+ * (precision 64) or float32 (precision 32) pipe of `device`: independent FMA chains, no memory
+ * traffic.  Source of the float64 roofline peak (2 DFMA/clk/SM on GB300).  Synchronous;
+ * allocates a small buffer. */
+int mgx_measure_fma_tflops(int device, int precision, double* tflops);
+
 void mgx_process_destroy(mgx_process* proc);
 const char* mgx_status_string(int status);
 int mgx_version(void);

@@ -60,6 +60,7 @@ def lib():
             "mgx_process_get_kernel": (I, [P]),
             "mgx_process_set_blocks_per_sm": (I, [P, I]),
             "mgx_process_destroy": (None, [P]),
+            "mgx_measure_fma_tflops": (I, [I, I, ctypes.POINTER(D)]),
             "mgx_status_string": (ctypes.c_char_p, [I]),
             "mgx_version": (I, []),
         }
@@ -80,6 +81,13 @@ def default_params():
     p = mgx_params()
     lib().mgx_params_default(ctypes.byref(p))
     return p
+
+
+def measure_fma_tflops(device=0, precision=64):
+    """Measured FMA throughput of the float64 (64) or float32 (32) pipe in TFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib().mgx_measure_fma_tflops(device, precision, ctypes.byref(v)), "mgx_measure_fma_tflops")
+    return v.value
 
 
 def builtin_processes():

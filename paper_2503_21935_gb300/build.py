@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmgx.so")
 GENERATED = os.path.join(HERE, "csrc", "generated", "programs.inc")
-SOURCES = [os.path.join(HERE, "csrc", "mgx.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "mgx.cu"), os.path.join(HERE, "csrc", "peaks.cu")]
 HEADERS = [os.path.join(HERE, "csrc", f) for f in ("mgx_kernel.cuh", "mgx_ops.cuh")] + \
           [os.path.join(ROOT, "include", "mgx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
