@@ -59,7 +59,9 @@ enum mgx_status {
  * amplitudes are float64 in every mode; the helicity sum is float64. */
 enum mgx_mode {
   MGX_FP64 = 0,       /* float64 colour sum */
-  MGX_MIXED_FP32 = 1  /* jamps rounded to float32, float32 quadratic form */
+  MGX_MIXED_FP32 = 1, /* jamps rounded to float32, float32 quadratic form */
+  MGX_MIXED_TF32 = 2  /* tensor-core colour sum: jamps split into two tf32 terms times the
+                         integer-scaled colour matrix (exact in tf32), float32 accumulation */
 };
 
 /* Standard-Model inputs.  Electroweak scheme {alpha_em(mZ), G_F, mZ}. */

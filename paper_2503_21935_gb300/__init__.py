@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libmgx.so")
 MGX_OK = 0
 MGX_FP64 = 0
 MGX_MIXED_FP32 = 1
-MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32}
+MGX_MIXED_TF32 = 2
+MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32, "mixed_tf32": MGX_MIXED_TF32}
 MGX_KERNEL_AUTO, MGX_KERNEL_THREAD, MGX_KERNEL_CTA = 0, 1, 2
 
 
@@ -144,7 +145,7 @@ class Process:
     def workspace(self, nevt, mode=MGX_FP64, host=False):
         import torch
         need = self.workspace_bytes(nevt, mode, host)
-        key = host
+        key = (host, mode == MGX_MIXED_TF32)
         ws = self._ws.get(key)
         if ws is None or ws.numel() < need:
             ws = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{self.device}")

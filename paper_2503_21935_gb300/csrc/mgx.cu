@@ -13,6 +13,7 @@
 
 #include "mgx.h"
 #include "mgx_ops.cuh"
+#include "colour_tc.cuh"
 
 namespace {
 
@@ -33,6 +34,7 @@ struct mgx_program_desc {
   const int32_t* extmass;
   int ws_doubles, ndiag, nterm, avg_den;
   int gs_power;          // power of g_s of every amplitude (vertices are evaluated with g_s = 1)
+  int col_den;           // common denominator of the colour matrix
   int counts[10];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil; current ops; amp terms; amp flows; amp groups
   struct {
     int nops;
@@ -147,7 +149,8 @@ __global__ void __launch_bounds__(kThreads)
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
               int32_t* __restrict__ selhel, int32_t* __restrict__ selcol, double* __restrict__ mh_out,
-              double* __restrict__ colw_out, double* __restrict__ ws, int64_t nthreads, int mode) {
+              double* __restrict__ colw_out, double* __restrict__ ws, int64_t nthreads, int mode,
+              double* __restrict__ jexp, double* __restrict__ colw_exp) {
   extern __shared__ double smem[];
   const int npar4 = 4 * P.npar;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,6 +187,20 @@ __global__ void __launch_bounds__(kThreads)
       const int nv = 1 << __popc(o.mdst);
       for (int v = 0; v < nv; ++v) op_variant(P, o, v, gs, pe, W);
     }
+    if (mode == MGX_MIXED_TF32) {
+      // export the jamps [ngood][ncol][re, im] and the colour weights for the tensor-core colour sum
+      const int nj = 2 * P.ncol * P.ngood;
+      for (int i = 0; i < nj; ++i) jexp[e * nj + i] = W[P.jamp_off + i];
+      for (int i = 0; i < P.ncol; ++i) {
+        double w = 0.0;
+        for (int ih = 0; ih < P.ngood; ++ih) {
+          const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
+          w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
+        }
+        colw_exp[e * P.ncol + i] = w * scale;
+      }
+      continue;
+    }
     for (int ih = 0; ih < P.ngood; ++ih) {
       const int jb = P.jamp_off + 2 * P.ncol * ih;
       const double mh = scale * quad_form([&](int k) { return W[jb + k]; }, P.colsym, P.colsym_f, P.ncol, mode);
@@ -205,6 +222,25 @@ __global__ void __launch_bounds__(kThreads)
     finish_event(P, e, [&](int ih) { return W[P.mh_off + ih]; }, [&](int i) { return W[P.colw_off + i]; },
                  rhel, rcol, me, selhel, selcol);
   }
+}
+
+// helicity sum and selections after the tensor-core colour sum: mh_tc holds |M_h|^2 / g_s^(2p)
+__global__ void __launch_bounds__(kThreads)
+    finish_kernel(const KParams P, int64_t nevt, const double* __restrict__ alphas, const double* __restrict__ rhel,
+                  const double* __restrict__ rcol, const double* __restrict__ mh_tc,
+                  const double* __restrict__ colw, double* __restrict__ me, int32_t* __restrict__ selhel,
+                  int32_t* __restrict__ selcol, double* __restrict__ mh_out, double* __restrict__ colw_out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nevt) return;
+  const double scale = coupling_scale(P, alphas[e]);
+  const double* m = mh_tc + e * P.ngood;
+  const double* w = colw + e * P.ncol;
+  if (mh_out)
+    for (int ih = 0; ih < P.ngood; ++ih) mh_out[e * P.ngood + ih] = scale * m[ih];
+  if (colw_out)
+    for (int i = 0; i < P.ncol; ++i) colw_out[e * P.ncol + i] = w[i];
+  finish_event(P, e, [&](int ih) { return scale * m[ih]; }, [&](int i) { return w[i]; }, rhel, rcol, me, selhel,
+               selcol);
 }
 
 // ---------------------------------------------------------------- CTA-per-event kernel
@@ -434,6 +470,8 @@ struct mgx_process {
   int4* d_cta_terms = nullptr;
   int* d_cta_items = nullptr;
   int3* d_cta_steps = nullptr;
+  float* d_bcanon = nullptr;  // integer-scaled colour matrix, canonical K-major tf32 tile
+  int tc_kpad = 0, tc_npad = 0, tc_cols = 0;
   int blocks_per_sm = 4;      // thread-per-event kernel
   int kernel = MGX_KERNEL_AUTO;
 };
@@ -489,17 +527,95 @@ int launch_cta(mgx_process* pr, const KParams& kp, int64_t nevt, const double* m
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
+bool mode_ok(int mode) { return mode == MGX_FP64 || mode == MGX_MIXED_FP32 || mode == MGX_MIXED_TF32; }
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Tensor-core colour-sum mode: events are processed in chunks; per chunk the amplitude kernel
+// exports jamps (f64) and colour weights, the tensor-core kernel forms |M_h|^2, the finish kernel
+// sums helicities and selects.
+struct TcPlan {
+  int64_t chunk = 0;
+  size_t ws = 0, jexp = 0, colw = 0, mh = 0, err = 0, total = 0;
+};
+
+TcPlan tc_plan(const mgx_process* pr, const KParams& kp, int64_t nevt) {
+  TcPlan t;
+  const size_t per_evt = (size_t)kp.ngood * kp.ncol * 2 * sizeof(double);
+  const int64_t full = grid_threads(pr, std::max<int64_t>(nevt, 1));
+  const int64_t budget = (int64_t)(((size_t)2 << 30) / per_evt);       // about 2 GiB of exported jamps
+  t.chunk = std::min<int64_t>(std::max<int64_t>(nevt, 1), std::max<int64_t>(full, budget / kThreads * kThreads));
+  t.ws = align256((size_t)grid_threads(pr, t.chunk) * kp.ws_doubles * sizeof(double));
+  t.jexp = align256((size_t)t.chunk * per_evt);
+  t.colw = align256((size_t)t.chunk * kp.ncol * sizeof(double));
+  t.mh = align256((size_t)t.chunk * kp.ngood * sizeof(double));
+  t.err = 256;
+  t.total = t.ws + t.jexp + t.colw + t.mh + t.err;
+  return t;
+}
+
+// marks every event of a chunk whose tensor-core colour sum timed out
+__global__ void tc_error_kernel(const int* err, int64_t n, double* me) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n && *err) me[e] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
+              const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
+              void* ws, size_t wsb, cudaStream_t st) {
+  const TcPlan t = tc_plan(pr, kp, nevt);
+  if (ws == nullptr || wsb < t.total) return MGX_ERR_WORKSPACE_TOO_SMALL;
+  char* p = (char*)ws;
+  double* w_thr = (double*)p; p += t.ws;
+  double* jexp = (double*)p; p += t.jexp;
+  double* colw = (double*)p; p += t.colw;
+  double* mhb = (double*)p; p += t.mh;
+  int* err = (int*)p;
+  const size_t smem_tc = colour_tc_smem(pr->tc_kpad, pr->tc_npad);
+  if (cudaFuncSetAttribute(colour_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc) != cudaSuccess)
+    return MGX_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, colour_tc_kernel, kTcRows, smem_tc) != cudaSuccess ||
+      per_sm < 1)
+    return MGX_ERR_CUDA;
+  per_sm = std::min(per_sm, 512 / pr->tc_cols);   // tensor-memory columns of one SM
+  const int npar4 = 4 * kp.npar;
+  const size_t shm = (size_t)kThreads * npar4 * sizeof(double);
+  for (int64_t c0 = 0; c0 < nevt; c0 += t.chunk) {
+    const int64_t n = std::min(t.chunk, nevt - c0);
+    const int64_t nt = grid_threads(pr, n);
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return MGX_ERR_CUDA;
+    me_kernel<<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(kp, n, mom + c0 * npar4, as + c0, nullptr, nullptr,
+                                                                me + c0, nullptr, nullptr, nullptr, nullptr, w_thr, nt,
+                                                                MGX_MIXED_TF32, jexp, colw);
+    const int64_t rows = 2 * n * kp.ngood;
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+    const int64_t blocks = std::min<int64_t>(tiles, (int64_t)per_sm * sm_count(pr->device));
+    colour_tc_kernel<<<(unsigned)blocks, kTcRows, smem_tc, st>>>(jexp, rows, kp.ncol, pr->tc_kpad, pr->tc_npad,
+                                                                 (uint32_t)pr->tc_cols, pr->d_bcanon,
+                                                                 1.0 / pr->prog->col_den, mhb, err);
+    finish_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        kp, n, as + c0, rh ? rh + c0 : nullptr, rc ? rc + c0 : nullptr, mhb, colw, me + c0, sh ? sh + c0 : nullptr,
+        sc ? sc + c0 : nullptr, mh ? mh + c0 * kp.ngood : nullptr, cw ? cw + c0 * kp.ncol : nullptr);
+    tc_error_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(err, n, me + c0);
+    if (cudaGetLastError() != cudaSuccess) return MGX_ERR_CUDA;
+  }
+  return MGX_OK;
+}
+
 int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
            const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
            int mode, void* ws, size_t wsb, cudaStream_t st) {
   if (nevt == 0) return MGX_OK;
+  if (mode == MGX_MIXED_TF32) return launch_tc(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
   if (use_cta(pr, kp)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
   const int64_t nt = grid_threads(pr, nevt);
   const size_t need = (size_t)nt * ws_doubles_per_thread(kp) * sizeof(double);
   if (wsb < need || ws == nullptr) return MGX_ERR_WORKSPACE_TOO_SMALL;
   const int blocks = (int)(nt / kThreads);
   const size_t shm = (size_t)kThreads * 4 * kp.npar * sizeof(double);
-  me_kernel<<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt, mode);
+  me_kernel<<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt, mode,
+                                           nullptr, nullptr);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
@@ -547,6 +663,7 @@ void mgx_process_destroy(mgx_process* pr) {
   cudaFree(pr->d_col);
   cudaFree(pr->d_colf);
   cudaFree(pr->d_terms);
+  cudaFree(pr->d_bcanon);
   cudaFree(pr->d_cta_ops);
   cudaFree(pr->d_cta_flows);
   cudaFree(pr->d_cta_terms);
@@ -649,6 +766,24 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
     cudaSetDevice(cur);
     return MGX_ERR_CUDA;
   }
+  if (ok) {
+    // integer-scaled colour matrix as a canonical K-major tf32 tile for the tensor-core colour sum
+    pr->tc_kpad = (n + 7) / 8 * 8;
+    pr->tc_npad = (n + 15) / 16 * 16;
+    pr->tc_cols = 32;
+    while (pr->tc_cols < pr->tc_npad) pr->tc_cols *= 2;
+    std::vector<float> bc((size_t)pr->tc_npad * pr->tc_kpad, 0.0f);
+    for (int r = 0; r < n; ++r)
+      for (int k = 0; k < n; ++k)
+        bc[umma::kmajor_offset(r, k, pr->tc_kpad, 4) / 4] = (float)(prog->colour[r * n + k] * prog->col_den);
+    ok = cudaMalloc(&pr->d_bcanon, sizeof(float) * bc.size()) == cudaSuccess &&
+         cudaMemcpy(pr->d_bcanon, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!ok) {
+    mgx_process_destroy(pr);
+    cudaSetDevice(cur);
+    return MGX_ERR_CUDA;
+  }
   kp.ops = pr->d_ops;
   kp.flows = pr->d_flows;
   kp.terms = pr->d_terms;
@@ -728,7 +863,11 @@ int mgx_colour_matrix(const mgx_process* pr, double* out) {
 
 int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* bytes) {
   if (!pr || !bytes || nevt < 0) return MGX_ERR_INVALID_ARGUMENT;
-  if (mode != MGX_FP64 && mode != MGX_MIXED_FP32) return MGX_ERR_UNSUPPORTED_MODE;
+  if (!mode_ok(mode)) return MGX_ERR_UNSUPPORTED_MODE;
+  if (mode == MGX_MIXED_TF32) {
+    *bytes = nevt == 0 ? 0 : tc_plan(pr, pr->kp, nevt).total;
+    return MGX_OK;
+  }
   *bytes = (nevt == 0 || use_cta(pr, pr->kp)) ? 0 : (size_t)grid_threads(pr, nevt) * pr->kp.ws_doubles * sizeof(double);
   return MGX_OK;
 }
@@ -737,7 +876,7 @@ int mgx_compute_ex(mgx_process* pr, int64_t nevt, const double* momenta, const d
                    const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel, int32_t* selcol,
                    double* mh, double* colw, int mode, void* workspace, size_t workspace_bytes, void* stream) {
   if (!pr || nevt < 0) return MGX_ERR_INVALID_ARGUMENT;
-  if (mode != MGX_FP64 && mode != MGX_MIXED_FP32) return MGX_ERR_UNSUPPORTED_MODE;
+  if (!mode_ok(mode)) return MGX_ERR_UNSUPPORTED_MODE;
   if (nevt == 0) return MGX_OK;
   if (!momenta || !alpha_s || !me) return MGX_ERR_INVALID_ARGUMENT;
   if ((selhel && !rnd_hel) || (selcol && !rnd_col)) return MGX_ERR_INVALID_ARGUMENT;
@@ -756,8 +895,6 @@ int mgx_compute(mgx_process* pr, int64_t nevt, const double* momenta, const doub
   return mgx_compute_ex(pr, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, mode,
                         workspace, workspace_bytes, stream);
 }
-
-static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 int mgx_host_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* bytes) {
   size_t ws = 0;
@@ -906,7 +1043,8 @@ extern "C" int mgx_compute_noalloc(mgx_process* pr, int64_t nevt, const double* 
   const int64_t nt = blocks * kThreads;
   const size_t shm = (size_t)kThreads * 4 * pr->kp.npar * sizeof(double);
   me_kernel<<<(unsigned)blocks, kThreads, shm, (cudaStream_t)stream>>>(
-      pr->kp, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, scratch, nt, mode);
+      pr->kp, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, scratch, nt, mode,
+      nullptr, nullptr);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 

@@ -451,6 +451,19 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
                    average_den=4 * ncol_in * ident, flop_counts=counts)
     prog.cta = cta
     prog.gs_power = gsp
+    # integer scaling of the colour matrix for the tensor-core colour sum (exact in tf32)
+    den = 1
+    for row in C:
+        for x in row:
+            den = math.lcm(den, Fraction(x).denominator)
+    for row in C:
+        for x in row:
+            v = abs(int(x * den))
+            while v and v % 2 == 0:
+                v //= 2
+            if v.bit_length() > 11:
+                raise ValueError("scaled colour matrix not exact in tf32")
+    prog.col_den = den
     return prog
 
 

@@ -88,6 +88,36 @@ def test_parity_mixed_fp32_colour_sum(name, nevt, bound):
     assert np.abs(got["me"] / ref["me"] - 1.0).max() <= bound
 
 
+@pytest.mark.parametrize("name,nevt,bound", [("ggtt", 300, 1e-5), ("ggttg", 200, 1e-5), ("ggttgg", 130, 1e-5),
+                                             ("ggttggg", 12, 1e-5)])
+def test_parity_tensor_core_colour_sum(name, nevt, bound):
+    """tcgen05 colour sum (jamps as two tf32 terms x integer-scaled colour matrix, f32 accumulation)."""
+    wl = WORKLOADS[name]
+    mom, a, rh, rc = make_inputs(wl, nevt)
+    proc = _proc(wl.process)
+    got = _run(proc, mom, a, rh, rc, mode=2)
+    ref = oracle_get(wl.process).evaluate(mom, a, rh, rc)
+    assert np.abs(got["me"] / ref["me"] - 1.0).max() <= bound
+    tot = ref["mh"].sum(axis=1, keepdims=True)
+    assert (np.abs(got["mh"] - ref["mh"][:, proc.good_helicities]) / tot).max() <= bound
+    # colour weights come from the float64 jamps in every mode
+    assert (np.abs(got["colw"] - ref["colw"]) / ref["colw"].sum(axis=1, keepdims=True)).max() <= TOL
+    tie_c = near_tie(ref["colw"], rc, TOL)
+    assert np.array_equal(got["selcol"][~tie_c], ref["selcol"][~tie_c])
+
+
+def test_tensor_core_colour_sum_chunks_and_tail():
+    """Several chunks and a ragged last tile give the same me as the float32 SIMT colour sum."""
+    wl = WORKLOADS["ggttg"]
+    n = 100003
+    mom, a, rh, rc = make_inputs(wl, n)
+    proc = _proc(wl.process)
+    tc = _run(proc, mom, a, rh, rc, mode=2)
+    f32 = _run(proc, mom, a, rh, rc, mode=1)
+    assert np.all(np.isfinite(tc["me"]))
+    assert np.abs(tc["me"] / f32["me"] - 1.0).max() <= 2e-5
+
+
 @pytest.mark.parametrize("nevt", [1, 127, 128, 129])
 def test_ragged_sizes(nevt):
     wl = WORKLOADS["ggttg"]
