@@ -183,6 +183,75 @@ int mgx_compute_noalloc(mgx_process* proc, int64_t nevt, const double* momenta, 
                         const double* rnd_hel, const double* rnd_col, double* me, int32_t* selhel,
                         int32_t* selcol, int mode, void* stream);
 
+/* ---- device-side event generation (random numbers -> momenta, Sec. 2) ----
+ * Philox-4x32-10 words for event e come from counter (e mod 2^32, block, stream, e >> 32)
+ * and key = seed, so results depend only on (seed, stream, event index) and equal the host
+ * generator bit for bit (the Python package `phasespace`). */
+
+/* out[i] = uniform in [0,1) with 53 bits from block 0 of event first+i (DEVICE array). */
+int mgx_uniforms(int64_t n, int64_t first, uint64_t seed, uint32_t stream_id, double* out, void* stream);
+
+/* Flat phase space by RAMBO for events first .. first+n-1: momenta [n][nfinal+2][4] (DEVICE):
+ * two beams along +-z with E = sqrts/2, then nfinal particles of masses masses_dev[nfinal]
+ * (DEVICE array); weight [n] (DEVICE, may be NULL) = phase-space weight.  nfinal <= 8. */
+int mgx_rambo(int64_t n, int64_t first, double sqrts, int nfinal, const double* masses_dev, uint64_t seed,
+              double* momenta, double* weight, void* stream);
+
+/* Generator-level cuts: pass[i] = 1 when every particle listed in list_dev[nlist] (indices into
+ * npar) has pT > ptmin and |eta| < etamax and every listed pair has dR > drmin, else 0. */
+int mgx_cuts(int64_t n, int npar, const double* momenta, int nlist, const int* list_dev, double ptmin,
+             double etamax, double drmin, uint8_t* pass, void* stream);
+
+/* ---- learned surrogate of log|M|^2 (two-stage unweighting) ----
+ * MLP x[24] -> 4 x 256 SiLU -> scalar; float32 master weights, bfloat16 tensor-core products
+ * with float32 accumulation.  Parameters are one flat float32 vector of mgx_mlp_num_params()
+ * entries: per hidden layer l, W_l [256][kin_l] row-major (kin_0 = 32: the 24 inputs zero-padded,
+ * padded columns zero) then b_l [256]; then w_out [256] and b_out.  Inputs are float32 [n][24]. */
+typedef struct mgx_mlp mgx_mlp;
+int mgx_mlp_num_params(void);
+/* Create a network on `device` with He-uniform weights from a seeded generator.  Synchronous. */
+int mgx_mlp_create(int device, uint64_t seed, mgx_mlp** out);
+void mgx_mlp_destroy(mgx_mlp* net);
+/* DEVICE workspace bytes for a training batch of n rows (training != 0, n <= 2^24) or for
+ * inference over any n (processed in chunks of 65536 rows). */
+int mgx_mlp_workspace_bytes(int64_t n, int training, size_t* bytes);
+/* Host copies of the flat float32 parameter vector (set also refreshes the bfloat16 copies). */
+int mgx_mlp_get_params(const mgx_mlp* net, float* host);
+int mgx_mlp_set_params(mgx_mlp* net, const float* host);
+/* y[n] = network(x[n][24]); DEVICE arrays; asynchronous on stream. */
+int mgx_mlp_forward(mgx_mlp* net, int64_t n, const float* x, float* y, void* ws, size_t wsb, void* stream);
+/* Gradient of the mean squared error over one batch of n rows (targets t[n]) into grad
+ * (DEVICE, num_params floats, may be NULL) and the loss into loss (DEVICE float, may be NULL). */
+int mgx_mlp_gradients(mgx_mlp* net, int n, const float* x, const float* t, float* grad, float* loss, void* ws,
+                      size_t wsb, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on one batch. */
+int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, float lr, float* loss, void* ws,
+                       size_t wsb, void* stream);
+
+/* ---- unweighting (plain hit-or-miss and two-stage with the surrogate) ----
+ * Plain: keep with probability min(1, w/w_max), weight max(1, w/w_max).  Two-stage
+ * (Danziger, Janssen, Schumann, Siegert, arXiv:2109.11964): stage 1 keeps with probability
+ * min(1, s/s_max) on the surrogate weight s, stage 2 evaluates the exact weight w of the
+ * survivors and keeps them with probability min(1, (w/s)/r_max); the kept event carries
+ * max(1, s/s_max) max(1, (w/s)/r_max), so the unweighted sample is unbiased.  All arrays DEVICE. */
+/* x[i][j] = float(momenta[i][j] / scale), j < ncomp (the flattened momenta of one event). */
+int mgx_features(int64_t n, int ncomp, const double* momenta, double scale, float* x, void* stream);
+/* s = exp(mean + sd y) * wps * pass (wps, pass may be NULL). */
+int mgx_surrogate_weight(int64_t n, const float* y, double mean, double sd, const double* wps,
+                         const uint8_t* pass, double* s, void* stream);
+/* w = me * wps * pass (wps, pass may be NULL). */
+int mgx_exact_weight(int64_t n, const double* me, const double* wps, const uint8_t* pass, double* w,
+                     void* stream);
+/* ratio = w/wref (wref NULL: w); keep = r * wmax < ratio; overweight = max(1, ratio/wmax) (may be NULL). */
+int mgx_accept(int64_t n, const double* w, const double* wref, double wmax, const double* r, uint8_t* keep,
+               double* overweight, void* stream);
+/* Deterministic stream compaction: index[0..count) = ascending i with keep[i] != 0; count to count_dev. */
+int mgx_compact_workspace_bytes(int64_t n, size_t* bytes);
+int mgx_compact(int64_t n, const uint8_t* keep, int32_t* index, int32_t* count_dev, void* ws, size_t wsb,
+                void* stream);
+/* dst[r][0..row) = src[index[r]][0..row) for r < m (float64 rows). */
+int mgx_gather(int64_t m, const int32_t* index, int row, const double* src, double* dst, void* stream);
+
 /* Measured fused-multiply-add throughput (TFLOP/s, fma = 2 flops) of the float64
  * (precision 64) or float32 (precision 32) pipe of `device`: independent FMA chains, no memory
  * traffic.  Source of the float64 roofline peak (2 DFMA/clk/SM on GB300).  Synchronous;

@@ -62,6 +62,25 @@ def lib():
             "mgx_process_set_blocks_per_sm": (I, [P, I]),
             "mgx_process_destroy": (None, [P]),
             "mgx_measure_fma_tflops": (I, [I, I, ctypes.POINTER(D)]),
+            "mgx_uniforms": (I, [I64, I64, U64, ctypes.c_uint32, P, P]),
+            "mgx_rambo": (I, [I64, I64, D, I, P, U64, P, P, P]),
+            "mgx_cuts": (I, [I64, I, P, I, P, D, D, D, P, P]),
+            "mgx_features": (I, [I64, I, P, D, P, P]),
+            "mgx_surrogate_weight": (I, [I64, P, D, D, P, P, P, P]),
+            "mgx_exact_weight": (I, [I64, P, P, P, P, P]),
+            "mgx_accept": (I, [I64, P, P, D, P, P, P, P]),
+            "mgx_compact_workspace_bytes": (I, [I64, ctypes.POINTER(SZ)]),
+            "mgx_compact": (I, [I64, P, P, P, P, SZ, P]),
+            "mgx_gather": (I, [I64, P, I, P, P, P]),
+            "mgx_mlp_num_params": (I, []),
+            "mgx_mlp_create": (I, [I, U64, ctypes.POINTER(P)]),
+            "mgx_mlp_destroy": (None, [P]),
+            "mgx_mlp_workspace_bytes": (I, [I64, I, ctypes.POINTER(SZ)]),
+            "mgx_mlp_get_params": (I, [P, P]),
+            "mgx_mlp_set_params": (I, [P, P]),
+            "mgx_mlp_forward": (I, [P, I64, P, P, P, SZ, P]),
+            "mgx_mlp_gradients": (I, [P, I, P, P, P, P, P, SZ, P]),
+            "mgx_mlp_train_step": (I, [P, I, P, P, ctypes.c_float, P, P, SZ, P]),
             "mgx_status_string": (ctypes.c_char_p, [I]),
             "mgx_version": (I, []),
         }
@@ -89,6 +108,120 @@ def measure_fma_tflops(device=0, precision=64):
     v = ctypes.c_double()
     _check(lib().mgx_measure_fma_tflops(device, precision, ctypes.byref(v)), "mgx_measure_fma_tflops")
     return v.value
+
+
+def _stream(device=None):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def uniforms(n, seed, stream_id, first=0, device=0):
+    """Device tensor of n uniforms in [0,1) (Philox, identical to phasespace.uniform01)."""
+    import torch
+    out = torch.empty(n, dtype=torch.float64, device=f"cuda:{device}")
+    _check(lib().mgx_uniforms(n, first, seed, stream_id, _ptr(out), _stream(out.device)), "mgx_uniforms")
+    return out
+
+
+def rambo(n, sqrts, masses, seed, first=0, device=0):
+    """Device RAMBO: (momenta [n, len(masses)+2, 4], weight [n]), identical events to phasespace.rambo."""
+    import torch
+    dev = torch.device(f"cuda:{device}")
+    m = torch.tensor(list(masses), dtype=torch.float64, device=dev)
+    mom = torch.empty((n, len(masses) + 2, 4), dtype=torch.float64, device=dev)
+    wt = torch.empty(n, dtype=torch.float64, device=dev)
+    _check(lib().mgx_rambo(n, first, float(sqrts), len(masses), _ptr(m), seed, _ptr(mom), _ptr(wt), _stream(dev)),
+           "mgx_rambo")
+    return mom, wt
+
+
+def cuts(momenta, particles, ptmin, etamax, drmin):
+    """Device uint8 mask of events passing pT / |eta| / pairwise dR cuts on the listed particles."""
+    import torch
+    dev = momenta.device
+    lst = torch.tensor(list(particles), dtype=torch.int32, device=dev)
+    out = torch.empty(momenta.shape[0], dtype=torch.uint8, device=dev)
+    _check(lib().mgx_cuts(momenta.shape[0], momenta.shape[1], _ptr(momenta), len(particles), _ptr(lst),
+                          float(ptmin), float(etamax), float(drmin), _ptr(out), _stream(dev)), "mgx_cuts")
+    return out
+
+
+class Mlp:
+    """The MLP surrogate (mgx_mlp_*): forward, gradients and Adam steps in the library's kernels."""
+
+    def __init__(self, seed=0, device=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise MgxError("no CUDA device: the mgx library has no CPU path")
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().mgx_mlp_create(device, seed, ctypes.byref(h)), "mgx_mlp_create")
+        self._h = h
+        self.nparams = lib().mgx_mlp_num_params()
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.mgx_mlp_destroy(h)
+            self._h = None
+
+    def _dev(self, x, dtype=None):
+        import torch
+        if isinstance(x, np.ndarray):
+            x = torch.from_numpy(np.ascontiguousarray(x))
+        return x.to(device=f"cuda:{self.device}", dtype=dtype or x.dtype).contiguous()
+
+    def _workspace(self, n, training):
+        import torch
+        b = ctypes.c_size_t()
+        _check(lib().mgx_mlp_workspace_bytes(n, int(training), ctypes.byref(b)), "mgx_mlp_workspace_bytes")
+        key = bool(training)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < b.value:
+            ws = torch.empty(b.value, dtype=torch.uint8, device=f"cuda:{self.device}")
+            self._ws[key] = ws
+        return ws
+
+    def get_params(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().mgx_mlp_get_params(self._h, p.ctypes.data_as(ctypes.c_void_p)), "mgx_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().mgx_mlp_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)), "mgx_mlp_set_params")
+
+    def forward(self, x, out=None):
+        """x [n, 24] float32 (host or device) -> y [n] (numpy if x was numpy)."""
+        import torch
+        host = isinstance(x, np.ndarray)
+        xd = self._dev(x, torch.float32)
+        n = xd.shape[0]
+        y = out if out is not None else torch.empty(n, dtype=torch.float32, device=xd.device)
+        ws = self._workspace(n, False)
+        _check(lib().mgx_mlp_forward(self._h, n, _ptr(xd), _ptr(y), _ptr(ws), ws.numel(), _stream(xd.device)),
+               "mgx_mlp_forward")
+        return y.cpu().numpy() if host else y
+
+    def gradients(self, x, t):
+        import torch
+        xd, td = self._dev(x, torch.float32), self._dev(t, torch.float32)
+        n = xd.shape[0]
+        g = torch.empty(self.nparams, dtype=torch.float32, device=xd.device)
+        loss = torch.empty(1, dtype=torch.float32, device=xd.device)
+        ws = self._workspace(n, True)
+        _check(lib().mgx_mlp_gradients(self._h, n, _ptr(xd), _ptr(td), _ptr(g), _ptr(loss), _ptr(ws), ws.numel(),
+                                       _stream(xd.device)), "mgx_mlp_gradients")
+        return float(loss.item()), g.cpu().numpy()
+
+    def train_step(self, x, t, lr=1e-3, loss_out=None):
+        import torch
+        xd, td = self._dev(x, torch.float32), self._dev(t, torch.float32)
+        n = xd.shape[0]
+        ws = self._workspace(n, True)
+        _check(lib().mgx_mlp_train_step(self._h, n, _ptr(xd), _ptr(td), ctypes.c_float(lr), _ptr(loss_out),
+                                        _ptr(ws), ws.numel(), _stream(xd.device)), "mgx_mlp_train_step")
 
 
 def builtin_processes():

@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmgx.so")
 GENERATED = os.path.join(HERE, "csrc", "generated", "programs.inc")
-SOURCES = [os.path.join(HERE, "csrc", "mgx.cu"), os.path.join(HERE, "csrc", "peaks.cu")]
-HEADERS = [os.path.join(HERE, "csrc", f) for f in ("mgx_kernel.cuh", "mgx_ops.cuh")] + \
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("mgx.cu", "peaks.cu", "phase_space.cu", "mlp.cu", "unweight.cu")]
+HEADERS = [os.path.join(HERE, "csrc", f) for f in ("mgx_kernel.cuh", "mgx_ops.cuh", "umma.cuh", "colour_tc.cuh")] + \
           [os.path.join(ROOT, "include", "mgx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -44,7 +44,7 @@ def build(force=False, verbose=False):
     deps = SOURCES + HEADERS + [GENERATED]
     if not force and not _stale(LIB, deps):
         return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "--threads", "4",
            "-I", os.path.join(ROOT, "include"), "-I", os.path.join(HERE, "csrc"),
            "-o", LIB + ".tmp", *SOURCES]
     if verbose:
