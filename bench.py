@@ -43,6 +43,7 @@ def _args():
     ap.add_argument("--impl", default="mgx", choices=["mgx", "reference"])
     ap.add_argument("--nevt", type=int, default=NEVT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     return ap.parse_args()
 
 
@@ -187,6 +188,113 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ secondary workloads
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def extra_modes(pkg, proc, M, A, RH, RC, nevt, stream):
+    """ggttgg at 2^20 events with the float32 SIMT and tensor-core (tcgen05 tf32) colour sums."""
+    out = {}
+    for name in ("mixed_fp32", "mixed_tf32"):
+        mode = pkg.MODES[name]
+        ms = _timed(lambda: proc.compute(M, A, RH, RC, mode=mode, stream=stream), 3, 1, stream)
+        out[name] = {"value": nevt / (ms * 1e-3), "unit": "events/s", "ms_per_step": ms}
+    return out
+
+
+def extra_ggttggg(pkg, dev, stream):
+    """g g > t t~ g g g, 2^18 events, float64 and mixed float32 colour sum."""
+    import numpy as np
+    import torch
+    from phasespace import WORKLOADS, make_inputs
+    wl = WORKLOADS["ggttggg"]
+    mom, a, rh, rc = make_inputs(wl, wl.nevt)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
+    proc = pkg.Process(wl.process, device=dev.index)
+    out = {"nevt": wl.nevt, "ndiagrams": proc.ndiagrams, "ncol": proc.ncol, "ngood": proc.ngood}
+    for name in ("fp64", "mixed_fp32"):
+        mode = pkg.MODES[name]
+        ms = _timed(lambda: proc.compute(M, A, RH, RC, mode=mode, stream=stream), 1, 1, stream)
+        out[name] = {"value": wl.nevt / (ms * 1e-3), "unit": "events/s", "ms_per_step": ms,
+                     "fp64_flops_per_event": proc.fp64_flops_per_event(mode)}
+    return out
+
+
+def extra_batched(pkg, dev, stream):
+    """g g > t t~ (2^22), t t~ g (2^20), t t~ g g (2^18), g u~ > ta+ ta- g g u~ (2^16): one
+    autotuned persistent launch captured in a CUDA graph vs one launch per process."""
+    import numpy as np
+    import torch
+    from phasespace import WORKLOADS, make_inputs
+    sets = [("ggtt", 1 << 22), ("ggttg", 1 << 20), ("ggttgg", 1 << 18), ("gu_tataggu", 1 << 16)]
+    procs, inputs, outs = [], [], []
+    for name, n in sets:
+        wl = WORKLOADS[name]
+        mom, a, rh, rc = make_inputs(wl, n)
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        inputs.append((t(mom), t(a), t(rh), t(rc)))
+        procs.append(pkg.Process(wl.process, device=dev.index))
+        outs.append({"me": torch.empty(n, dtype=torch.float64, device=dev),
+                     "selhel": torch.empty(n, dtype=torch.int32, device=dev),
+                     "selcol": torch.empty(n, dtype=torch.int32, device=dev)})
+    total = sum(n for _, n in sets)
+
+    def seq():
+        for p, inp, o in zip(procs, inputs, outs):
+            p.compute(*inp, stream=stream, out=o)
+    ms_seq = _timed(seq, 2, 1, stream)
+    b = pkg.Batch(procs)
+    bps, epi = b.autotune(inputs, outs)
+    side = torch.cuda.Stream(device=dev)           # graphs are captured on a non-default stream
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        b.capture(inputs, outs, side)
+        ms_b = _timed(lambda: b.replay(side), 3, 1, side)
+    return {"events": total, "batched_graph": {"value": total / (ms_b * 1e-3), "unit": "events/s", "ms": ms_b,
+                                               "blocks_per_sm": bps, "events_per_item": epi},
+            "sequential": {"value": total / (ms_seq * 1e-3), "unit": "events/s", "ms": ms_seq}}
+
+
+def extra_surrogate(pkg, dev):
+    """g g > t t~ g g with cuts: surrogate training, then unweighted events/s plain vs two-stage."""
+    import torch
+    from paper_2503_21935_gb300.surrogate import Unweighter
+    U = Unweighter("g g > t t~ g g", 1500.0, [173.0, 173.0, 0.0, 0.0], cut_particles=[4, 5], device=dev.index,
+                   seed=5)
+    t0 = time.perf_counter()
+    hist = U.train(1 << 22, steps=4000, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    U.calibrate(1 << 20)
+    res = {"training": {"events": 1 << 22, "steps": 4000, "batch": 8192, "seconds": train_s,
+                        "loss_first": hist[0][1], "loss_last": hist[-1][1]}}
+    for name, fn in (("plain", U.plain), ("surrogate", U.two_stage)):
+        fn(1 << 20, seed=900)                      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn(1 << 22, seed=901)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        n_unw = int(r["weight"].shape[0])
+        res[name] = {"value": n_unw / dt, "unit": "unweighted events/s", "generated": r["generated"],
+                     "unweighted": n_unw, "exact_me_calls": r["exact_calls"], "seconds": dt,
+                     "overweight_fraction": float((r["weight"] > 1).float().mean().item()) if n_unw else None}
+    res["gain"] = res["surrogate"]["value"] / res["plain"]["value"] if res["plain"]["value"] else None
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -295,6 +403,19 @@ def run_gpu(args):
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu,
                 "wall_s_timed": wall}
+        if not args.no_extras and world == 1:
+            extras = {}
+            for key, fn in (("ggttgg_modes", lambda: extra_modes(pkg, proc, M, A, RH, RC, nevt, stream)),
+                            ("ggttggg", lambda: extra_ggttggg(pkg, dev, stream)),
+                            ("batched", lambda: extra_batched(pkg, dev, stream)),
+                            ("surrogate_unweighting", lambda: extra_surrogate(pkg, dev))):
+                t0 = time.perf_counter()
+                try:
+                    extras[key] = fn()
+                except Exception as exc:          # a secondary workload must not hide the headline
+                    extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+                extras[key]["wall_s"] = time.perf_counter() - t0
+            line["extras"] = extras
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -154,6 +154,47 @@ int mgx_process_get_kernel(const mgx_process* proc);        /* the kernel AUTO r
  * the workspace size grows with it. */
 int mgx_process_set_blocks_per_sm(mgx_process* proc, int blocks_per_sm);
 
+/* ---- batched multi-process launch (one persistent kernel over several processes) ----
+ * Work items of events_per_item events of one process are numbered process after process and
+ * taken from a device counter by the CTAs of one persistent grid (no waits), so processes with
+ * very different event counts and costs share the GPU in one launch.  Results are identical to
+ * per-process mgx_compute (each event is evaluated by the same code). */
+typedef struct mgx_batch mgx_batch;
+typedef struct mgx_batch_io {
+  int64_t nevt;
+  const double* momenta;  /* DEVICE [nevt][npar][4] */
+  const double* alpha_s;  /* DEVICE [nevt] */
+  const double* rnd_hel;  /* DEVICE [nevt] or NULL */
+  const double* rnd_col;  /* DEVICE [nevt] or NULL */
+  double* me;             /* DEVICE [nevt] */
+  int32_t* selhel;        /* DEVICE [nevt] or NULL */
+  int32_t* selcol;        /* DEVICE [nevt] or NULL */
+} mgx_batch_io;
+/* procs[nproc] (1..16) on one device; the handles must outlive the batch. */
+int mgx_batch_create(mgx_process* const* procs, int nproc, mgx_batch** out);
+void mgx_batch_destroy(mgx_batch* batch);
+/* DEVICE workspace bytes (independent of the event counts). */
+int mgx_batch_workspace_bytes(const mgx_batch* batch, size_t* bytes);
+/* io[nproc], one entry per process in creation order; modes MGX_FP64 / MGX_MIXED_FP32. Async. */
+int mgx_batch_compute(mgx_batch* batch, const mgx_batch_io* io, int mode, void* workspace, size_t workspace_bytes,
+                      void* stream);
+/* Capture the batched launch (counter reset + kernel) for these buffers into a CUDA graph owned
+ * by the batch (stream must not be the legacy default stream); mgx_batch_replay launches it. */
+int mgx_batch_capture(mgx_batch* batch, const mgx_batch_io* io, int mode, void* workspace, size_t workspace_bytes,
+                      void* stream);
+int mgx_batch_replay(mgx_batch* batch, void* stream);
+/* Autotuner: times the batched launch on these buffers for blocks per SM in {2, 4} and
+ * events per work item in {128, 512, 2048}, keeps the fastest.  Synchronous. */
+int mgx_batch_autotune(mgx_batch* batch, const mgx_batch_io* io, int mode, void* workspace,
+                       size_t workspace_bytes, void* stream, int* blocks_per_sm, int* events_per_item);
+/* Autotuner of a single process: times mgx_compute on these inputs for the thread-per-event
+ * kernel at 2 and 4 blocks per SM and the CTA-per-event kernel (when usable), keeps the fastest
+ * (me_scratch: DEVICE [nevt] output buffer).  Query mgx_workspace_bytes again afterwards.
+ * Synchronous. */
+int mgx_process_autotune(mgx_process* proc, int64_t nevt, const double* momenta, const double* alpha_s, int mode,
+                         void* workspace, size_t workspace_bytes, void* stream, int* kernel, int* blocks_per_sm,
+                         double* me_scratch);
+
 /* Float64 work per event of this process in `mode`, from the op table and per-op
  * instruction counts of the device code: instructions (add, multiply and fused
  * multiply-add each one) and flops (a fused multiply-add counted as two).  Used for

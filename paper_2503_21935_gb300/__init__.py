@@ -72,6 +72,14 @@ def lib():
             "mgx_compact_workspace_bytes": (I, [I64, ctypes.POINTER(SZ)]),
             "mgx_compact": (I, [I64, P, P, P, P, SZ, P]),
             "mgx_gather": (I, [I64, P, I, P, P, P]),
+            "mgx_batch_create": (I, [P, I, ctypes.POINTER(P)]),
+            "mgx_batch_destroy": (None, [P]),
+            "mgx_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
+            "mgx_batch_compute": (I, [P, P, I, P, SZ, P]),
+            "mgx_batch_capture": (I, [P, P, I, P, SZ, P]),
+            "mgx_batch_replay": (I, [P, P]),
+            "mgx_batch_autotune": (I, [P, P, I, P, SZ, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "mgx_process_autotune": (I, [P, I64, P, P, I, P, SZ, P, ctypes.POINTER(I), ctypes.POINTER(I), P]),
             "mgx_mlp_num_params": (I, []),
             "mgx_mlp_create": (I, [I, U64, ctypes.POINTER(P)]),
             "mgx_mlp_destroy": (None, [P]),
@@ -144,6 +152,72 @@ def cuts(momenta, particles, ptmin, etamax, drmin):
     _check(lib().mgx_cuts(momenta.shape[0], momenta.shape[1], _ptr(momenta), len(particles), _ptr(lst),
                           float(ptmin), float(etamax), float(drmin), _ptr(out), _stream(dev)), "mgx_cuts")
     return out
+
+
+class mgx_batch_io(ctypes.Structure):
+    _fields_ = [("nevt", ctypes.c_int64)] + [(n, ctypes.c_void_p) for n in
+                                             ("momenta", "alpha_s", "rnd_hel", "rnd_col", "me", "selhel", "selcol")]
+
+
+class Batch:
+    """Several processes in one persistent launch (mgx_batch_*), optionally captured in a CUDA graph."""
+
+    def __init__(self, processes):
+        import torch
+        self.procs = list(processes)
+        arr = (ctypes.c_void_p * len(self.procs))(*[p._h.value for p in self.procs])
+        h = ctypes.c_void_p()
+        _check(lib().mgx_batch_create(arr, len(self.procs), ctypes.byref(h)), "mgx_batch_create")
+        self._h = h
+        b = ctypes.c_size_t()
+        _check(lib().mgx_batch_workspace_bytes(h, ctypes.byref(b)), "mgx_batch_workspace_bytes")
+        self.ws = torch.empty(b.value, dtype=torch.uint8, device=f"cuda:{self.procs[0].device}")
+        self._io = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.mgx_batch_destroy(h)
+            self._h = None
+
+    def _make_io(self, inputs, outputs):
+        io = (mgx_batch_io * len(self.procs))()
+        for k, (inp, out) in enumerate(zip(inputs, outputs)):
+            mom, a = inp[0], inp[1]
+            rh = inp[2] if len(inp) > 2 else None
+            rc = inp[3] if len(inp) > 3 else None
+            io[k].nevt = mom.shape[0]
+            io[k].momenta, io[k].alpha_s = mom.data_ptr(), a.data_ptr()
+            io[k].rnd_hel = rh.data_ptr() if rh is not None else None
+            io[k].rnd_col = rc.data_ptr() if rc is not None else None
+            io[k].me = out["me"].data_ptr()
+            io[k].selhel = out["selhel"].data_ptr() if out.get("selhel") is not None else None
+            io[k].selcol = out["selcol"].data_ptr() if out.get("selcol") is not None else None
+        self._io = io
+        return io
+
+    def compute(self, inputs, outputs, mode=MGX_FP64, stream=None):
+        """inputs: per process (momenta, alpha_s[, rnd_hel, rnd_col]); outputs: per process dict(me, selhel, selcol)."""
+        io = self._make_io(inputs, outputs)
+        st = stream or _stream(self.ws.device)
+        _check(lib().mgx_batch_compute(self._h, io, mode, _ptr(self.ws), self.ws.numel(),
+                                       ctypes.c_void_p(st.cuda_stream) if hasattr(st, "cuda_stream") else st),
+               "mgx_batch_compute")
+
+    def capture(self, inputs, outputs, stream, mode=MGX_FP64):
+        io = self._make_io(inputs, outputs)
+        _check(lib().mgx_batch_capture(self._h, io, mode, _ptr(self.ws), self.ws.numel(),
+                                       ctypes.c_void_p(stream.cuda_stream)), "mgx_batch_capture")
+
+    def replay(self, stream):
+        _check(lib().mgx_batch_replay(self._h, ctypes.c_void_p(stream.cuda_stream)), "mgx_batch_replay")
+
+    def autotune(self, inputs, outputs, mode=MGX_FP64):
+        io = self._make_io(inputs, outputs)
+        b, e = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mgx_batch_autotune(self._h, io, mode, _ptr(self.ws), self.ws.numel(), _stream(self.ws.device),
+                                        ctypes.byref(b), ctypes.byref(e)), "mgx_batch_autotune")
+        return b.value, e.value
 
 
 class Mlp:
@@ -296,6 +370,21 @@ class Process:
     def set_blocks_per_sm(self, n):
         _check(lib().mgx_process_set_blocks_per_sm(self._h, n), "mgx_process_set_blocks_per_sm")
         self._ws = {}
+
+    def autotune(self, momenta, alpha_s, mode=MGX_FP64):
+        """Pick the fastest kernel / blocks-per-SM for these inputs (mgx_process_autotune)."""
+        import torch
+        n = momenta.shape[0]
+        self.set_kernel(MGX_KERNEL_THREAD)
+        self.set_blocks_per_sm(4)
+        ws = self.workspace(n, mode)
+        me = torch.empty(n, dtype=torch.float64, device=momenta.device)
+        k, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mgx_process_autotune(self._h, n, _ptr(momenta), _ptr(alpha_s), mode, _ptr(ws), ws.numel(),
+                                          _stream(momenta.device), ctypes.byref(k), ctypes.byref(b), _ptr(me)),
+               "mgx_process_autotune")
+        self._ws = {}
+        return k.value, b.value
 
     def fp64_ops_per_event(self, mode=MGX_FP64):
         """Float64 instructions per event (fma, mul, add one each)."""

@@ -145,6 +145,81 @@ __device__ inline void finish_event(const KParams& P, int64_t e, const A& mh, co
 // Each thread owns one event at a time; current variants and jamps live in a per-thread
 // global workspace (offset-major so a warp's accesses coalesce).  Used for processes whose
 // per-event store does not fit in shared memory.
+// One event, evaluated by one thread: the whole op table into the workspace view W, then the
+// colour sum, helicity sum and selections (or, in the tensor-core mode, the export of the jamps).
+__device__ inline void eval_event(const KParams& P, int64_t e, const double* pe, const WS& W,
+                                  const double* __restrict__ alphas, const double* __restrict__ rhel,
+                                  const double* __restrict__ rcol, double* __restrict__ me,
+                                  int32_t* __restrict__ selhel, int32_t* __restrict__ selcol,
+                                  double* __restrict__ mh_out, double* __restrict__ colw_out, int mode,
+                                  double* __restrict__ jexp, double* __restrict__ colw_exp) {
+  const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
+  const double scale = coupling_scale(P, alphas[e]);
+  for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = 0.0;
+  for (int iop = 0; iop < P.nops; ++iop) {
+    const Op o = load_op(P.ops, iop);
+    if (o.code == OP_AMP) {
+      const int2* fl = P.flows + o.cpl;
+      for (int ih = 0; ih < P.ngood; ++ih) {
+        const cx amp = group_amp(P.terms, o, P.good[ih], W);
+        const int jb = P.jamp_off + 2 * P.ncol * ih;
+        for (int f = 0; f < o.mass; ++f) {
+          const int2 q = __ldg(fl + f);
+          add_phase(W[jb + 2 * q.x], W[jb + 2 * q.x + 1], q.y, amp);
+        }
+      }
+      continue;
+    }
+    op_header(P, o, gs, pe, W);
+    const int nv = 1 << __popc(o.mdst);
+    for (int v = 0; v < nv; ++v) op_variant(P, o, v, gs, pe, W);
+  }
+  if (mode == MGX_MIXED_TF32) {
+    // export the jamps [ngood][ncol][re, im] and the colour weights for the tensor-core colour sum
+    const int nj = 2 * P.ncol * P.ngood;
+    for (int i = 0; i < nj; ++i) jexp[e * nj + i] = W[P.jamp_off + i];
+    for (int i = 0; i < P.ncol; ++i) {
+      double w = 0.0;
+      for (int ih = 0; ih < P.ngood; ++ih) {
+        const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
+        w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
+      }
+      colw_exp[e * P.ncol + i] = w * scale;
+    }
+    return;
+  }
+  for (int ih = 0; ih < P.ngood; ++ih) {
+    const int jb = P.jamp_off + 2 * P.ncol * ih;
+    const double mh = scale * quad_form([&](int k) { return W[jb + k]; }, P.colsym, P.colsym_f, P.ncol, mode);
+    W[P.mh_off + ih] = mh;
+    if (mh_out) mh_out[e * P.ngood + ih] = mh;
+  }
+  if (selcol || colw_out) {
+    for (int i = 0; i < P.ncol; ++i) {
+      double w = 0.0;
+      for (int ih = 0; ih < P.ngood; ++ih) {
+        const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
+        w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
+      }
+      w *= scale;
+      W[P.colw_off + i] = w;
+      if (colw_out) colw_out[e * P.ncol + i] = w;
+    }
+  }
+  finish_event(P, e, [&](int ih) { return W[P.mh_off + ih]; }, [&](int i) { return W[P.colw_off + i]; }, rhel, rcol,
+               me, selhel, selcol);
+}
+
+// stage the momenta of events [base, base + nb) (contiguous [events][npar][4]) through shared memory
+__device__ __forceinline__ void stage_momenta(const double* __restrict__ mom, int64_t base, int64_t nb, int npar4,
+                                              double* smem) {
+  const double2* src = reinterpret_cast<const double2*>(mom + base * npar4);
+  double2* dst = reinterpret_cast<double2*>(smem);
+  __syncthreads();
+  for (int i = threadIdx.x; i < (int)(nb * npar4 / 2); i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads)
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
@@ -156,71 +231,68 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const WS W{ws + tid, nthreads};
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nevt; base += nthreads) {
-    // stage this block's momenta (contiguous [events][npar][4]) through shared memory
-    const int64_t nb = min((int64_t)blockDim.x, nevt - base);
-    const double2* src = reinterpret_cast<const double2*>(mom + base * npar4);
-    double2* dst = reinterpret_cast<double2*>(smem);
-    __syncthreads();
-    for (int i = threadIdx.x; i < (int)(nb * npar4 / 2); i += blockDim.x) dst[i] = __ldg(src + i);
-    __syncthreads();
+    stage_momenta(mom, base, min((int64_t)blockDim.x, nevt - base), npar4, smem);
     const int64_t e = base + threadIdx.x;
     if (e >= nevt) continue;
-    const double* pe = smem + threadIdx.x * npar4;
-    const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
-    const double scale = coupling_scale(P, alphas[e]);
-    for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = 0.0;
-    for (int iop = 0; iop < P.nops; ++iop) {
-      const Op o = load_op(P.ops, iop);
-      if (o.code == OP_AMP) {
-        const int2* fl = P.flows + o.cpl;
-        for (int ih = 0; ih < P.ngood; ++ih) {
-          const cx amp = group_amp(P.terms, o, P.good[ih], W);
-          const int jb = P.jamp_off + 2 * P.ncol * ih;
-          for (int f = 0; f < o.mass; ++f) {
-            const int2 q = __ldg(fl + f);
-            add_phase(W[jb + 2 * q.x], W[jb + 2 * q.x + 1], q.y, amp);
-          }
-        }
-        continue;
-      }
-      op_header(P, o, gs, pe, W);
-      const int nv = 1 << __popc(o.mdst);
-      for (int v = 0; v < nv; ++v) op_variant(P, o, v, gs, pe, W);
+    eval_event(P, e, smem + threadIdx.x * npar4, W, alphas, rhel, rcol, me, selhel, selcol, mh_out, colw_out, mode,
+               jexp, colw_exp);
+  }
+}
+
+// ---------------------------------------------------------------- batched multi-process kernel
+// One persistent launch over several processes with uneven event counts.  Work items are
+// ranges of `events_per_item` events of one process, numbered process after process; CTAs
+// take items from a device counter (atomicAdd: no waits), so the load balances across processes.
+struct BatchIO {
+  int64_t nevt;
+  const double* mom;
+  const double* alphas;
+  const double* rhel;
+  const double* rcol;
+  double* me;
+  int32_t* selhel;
+  int32_t* selcol;
+};
+
+constexpr int kMaxBatch = 16;
+
+struct BatchIOArray {
+  BatchIO io[kMaxBatch];
+};
+
+struct BatchDesc {
+  int nproc, events_per_item, max_npar4;
+  int64_t item_start[kMaxBatch + 1];
+};
+
+__global__ void __launch_bounds__(kThreads)
+    batch_kernel(const KParams* __restrict__ params, const BatchIOArray io, const BatchDesc D,
+                 unsigned long long* __restrict__ counter, double* __restrict__ ws, int64_t nthreads, int mode) {
+  extern __shared__ double smem[];
+  __shared__ long long s_item;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const WS W{ws + tid, nthreads};
+  const int64_t nitems = D.item_start[D.nproc];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= nitems) break;
+    int p = 0;
+    while (item >= D.item_start[p + 1]) ++p;
+    const KParams& P = params[p];
+    const BatchIO b = io.io[p];
+    const int npar4 = 4 * P.npar;
+    const int64_t first = (item - D.item_start[p]) * D.events_per_item;
+    const int64_t last = min(first + (int64_t)D.events_per_item, b.nevt);
+    for (int64_t base = first; base < last; base += blockDim.x) {
+      stage_momenta(b.mom, base, min((int64_t)blockDim.x, last - base), npar4, smem);
+      const int64_t e = base + threadIdx.x;
+      if (e < last)
+        eval_event(P, e, smem + threadIdx.x * npar4, W, b.alphas, b.rhel, b.rcol, b.me, b.selhel, b.selcol, nullptr,
+                   nullptr, mode, nullptr, nullptr);
     }
-    if (mode == MGX_MIXED_TF32) {
-      // export the jamps [ngood][ncol][re, im] and the colour weights for the tensor-core colour sum
-      const int nj = 2 * P.ncol * P.ngood;
-      for (int i = 0; i < nj; ++i) jexp[e * nj + i] = W[P.jamp_off + i];
-      for (int i = 0; i < P.ncol; ++i) {
-        double w = 0.0;
-        for (int ih = 0; ih < P.ngood; ++ih) {
-          const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
-          w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
-        }
-        colw_exp[e * P.ncol + i] = w * scale;
-      }
-      continue;
-    }
-    for (int ih = 0; ih < P.ngood; ++ih) {
-      const int jb = P.jamp_off + 2 * P.ncol * ih;
-      const double mh = scale * quad_form([&](int k) { return W[jb + k]; }, P.colsym, P.colsym_f, P.ncol, mode);
-      W[P.mh_off + ih] = mh;
-      if (mh_out) mh_out[e * P.ngood + ih] = mh;
-    }
-    if (selcol || colw_out) {
-      for (int i = 0; i < P.ncol; ++i) {
-        double w = 0.0;
-        for (int ih = 0; ih < P.ngood; ++ih) {
-          const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
-          w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
-        }
-        w *= scale;
-        W[P.colw_off + i] = w;
-        if (colw_out) colw_out[e * P.ncol + i] = w;
-      }
-    }
-    finish_event(P, e, [&](int ih) { return W[P.mh_off + ih]; }, [&](int i) { return W[P.colw_off + i]; },
-                 rhel, rcol, me, selhel, selcol);
   }
 }
 
@@ -986,6 +1058,205 @@ double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) { return pr ? fp6
 double mgx_fp64_flops_per_event(const mgx_process* pr, int mode) { return pr ? fp64_work(pr, mode, true) : 0.0; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batched launch and autotuning
+struct mgx_batch {
+  int device = 0;
+  std::vector<mgx_process*> procs;
+  KParams* d_params = nullptr;
+  int blocks_per_sm = 4;
+  int events_per_item = 512;
+  int max_ws = 0, max_npar4 = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int kBatchMaxBlocksPerSm = 4;
+
+int batch_launch(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_t wsb, cudaStream_t st,
+                 int blocks_per_sm, int epi) {
+  const int n = (int)b->procs.size();
+  BatchDesc D{};
+  D.nproc = n;
+  D.events_per_item = epi;
+  D.max_npar4 = b->max_npar4;
+  D.item_start[0] = 0;
+  for (int p = 0; p < n; ++p) D.item_start[p + 1] = D.item_start[p] + (io[p].nevt + epi - 1) / epi;
+  BatchIO ios[kMaxBatch];
+  for (int p = 0; p < n; ++p) {
+    if (io[p].nevt < 0 || (io[p].nevt > 0 && (!io[p].momenta || !io[p].alpha_s || !io[p].me))) return MGX_ERR_INVALID_ARGUMENT;
+    if ((io[p].selhel && !io[p].rnd_hel) || (io[p].selcol && !io[p].rnd_col)) return MGX_ERR_INVALID_ARGUMENT;
+    if (reinterpret_cast<uintptr_t>(io[p].momenta) % 16 != 0) return MGX_ERR_INVALID_ARGUMENT;
+    ios[p] = BatchIO{io[p].nevt, io[p].momenta, io[p].alpha_s, io[p].rnd_hel, io[p].rnd_col, io[p].me, io[p].selhel,
+                     io[p].selcol};
+  }
+  if (D.item_start[n] == 0) return MGX_OK;
+  const int64_t nt = (int64_t)sm_count(b->device) * blocks_per_sm * kThreads;
+  const size_t need = 256 + (size_t)nt * b->max_ws * sizeof(double);
+  if (!ws || wsb < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MGX_ERR_WORKSPACE_TOO_SMALL;
+  unsigned long long* counter = (unsigned long long*)ws;
+  double* w = (double*)((char*)ws + 256);
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st) != cudaSuccess) return MGX_ERR_CUDA;
+  BatchIOArray arr;
+  for (int p = 0; p < n; ++p) arr.io[p] = ios[p];
+  const size_t shm = (size_t)kThreads * b->max_npar4 * sizeof(double);
+  batch_kernel<<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(b->d_params, arr, D, counter, w, nt, mode);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int mgx_batch_create(mgx_process* const* procs, int nproc, mgx_batch** out) {
+  if (!procs || !out || nproc < 1 || nproc > kMaxBatch) return MGX_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  for (int p = 0; p < nproc; ++p)
+    if (!procs[p] || procs[p]->device != procs[0]->device) return MGX_ERR_DEVICE_MISMATCH;
+  mgx_batch* b = new mgx_batch();
+  b->device = procs[0]->device;
+  std::vector<KParams> kp;
+  for (int p = 0; p < nproc; ++p) {
+    b->procs.push_back(procs[p]);
+    kp.push_back(procs[p]->kp);
+    b->max_ws = std::max(b->max_ws, procs[p]->kp.ws_doubles);
+    b->max_npar4 = std::max(b->max_npar4, 4 * procs[p]->kp.npar);
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(b->device);
+  const bool ok = cudaMalloc(&b->d_params, sizeof(KParams) * nproc) == cudaSuccess &&
+                  cudaMemcpy(b->d_params, kp.data(), sizeof(KParams) * nproc, cudaMemcpyHostToDevice) == cudaSuccess;
+  cudaSetDevice(cur);
+  if (!ok) {
+    mgx_batch_destroy(b);
+    return MGX_ERR_CUDA;
+  }
+  *out = b;
+  return MGX_OK;
+}
+
+extern "C" void mgx_batch_destroy(mgx_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_params);
+  delete b;
+}
+
+extern "C" int mgx_batch_workspace_bytes(const mgx_batch* b, size_t* bytes) {
+  if (!b || !bytes) return MGX_ERR_INVALID_ARGUMENT;
+  *bytes = 256 + (size_t)sm_count(b->device) * kBatchMaxBlocksPerSm * kThreads * b->max_ws * sizeof(double);
+  return MGX_OK;
+}
+
+extern "C" int mgx_batch_compute(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_t wsb, void* stream) {
+  if (!b || !io) return MGX_ERR_INVALID_ARGUMENT;
+  if (mode != MGX_FP64 && mode != MGX_MIXED_FP32) return MGX_ERR_UNSUPPORTED_MODE;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return MGX_ERR_CUDA;
+  if (cur != b->device) return MGX_ERR_DEVICE_MISMATCH;
+  return batch_launch(b, io, mode, ws, wsb, (cudaStream_t)stream, b->blocks_per_sm, b->events_per_item);
+}
+
+extern "C" int mgx_batch_capture(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_t wsb, void* stream) {
+  if (!b || !io || !stream) return MGX_ERR_INVALID_ARGUMENT;
+  if (mode != MGX_FP64 && mode != MGX_MIXED_FP32) return MGX_ERR_UNSUPPORTED_MODE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MGX_ERR_CUDA;
+  const int rc = batch_launch(b, io, mode, ws, wsb, st, b->blocks_per_sm, b->events_per_item);
+  cudaGraph_t g = nullptr;
+  const bool ended = cudaStreamEndCapture(st, &g) == cudaSuccess;
+  if (rc != MGX_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (!ended || !g) return MGX_ERR_CUDA;
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return MGX_ERR_CUDA;
+  return MGX_OK;
+}
+
+extern "C" int mgx_batch_replay(mgx_batch* b, void* stream) {
+  if (!b || !b->exec) return MGX_ERR_INVALID_ARGUMENT;
+  return cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+extern "C" int mgx_batch_autotune(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_t wsb, void* stream,
+                                  int* blocks_per_sm, int* events_per_item) {
+  if (!b || !io) return MGX_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bb = b->blocks_per_sm, be = b->events_per_item;
+  const int bps_c[] = {2, 4};
+  const int epi_c[] = {128, 512, 2048};
+  for (int bps : bps_c)
+    for (int epi : epi_c) {
+      int rc = batch_launch(b, io, mode, ws, wsb, st, bps, epi);   // warm-up
+      if (rc != MGX_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2; ++r) batch_launch(b, io, mode, ws, wsb, st, bps, epi);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return MGX_ERR_CUDA; }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bb = bps; be = epi; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->blocks_per_sm = bb;
+  b->events_per_item = be;
+  if (blocks_per_sm) *blocks_per_sm = bb;
+  if (events_per_item) *events_per_item = be;
+  return MGX_OK;
+}
+
+extern "C" int mgx_process_autotune(mgx_process* pr, int64_t nevt, const double* momenta, const double* alpha_s,
+                                    int mode, void* workspace, size_t workspace_bytes, void* stream, int* kernel,
+                                    int* blocks_per_sm, double* me_scratch) {
+  if (!pr || nevt <= 0 || !momenta || !alpha_s || !me_scratch) return MGX_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  struct Cand { int kernel, bps; };
+  std::vector<Cand> cands = {{MGX_KERNEL_THREAD, 2}, {MGX_KERNEL_THREAD, 4}};
+  if (cta_usable(pr, pr->kp) && mode != MGX_MIXED_TF32) cands.push_back({MGX_KERNEL_CTA, 4});
+  const int save_k = pr->kernel, save_b = pr->blocks_per_sm;
+  float best = 1e30f;
+  Cand pick{save_k, save_b};
+  for (const Cand& c : cands) {
+    pr->kernel = c.kernel;
+    pr->blocks_per_sm = c.bps;
+    size_t need = 0;
+    mgx_workspace_bytes(pr, nevt, mode, &need);
+    if (need > workspace_bytes) continue;
+    int rc = mgx_compute(pr, nevt, momenta, alpha_s, nullptr, nullptr, me_scratch, nullptr, nullptr, mode, workspace,
+                         workspace_bytes, stream);
+    if (rc != MGX_OK) continue;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2; ++r)
+      mgx_compute(pr, nevt, momenta, alpha_s, nullptr, nullptr, me_scratch, nullptr, nullptr, mode, workspace,
+                  workspace_bytes, stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; pick = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pr->kernel = pick.kernel;
+  pr->blocks_per_sm = pick.bps;
+  if (kernel) *kernel = pick.kernel;
+  if (blocks_per_sm) *blocks_per_sm = pick.bps;
+  return best < 1e30f ? MGX_OK : MGX_ERR_CUDA;
+}
 
 // ------------------------------------------------------------------ allocation-free entry point
 // Some callers cannot allocate device memory at the point where they evaluate matrix elements:

@@ -38,6 +38,7 @@ WORKLOADS = {
     "ggttg": Workload("ggttg", "g g > t t~ g", 1500.0, 1 << 20, 8, 9),
     "ggttgg": Workload("ggttgg", "g g > t t~ g g", 1500.0, 1 << 20, 2, 3),
     "ggttggg": Workload("ggttggg", "g g > t t~ g g g", 1500.0, 1 << 18, 4, 5),
+    "gu_tataggu": Workload("gu_tataggu", "g u~ > ta+ ta- g g u~", 1500.0, 1 << 16, 10, 11),
 }
 
 

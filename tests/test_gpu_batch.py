@@ -1,0 +1,78 @@
+"""Batched multi-process launch, CUDA-graph replay and autotuning: results identical to the
+per-process entry point."""
+import numpy as np
+import pytest
+
+from phasespace import WORKLOADS, make_inputs
+
+pytestmark = pytest.mark.gpu
+
+SET = [("ggtt", 3000), ("ggttg", 700), ("ggttgg", 300), ("gu_tataggu", 129)]
+
+
+def _setup():
+    import torch
+    import paper_2503_21935_gb300 as pkg
+    dev = torch.device("cuda:0")
+    procs, inputs, outs, refs = [], [], [], []
+    for name, n in SET:
+        wl = WORKLOADS[name]
+        mom, a, rh, rc = make_inputs(wl, n)
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        inp = (t(mom), t(a), t(rh), t(rc))
+        p = pkg.Process(wl.process)
+        ref = p.compute(*inp)
+        procs.append(p)
+        inputs.append(inp)
+        outs.append({"me": torch.zeros(n, dtype=torch.float64, device=dev),
+                     "selhel": torch.zeros(n, dtype=torch.int32, device=dev),
+                     "selcol": torch.zeros(n, dtype=torch.int32, device=dev)})
+        refs.append(ref)
+    return pkg, procs, inputs, outs, refs
+
+
+def _same(outs, refs):
+    import torch
+    for o, r in zip(outs, refs):
+        assert torch.equal(o["me"], r["me"])
+        assert torch.equal(o["selhel"], r["selhel"]) and torch.equal(o["selcol"], r["selcol"])
+
+
+def test_batch_equals_per_process():
+    import torch
+    pkg, procs, inputs, outs, refs = _setup()
+    b = pkg.Batch(procs)
+    b.compute(inputs, outs)
+    torch.cuda.synchronize()
+    _same(outs, refs)
+
+
+def test_batch_graph_replay_and_autotune():
+    import torch
+    pkg, procs, inputs, outs, refs = _setup()
+    b = pkg.Batch(procs)
+    bps, epi = b.autotune(inputs, outs)
+    assert bps in (2, 4) and epi in (128, 512, 2048)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        b.capture(inputs, outs, st)
+        for _ in range(2):
+            for o in outs:
+                o["me"].zero_()
+            b.replay(st)
+    st.synchronize()
+    _same(outs, refs)
+
+
+def test_process_autotune_keeps_results():
+    import torch
+    import paper_2503_21935_gb300 as pkg
+    wl = WORKLOADS["ggttg"]
+    mom, a, _, _ = make_inputs(wl, 20000)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    p = pkg.Process(wl.process)
+    ref = p.compute(t(mom), t(a))["me"].clone()
+    k, bps = p.autotune(t(mom), t(a))
+    assert k in (1, 2)
+    got = p.compute(t(mom), t(a))["me"]
+    assert torch.equal(got, ref) or (got / ref - 1).abs().max().item() < 1e-14

@@ -37,7 +37,7 @@ def _run(proc, mom, a, rh, rc, mode=0):
     return {k: v.cpu().numpy() for k, v in r.items()}
 
 
-CASES = [("eemumu", 300), ("ggtt", 300), ("ggttg", 260), ("ggttgg", 160), ("ggttggg", 20)]
+CASES = [("eemumu", 300), ("ggtt", 300), ("ggttg", 260), ("ggttgg", 160), ("ggttggg", 20), ("gu_tataggu", 140)]
 KERNELS = {"thread": 1, "cta": 2}
 
 
@@ -69,7 +69,7 @@ def test_parity_fp64(name, nevt, kernel):
     assert np.array_equal(got["selcol"][~tie_c], ref["selcol"][~tie_c])
 
 
-@pytest.mark.parametrize("name", ["eemumu", "ggtt", "ggttg", "ggttgg"])
+@pytest.mark.parametrize("name", ["eemumu", "ggtt", "ggttg", "ggttgg", "gu_tataggu"])
 def test_helicity_filter_matches_oracle(name):
     wl = WORKLOADS[name]
     proc = _proc(wl.process)

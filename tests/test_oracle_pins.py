@@ -227,3 +227,14 @@ def test_selection_frequencies_follow_weights():
     chi2 = ((counts[m] - expect[m]) ** 2 / expect[m]).sum()
     assert chi2 < 3 * m.sum() + 30
     assert np.all(counts[~m] <= 20)
+
+
+def test_ew_qcd_process_colour_and_gauge():
+    """g u~ > ta+ ta- g g u~ (photon/Z to a massive tau pair, one quark line, three gluons):
+    flow decomposition vs the explicit colour sum, and the gluon Ward identity (no top width)."""
+    me = get("g u~ > ta+ ta- g g u~")
+    p, a, _, _ = make_inputs(WORKLOADS["gu_tataggu"], 4)
+    assert np.abs(me.me_bruteforce_colour(p[:2], a[:2]) / me.evaluate(p[:2], a[:2])["me"] - 1).max() < 1e-13
+    J = me.jamps(p, a)
+    for leg in (0, 4, 5):
+        assert np.abs(me.jamps(p, a, gauge_leg=leg)).max() / (np.abs(J).max() * p[:, leg, 0].max()) < 1e-13
