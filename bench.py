@@ -39,7 +39,7 @@ def _args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed_fp32"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed_fp32", "mixed_tf32"])
     ap.add_argument("--impl", default="mgx", choices=["mgx", "reference"])
     ap.add_argument("--nevt", type=int, default=NEVT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -384,7 +384,7 @@ def run_gpu(args):
         line = {"metric": METRIC if args.mode == "fp64" else METRIC.replace("FP64", "mixed FP32 colour sum"),
                 "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.mode == "fp64" else "f64+f32", "data": "synthetic",
+                "dtype": {"fp64": "f64", "mixed_fp32": "f64+f32", "mixed_tf32": "f64+tf32"}[args.mode], "data": "synthetic",
                 "config": {"workload": f"g g > t t~ g g, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, "
                                        "alpha_s=0.118", "process": wl.process, "nevt_per_gpu": nevt,
                            "mode": args.mode, "ngood": proc.ngood, "ndiagrams": proc.ndiagrams,

@@ -35,7 +35,7 @@ struct mgx_program_desc {
   int ws_doubles, ndiag, nterm, avg_den;
   int gs_power;          // power of g_s of every amplitude (vertices are evaluated with g_s = 1)
   int col_den;           // common denominator of the colour matrix
-  int counts[10];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil; current ops; amp terms; amp flows; amp groups
+  int counts[11];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows, groups
   struct {
     int nops;
     const int32_t* ops;
@@ -1042,11 +1042,12 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   const double ngood = (double)pr->good.size();
   const double n = pr->prog->ncol;
   struct K { double fma, mul, add; };
-  const K ffv_f{56, 24, 10}, ffv_v{24, 24, 24}, bil{16, 16, 24}, vvv{58, 14, 0}, vvvv{52, 16, 0},
-      term{14, 2, 2}, flow{0, 0, 2};
+  const K ffv_f{56, 24, 10}, ffv_v{24, 24, 24}, bil{16, 16, 24}, rbil{24, 8, 8}, vvv{58, 14, 0},
+      vvvv{52, 16, 0}, term{14, 2, 2}, flow{0, 0, 2};
   auto w = [&](const K& k) { return flops ? 2 * k.fma + k.mul + k.add : k.fma + k.mul + k.add; };
-  double t = w(ffv_f) * (c[0] + c[1]) + w(ffv_v) * c[2] + w(vvv) * c[3] + w(vvvv) * c[4] + w(bil) * c[5];
-  t += ngood * (w(term) * c[7] + w(flow) * c[8]);
+  double t = w(ffv_f) * (c[0] + c[1]) + w(ffv_v) * c[2] + w(vvv) * c[3] + w(vvvv) * c[4] + w(bil) * c[5] +
+             w(rbil) * c[6];
+  t += ngood * (w(term) * c[8] + w(flow) * c[9]);
   if (mode == MGX_FP64) t += ngood * (flops ? 2 * n * n + 4 * n : n * n + 3 * n);  // quadratic form
   else if (!flops) t += ngood * 2 * n;                                              // f64 -> f32 conversions
   t += ngood * (flops ? 4 * n : 2 * n);                                             // colour weights

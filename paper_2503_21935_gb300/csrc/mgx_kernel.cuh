@@ -20,7 +20,7 @@
 
 namespace mgx {
 
-enum { OP_EXT = 1, OP_FFV_F = 2, OP_FFV_FB = 3, OP_FFV_V = 4, OP_VVV = 5, OP_VVVV = 6, OP_AMP = 7, OP_BIL = 8 };
+enum { OP_EXT = 1, OP_FFV_F = 2, OP_FFV_FB = 3, OP_FFV_V = 4, OP_VVV = 5, OP_VVVV = 6, OP_AMP = 7, OP_BIL = 8, OP_RBIL = 9 };
 enum { EXT_U = 0, EXT_V = 1, EXT_UBAR = 2, EXT_VBAR = 3, EXT_EPS_IN = 4, EXT_EPS_OUT = 5 };
 enum { CPL_GS = 1, CPL_CHIRAL = 2 };
 
@@ -32,7 +32,7 @@ constexpr int MAXNPAR = 8;
 struct KParams {
   const int4* ops;       // 4 int4 (16 int32 fields) per op
   const int2* flows;     // (colour flow, phase code 0..3 for 1, i, -1, -i)
-  const int4* terms;     // 2 int4 per diagram term: (Q base, Q mask, V base, V mask), (phase, -, -, -)
+  const int4* terms;     // 2 int4 per diagram term: (bilinear base, mask, other base, mask), (phase, kind, -, -)
   const double* colsym;  // ncol*ncol: C_ii on the diagonal, 2 C_ij above it
   const float* colsym_f;
   int nops, ncol, npar, nin, ngood;

@@ -69,8 +69,8 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
     W.storek(o.dst, k);
     return;
   }
-  if (o.code == OP_BIL) {
-    // root bilinear: no propagator; a non-chiral coupling is folded into the prefactor
+  if (o.code == OP_BIL || o.code == OP_RBIL) {
+    // root bilinears: no propagator; a non-chiral coupling is folded into the prefactor
     cx cl, cr;
     bool chiral;
     coupling(P, o.cpl, gs, cl, cr, chiral);
@@ -258,6 +258,39 @@ __device__ inline void var_ffv_v(const KParams& P, const Op& o, int v, double gs
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
+// row bilinear R = pref psibar_root Vslash (cL PL + cR PR): a row spinor, closed later by R . psi
+template <class S>
+__device__ inline void var_rbil(const KParams& P, const Op& o, int v, double gs, const S& W) {
+  const int hb = pdep(v, o.mdst);
+  cx pb[4], V[4];
+  W.load4(o.va + 8 * pext(hb, o.ma), pb);
+  W.load4(o.vb + 8 * pext(hb, o.mb), V);
+  const cx pref = cx{W[o.dst + 4], W[o.dst + 5]};
+  const Slash Sl = slash(V);
+  // psibar Vslash = (psibar_l B, psibar_u A)
+  cx x[4] = {cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00)), cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01)),
+             cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00)), cfma(pb[1], Sl.a11, cmul(pb[0], Sl.a01))};
+  if (P.cplflags[o.cpl] & CPL_CHIRAL) {
+    cx cl, cr;
+    bool ch;
+    coupling(P, o.cpl, gs, cl, cr, ch);
+    x[0] = cmul(cl, x[0]); x[1] = cmul(cl, x[1]);
+    x[2] = cmul(cr, x[2]); x[3] = cmul(cr, x[3]);
+  }
+  cx out[4];
+  if (pref.r == 0.0 && pref.i == 1.0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = cx{-x[j].i, x[j].r};
+  } else if (pref.r == 0.0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = cx{-pref.i * x[j].i, pref.i * x[j].r};
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = cmul(pref, x[j]);
+  }
+  W.store4(o.dst + 6 + 8 * v, out);
+}
+
 // J^r = i [ (e1.e2) s(k1-k2)^r + e2^r (s(k2-k3).e1) + e1^r (s(k3-k1).e2) ],  s = -g_s/P^2
 template <class S>
 __device__ inline void var_vvv(const KParams& P, const Op& o, int v, const S& W) {
@@ -315,6 +348,7 @@ __device__ inline void op_variant(const KParams& P, const Op& o, int v, double g
     case OP_FFV_FB: var_ffv_fb(P, o, v, gs, W); break;
     case OP_FFV_V:
     case OP_BIL: var_ffv_v(P, o, v, gs, W); break;   // the bilinear is the vertex current without propagator
+    case OP_RBIL: var_rbil(P, o, v, gs, W); break;
     case OP_VVV: var_vvv(P, o, v, W); break;
     default: var_vvvv(P, o, v, W); break;
   }
@@ -332,19 +366,29 @@ __device__ __forceinline__ void add_phase(double& jr, double& ji, int code, cx a
 
 // ================================================================ diagram amplitudes
 // A group of diagram terms sharing one colour vector (up to a phase): sum over the group of
-// phase_t * Q_t(h) . V_t(h), where Q_t is the root bilinear psibar gamma^mu (cL PL + cR PR) psi
-// of the term's column current (couplings included) and V_t its vector current.
-// AMP op fields: aux = first term, aux2 = terms, cpl = first flow, mass = flows.
+// phase_t * amp_t(h), where amp_t = Q . V (kind 0: column bilinear Q^mu = psibar gamma^mu (..) psi_C
+// of the term's column current, Minkowski dot with its vector current) or amp_t = R . psi_C
+// (kind 1: row bilinear R = psibar Vslash (..), spinor dot with the column current); couplings
+// are inside the bilinears.  AMP op fields: aux = first term, aux2 = terms, cpl = first flow, mass = flows.
 template <class S>
 __device__ __forceinline__ cx group_amp(const int4* terms, const Op& o, int h, const S& W) {
   cx acc{0.0, 0.0};
   for (int t = 0; t < o.aux2; ++t) {
     const int4 a = __ldg(terms + 2 * (o.aux + t));
-    const int ph = __ldg(terms + 2 * (o.aux + t) + 1).x;
-    cx Q[4], V[4];
-    W.load4(a.x + 8 * pext(h, a.y), Q);
-    W.load4(a.z + 8 * pext(h, a.w), V);
-    add_phase(acc.r, acc.i, ph, mdot(Q, V));
+    const int4 b = __ldg(terms + 2 * (o.aux + t) + 1);
+    cx X[4], Y[4];
+    W.load4(a.x + 8 * pext(h, a.y), X);
+    W.load4(a.z + 8 * pext(h, a.w), Y);
+    cx amp;
+    if (b.y == 0) {
+      amp = mdot(X, Y);
+    } else {
+      amp = cmul(X[0], Y[0]);
+      amp = cfma(X[1], Y[1], amp);
+      amp = cfma(X[2], Y[2], amp);
+      amp = cfma(X[3], Y[3], amp);
+    }
+    add_phase(acc.r, acc.i, b.x, amp);
   }
   return acc;
 }

@@ -21,7 +21,7 @@ from . import sm
 from .colour import colour_matrix
 from .diagrams import Diagrams, Current
 
-OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP, OP_BIL = 1, 2, 3, 4, 5, 6, 7, 8
+OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP, OP_BIL, OP_RBIL = 1, 2, 3, 4, 5, 6, 7, 8, 9
 EXT_U, EXT_V, EXT_UBAR, EXT_VBAR, EXT_EPS_IN, EXT_EPS_OUT = 0, 1, 2, 3, 4, 5
 NFIELD = 16
 
@@ -61,7 +61,10 @@ def _bit(npar, leg):
     return 1 << (npar - 1 - leg)
 
 
-HEADER = {"EXT": 4, "FFV_F": 6, "FFV_FB": 6, "FFV_V": 6, "VVV": 18, "VVVV": 6, "BIL": 6}
+HEADER = {"EXT": 4, "FFV_F": 6, "FFV_FB": 6, "FFV_V": 6, "VVV": 18, "VVVV": 6, "BIL": 6, "RBIL": 6}
+# float64 instructions per variant of the two root bilinears (column: Q = psibar gamma psi_col;
+# row: R = psibar Vslash), used to choose between them
+BIL_COST = {"BIL": 56, "RBIL": 40}
 SMEM_STORE_BUDGET = 96 * 1024     # bytes of shared memory for one event's current store
 
 
@@ -109,22 +112,40 @@ class _Builder:
         self._add_bilinears()
 
     def _add_bilinears(self):
-        """Root bilinears Q^mu = psibar_root gamma^mu (cL PL + cR PR) psi_col, one per (column
-        current, coupling): every diagram term is then Q . V, so the fermion-line algebra at the
-        root vertex is done once per (root, column) helicity pair instead of per full helicity."""
+        """Close every diagram term at the root vertex through a bilinear.  A term (column current C,
+        vector current V) is psibar_root Vslash (cL PL + cR PR) psi_C; it is evaluated either as
+        Q_C . V with the column bilinear Q_C^mu = psibar gamma^mu (..) psi_C (one per C and coupling,
+        2^(1+|C|) variants) or as R_V . psi_C with the row bilinear R_V = psibar Vslash (..) (one per V
+        and coupling, 2^(1+|V|) variants).  The set of bilinears is a minimum-weight vertex cover of
+        the bipartite (C, V) graph of the terms (exact, by max-flow / min-cut), so the cheaper side
+        is built wherever a current is shared by many terms."""
         D = self.D
-        key_of = {}
+        nb = lambda m: bin(m).count("1")
+        info = []
         for t in D.terms:
             col, vec = D.currents[t.col], D.currents[t.vec]
-            k = self.coupling_index(vec.flav, col.flav)
-            key = (t.col, k)
-            if key not in key_of:
-                c = Current(len(D.currents), D.root_current.mask | col.mask, "BIL", "BIL",
-                            children=(self.ROOT, t.col))
-                c.cpl = k
-                D.currents.append(c)
-                key_of[key] = c.id
-            t.bil = key_of[key]
+            info.append((t, (t.col, self.coupling_index(vec.flav, col.flav)), (t.vec, self.coupling_index(vec.flav, col.flav))))
+        Cs = sorted({c for _, c, _ in info})
+        Vs = sorted({v for _, _, v in info})
+        wC = {c: BIL_COST["BIL"] * 2 ** (1 + nb(D.currents[c[0]].mask)) for c in Cs}
+        wV = {v: BIL_COST["RBIL"] * 2 ** (1 + nb(D.currents[v[0]].mask)) for v in Vs}
+        cover_C, cover_V = _bipartite_min_cover(Cs, Vs, {(c, v) for _, c, v in info}, wC, wV)
+        made = {}
+        for t, c, v in info:
+            if c in cover_C:
+                key, kind, other = ("BIL", c), "BIL", t.vec
+            else:
+                key, kind, other = ("RBIL", v), "RBIL", t.col
+            if key not in made:
+                src = t.col if kind == "BIL" else t.vec
+                node = Current(len(D.currents), D.root_current.mask | D.currents[src].mask, kind, kind,
+                               children=(self.ROOT, src))
+                node.cpl = key[1][1]
+                D.currents.append(node)
+                made[key] = node.id
+            t.bil = made[key]
+            t.other = other
+            t.kind = 0 if kind == "BIL" else 1
 
     def hmask(self, m):
         return sum(_bit(self.npar, p) for p in range(self.npar) if m >> p & 1)
@@ -194,6 +215,8 @@ class _Builder:
             op[0], op[11] = OP_VVVV, c.struct
         elif c.op == "BIL":
             op[0], op[9] = OP_BIL, c.cpl
+        elif c.op == "RBIL":
+            op[0], op[9] = OP_RBIL, c.cpl
         else:
             raise ValueError(c.op)
         return op
@@ -209,14 +232,63 @@ class _Builder:
         op[12] = len(tis)
         for ti, ph in zip(tis, phases):
             t = D.terms[ti]
-            bil, vec = D.currents[t.bil], D.currents[t.vec]
-            terms += [self.varbase(t.bil, offset), self.hmask(bil.mask), self.varbase(t.vec, offset),
-                      self.hmask(vec.mask), ph, 0, 0, 0]
+            bil, oth = D.currents[t.bil], D.currents[t.other]
+            terms += [self.varbase(t.bil, offset), self.hmask(bil.mask), self.varbase(t.other, offset),
+                      self.hmask(oth.mask), ph, t.kind, 0, 0]
         op[9] = len(flows) // 2
         op[10] = len(fl)
         for f, ph in fl:
             flows += [f, ph]
         return op
+
+
+def _bipartite_min_cover(left, right, edges, wl, wr):
+    """Minimum-weight vertex cover of a bipartite graph (every edge needs one endpoint chosen):
+    the source side of a minimum s-t cut with capacities wl (source -> left), wr (right -> sink)
+    and infinite left -> right edges (Konig / max-flow min-cut).  Edmonds-Karp max flow."""
+    import collections
+    S, T = ("s",), ("t",)
+    cap = collections.defaultdict(float)
+    adj = collections.defaultdict(set)
+
+    def link(a, b, c):
+        cap[(a, b)] += c
+        adj[a].add(b)
+        adj[b].add(a)
+    inf = float("inf")
+    for x in left:
+        link(S, ("L", x), wl[x])
+    for y in right:
+        link(("R", y), T, wr[y])
+    for x, y in edges:
+        link(("L", x), ("R", y), inf)
+    while True:
+        parent = {S: None}
+        q = collections.deque([S])
+        while q and T not in parent:
+            u = q.popleft()
+            for w in adj[u]:
+                if w not in parent and cap[(u, w)] > 0:
+                    parent[w] = u
+                    q.append(w)
+        if T not in parent:
+            break
+        f, w = inf, T
+        while parent[w] is not None:
+            f = min(f, cap[(parent[w], w)])
+            w = parent[w]
+        w = T
+        while parent[w] is not None:
+            cap[(parent[w], w)] -= f
+            cap[(w, parent[w])] += f
+            w = parent[w]
+    reach = set(parent)          # residual-reachable from the source after the last search
+    cover_left = {x for x in left if ("L", x) not in reach}
+    cover_right = {y for y in right if ("R", y) in reach}
+    for x, y in edges:
+        if x not in cover_left and y not in cover_right:
+            raise RuntimeError("vertex cover does not cover every term")
+    return cover_left, cover_right
 
 
 def _term_groups(D):
@@ -253,7 +325,7 @@ def _term_groups(D):
 
 def _closure(D, ti):
     out = set()
-    st = [D.terms[ti].bil, D.terms[ti].vec]
+    st = [D.terms[ti].bil, D.terms[ti].other]
     while st:
         x = st.pop()
         if x in out:
@@ -282,7 +354,7 @@ def _dfs_schedule(B):
     for gi, (tis, _, _) in enumerate(groups):
         for ti in tis:
             emit(D.terms[ti].bil)
-            emit(D.terms[ti].vec)
+            emit(D.terms[ti].other)
         order.append(("A", gi))
 
     def uses(item):
@@ -291,7 +363,7 @@ def _dfs_schedule(B):
             return list(cur[x].children)
         out = []
         for ti in groups[x][0]:
-            out += [D.terms[ti].bil, D.terms[ti].vec]
+            out += [D.terms[ti].bil, D.terms[ti].other]
         return out
     last = {}
     for pos, item in enumerate(order):
@@ -417,10 +489,10 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     npar = D.npar
     B = _Builder(D)
     ops, flows, terms, top = _dfs_schedule(B)
-    counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, bil=0, amp=0, amp_flows=0,
-                  var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0)
+    counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, bil=0, rbil=0, amp=0, amp_flows=0,
+                  var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0, var_rbil=0)
     name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
-            OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil"}
+            OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil", OP_RBIL: "rbil"}
     for op in ops:
         k = name[op[0]]
         counts[k] += 1
