@@ -7,7 +7,7 @@ alpha_s and random numbers already resident in HBM): external wavefunctions,
 every diagram amplitude, jamps, colour sum, helicity sum, helicity and colour
 selection.  Metric: |M|^2 evaluations per second (whole job).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|mixed_fp32] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|mixed_fp32|mixed_tf32|mixed_bf16x3|float] [--impl reference]
 
 Under torchrun each rank processes its own 2^20 events (weak scaling, no data
 collective); rank 0 prints one JSON line.  --impl reference times the float64
@@ -32,6 +32,8 @@ METRIC = "gg->ttgg |M|^2 evals/s (FP64)"
 # FP64 pipe: 152 SMs x 2 DFMA/clk/SM (measured: 1.20 TFLOP/s at 1995 MHz) x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_PEAK_GINST = 152 * 2 * 2.070e9 / 1e9       # float64 instructions per second, any of fma/mul/add
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP32_PEAK_GINST = 152 * 128 * 2.070e9 / 1e9
 
 
 def _args():
@@ -39,7 +41,7 @@ def _args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed_fp32", "mixed_tf32"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed_fp32", "mixed_tf32", "mixed_bf16x3", "float"])
     ap.add_argument("--impl", default="mgx", choices=["mgx", "reference"])
     ap.add_argument("--nevt", type=int, default=NEVT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -204,9 +206,10 @@ def _timed(fn, steps, warmup, stream):
 
 
 def extra_modes(pkg, proc, M, A, RH, RC, nevt, stream):
-    """ggttgg at 2^20 events with the float32 SIMT and tensor-core (tcgen05 tf32) colour sums."""
+    """ggttgg at 2^20 events with the float32 SIMT and tensor-core (tcgen05 tf32, bf16x3) colour sums,
+    and the float32 path (amplitudes and colour sum)."""
     out = {}
-    for name in ("mixed_fp32", "mixed_tf32"):
+    for name in ("mixed_fp32", "mixed_tf32", "mixed_bf16x3", "float"):
         mode = pkg.MODES[name]
         ms = _timed(lambda: proc.compute(M, A, RH, RC, mode=mode, stream=stream), 3, 1, stream)
         out[name] = {"value": nevt / (ms * 1e-3), "unit": "events/s", "ms_per_step": ms}
@@ -214,7 +217,7 @@ def extra_modes(pkg, proc, M, A, RH, RC, nevt, stream):
 
 
 def extra_ggttggg(pkg, dev, stream):
-    """g g > t t~ g g g, 2^18 events, float64 and mixed float32 colour sum."""
+    """g g > t t~ g g g, 2^18 events: float64, mixed float32 colour sum, float32 path."""
     import numpy as np
     import torch
     from phasespace import WORKLOADS, make_inputs
@@ -224,7 +227,7 @@ def extra_ggttggg(pkg, dev, stream):
     M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
     proc = pkg.Process(wl.process, device=dev.index)
     out = {"nevt": wl.nevt, "ndiagrams": proc.ndiagrams, "ncol": proc.ncol, "ngood": proc.ngood}
-    for name in ("fp64", "mixed_fp32"):
+    for name in ("fp64", "mixed_fp32", "float"):
         mode = pkg.MODES[name]
         ms = _timed(lambda: proc.compute(M, A, RH, RC, mode=mode, stream=stream), 1, 1, stream)
         out[name] = {"value": wl.nevt / (ms * 1e-3), "unit": "events/s", "ms_per_step": ms,
@@ -376,30 +379,40 @@ def run_gpu(args):
     d2h = sum(x.numel() * x.element_size() for x in (hme, hsh, hsc))
 
     if rank == 0:
-        flops = proc.fp64_flops_per_event(mode) * nevt         # algorithmic float64 flops per launch
-        insts = proc.fp64_ops_per_event(mode) * nevt           # float64 instructions per launch
+        f32 = args.mode == "float"                              # same arithmetic on the float32 pipe
+        flops = proc.fp64_flops_per_event(0 if f32 else mode) * nevt   # algorithmic flops per launch
+        insts = proc.fp64_ops_per_event(0 if f32 else mode) * nevt     # instructions per launch
         launch_s = statistics.mean(launch_ms) * 1e-3
         achieved = flops / launch_s / 1e12
+        peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+        peak_inst = FP32_PEAK_GINST if f32 else FP64_PEAK_GINST
+        tc_chunks = -(-nevt * proc.ngood * proc.ncol * 16 // (2 << 30)) if args.mode.startswith("mixed_") and \
+            args.mode != "mixed_fp32" else 0
         per_evt = _traffic_per_event("me_kernel", WORKLOAD)
-        line = {"metric": METRIC if args.mode == "fp64" else METRIC.replace("FP64", "mixed FP32 colour sum"),
+        line = {"metric": METRIC.replace("FP64", {"fp64": "FP64", "mixed_fp32": "mixed FP32 colour sum",
+                                                   "mixed_tf32": "tcgen05 TF32 colour sum",
+                                                   "mixed_bf16x3": "tcgen05 BF16x3 colour sum",
+                                                   "float": "FP32"}[args.mode]),
                 "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "mixed_fp32": "f64+f32", "mixed_tf32": "f64+tf32"}[args.mode], "data": "synthetic",
+                "dtype": {"fp64": "f64", "mixed_fp32": "f64+f32", "mixed_tf32": "f64+tf32", "mixed_bf16x3": "f64+bf16",
+                          "float": "f32"}[args.mode], "data": "synthetic",
                 "config": {"workload": f"g g > t t~ g g, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, "
                                        "alpha_s=0.118", "process": wl.process, "nevt_per_gpu": nevt,
                            "mode": args.mode, "ngood": proc.ngood, "ndiagrams": proc.ndiagrams,
                            "ncol": proc.ncol, "l2": "inputs larger than L2 (192 MiB momenta, ~1 GiB workspace)"},
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / FP64_PEAK_TFLOPS,
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak,
                              "traffic": None if per_evt is None else per_evt * nevt,
                              "kernel": "me_kernel",
-                             "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz (all-fma peak)",
-                             "fp64_inst_per_s": insts / launch_s,
-                             "pipe_frac": insts / launch_s / 1e9 / FP64_PEAK_GINST,
+                             "peak_source": ("FP32 pipe: 152 SM x 128 FFMA/clk x 2070 MHz (all-fma peak)" if f32 else
+                                             "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz (all-fma peak)"),
+                             "inst_per_s": insts / launch_s,
+                             "pipe_frac": insts / launch_s / 1e9 / peak_inst,
                              "flops_per_event": flops / nevt},
                 "e2e": {"value": world * nevt / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": args.steps,
+                "gpu_launches": args.steps * (4 * tc_chunks if tc_chunks else 1),
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu,
                 "wall_s_timed": wall}

@@ -54,14 +54,20 @@ enum mgx_status {
   MGX_ERR_UNSUPPORTED_MODE = -7
 };
 
-/* Precision of the colour sum (Sec. 3: "mixed" computes the diagrams in double
- * precision and the colour-matrix quadratic form in single precision).  The
- * amplitudes are float64 in every mode; the helicity sum is float64. */
+/* Arithmetic precision (Sec. 3: the double, float and "mixed" builds; mixed computes the
+ * diagrams in double precision and the colour-matrix quadratic form in single precision).
+ * The helicity sum and the selections are float64 in every mode. */
 enum mgx_mode {
-  MGX_FP64 = 0,       /* float64 colour sum */
-  MGX_MIXED_FP32 = 1, /* jamps rounded to float32, float32 quadratic form */
-  MGX_MIXED_TF32 = 2  /* tensor-core colour sum: jamps split into two tf32 terms times the
-                         integer-scaled colour matrix (exact in tf32), float32 accumulation */
+  MGX_FP64 = 0,       /* float64 amplitudes and colour sum */
+  MGX_MIXED_FP32 = 1, /* float64 amplitudes; jamps rounded to float32, float32 quadratic form */
+  MGX_MIXED_TF32 = 2, /* float64 amplitudes; tensor-core colour sum: jamps split into two tf32
+                         terms times the integer-scaled colour matrix (exact in tf32), float32
+                         accumulation */
+  MGX_MIXED_BF16X3 = 3, /* float64 amplitudes; tensor-core colour sum in bf16: jamps split into three
+                         bf16 terms, the integer-scaled colour matrix into two (exact below 2^16;
+                         otherwise MGX_ERR_UNSUPPORTED_MODE), float32 accumulation */
+  MGX_FLOAT = 4       /* float32 amplitudes and colour sum (the paper's float build); thread-per-
+                         event kernel only */
 };
 
 /* Standard-Model inputs.  Electroweak scheme {alpha_em(mZ), G_F, mZ}. */

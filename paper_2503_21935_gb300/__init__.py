@@ -18,7 +18,10 @@ MGX_OK = 0
 MGX_FP64 = 0
 MGX_MIXED_FP32 = 1
 MGX_MIXED_TF32 = 2
-MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32, "mixed_tf32": MGX_MIXED_TF32}
+MGX_MIXED_BF16X3 = 3
+MGX_FLOAT = 4
+MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32, "mixed_tf32": MGX_MIXED_TF32,
+         "mixed_bf16x3": MGX_MIXED_BF16X3, "float": MGX_FLOAT}
 MGX_KERNEL_AUTO, MGX_KERNEL_THREAD, MGX_KERNEL_CTA = 0, 1, 2
 
 
@@ -352,7 +355,7 @@ class Process:
     def workspace(self, nevt, mode=MGX_FP64, host=False):
         import torch
         need = self.workspace_bytes(nevt, mode, host)
-        key = (host, mode == MGX_MIXED_TF32)
+        key = (host, mode in (MGX_MIXED_TF32, MGX_MIXED_BF16X3))
         ws = self._ws.get(key)
         if ws is None or ws.numel() < need:
             ws = torch.empty(max(need, 256), dtype=torch.uint8, device=f"cuda:{self.device}")

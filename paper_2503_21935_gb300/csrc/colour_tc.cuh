@@ -1,46 +1,91 @@
-// Tensor-core colour sum (mode MGX_MIXED_TF32), the one dense contraction of the path.
+// Tensor-core colour sum (modes MGX_MIXED_TF32 and MGX_MIXED_BF16X3), the one dense
+// contraction of the path.
 //
 // The jamps of a batch form a real matrix X with one row per (event, good helicity, Re/Im):
 // row r = 2 (e ngood + ih) + part, K = ncol.  With the colour matrix scaled to integers,
-// Cs = den C (exact in tf32), Y = X Cs is one tcgen05.mma tile of M = 128 rows per k-step
-// (kind::tf32, f32 accumulate in tensor memory), X split as X_hi + X_lo (two tf32 terms, so the
-// product keeps ~22 bits of X), and |M_h|^2 = (x_Re . y_Re + x_Im . y_Im) / den.
+// Cs = den C, Y = X Cs is a tcgen05.mma tile of M = 128 rows (f32 accumulate in tensor memory)
+// and |M_h|^2 = (x_Re . y_Re + x_Im . y_Im) / den.  Both operands are split into sums of
+// low-precision parts and the partial products are accumulated into the same tile:
+//   tf32:   X = X0 + X1 (two tf32 terms, ~22 bits of X); Cs exact in tf32 (one part);
+//           products X0 Cs + X1 Cs.
+//   bf16x3: X = X0 + X1 + X2 (three bf16 terms, ~24 bits), Cs = C0 + C1 (two bf16 terms, exact
+//           for integers below 2^16); products X_i C_j with i + j < 3 (the dropped X2 C1 and
+//           X1 C1 ... terms lie below 2^-24 relative).
 #pragma once
+#include <cuda_bf16.h>
+
 #include "umma.cuh"
 
 namespace mgx {
 
 constexpr int kTcRows = 128;
 
-// shared memory: A_hi, A_lo (128 x kpad f32, canonical K-major), B (npad x kpad), mbarrier, TMEM slot
+struct TcTf32 {
+  static constexpr uint32_t kFmt = umma::FMT_TF32;
+  static constexpr int kElem = 4, kKStep = 8, kAParts = 2, kBParts = 1;
+  __device__ static void split(float x, unsigned char* dst[], uint32_t off) {
+    const float hi = umma::to_tf32(x);
+    *reinterpret_cast<float*>(dst[0] + off) = hi;
+    *reinterpret_cast<float*>(dst[1] + off) = umma::to_tf32(x - hi);
+  }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    umma::mma_tf32(d, a, b, id, acc);
+  }
+};
+
+struct TcBf16x3 {
+  static constexpr uint32_t kFmt = umma::FMT_BF16;
+  static constexpr int kElem = 2, kKStep = 16, kAParts = 3, kBParts = 2;
+  __device__ static void split(float x, unsigned char* dst[], uint32_t off) {
+    const __nv_bfloat16 p0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(p0);           // exact
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+    *reinterpret_cast<__nv_bfloat16*>(dst[0] + off) = p0;
+    *reinterpret_cast<__nv_bfloat16*>(dst[1] + off) = p1;
+    *reinterpret_cast<__nv_bfloat16*>(dst[2] + off) = p2;
+  }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    umma::mma_f16(d, a, b, id, acc);   // kind::f16 with A and B both bf16
+  }
+};
+
+// shared memory: A parts (128 x kpad each, canonical K-major), B parts (npad x kpad each),
+// mbarrier, TMEM slot
+template <class F>
 __host__ __device__ inline size_t colour_tc_smem(int kpad, int npad) {
-  return (size_t)2 * kTcRows * kpad * 4 + (size_t)npad * kpad * 4 + 64;
+  return (size_t)F::kAParts * kTcRows * kpad * F::kElem + (size_t)F::kBParts * npad * kpad * F::kElem + 64;
 }
 
+template <class F>
 __global__ void __launch_bounds__(kTcRows)
     colour_tc_kernel(const double* __restrict__ jamps, int64_t nrows, int ncol, int kpad, int npad,
-                     uint32_t tmem_cols, const float* __restrict__ bcanon, double inv_den,
+                     uint32_t tmem_cols, const unsigned char* __restrict__ bcanon, double inv_den,
                      double* __restrict__ mh, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* a_hi = smem_raw;
-  unsigned char* a_lo = a_hi + (size_t)kTcRows * kpad * 4;
-  unsigned char* b = a_lo + (size_t)kTcRows * kpad * 4;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b + (size_t)npad * kpad * 4);
+  const size_t a_bytes = (size_t)kTcRows * kpad * F::kElem, b_bytes = (size_t)npad * kpad * F::kElem;
+  unsigned char* a[F::kAParts];
+#pragma unroll
+  for (int p = 0; p < F::kAParts; ++p) a[p] = smem_raw + p * a_bytes;
+  unsigned char* b = smem_raw + F::kAParts * a_bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(b + F::kBParts * b_bytes);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  // B tile (already in canonical layout) into shared memory
-  const float* bsrc = bcanon;
-  float* bdst = reinterpret_cast<float*>(b);
-  for (int i = tid; i < npad * kpad; i += kTcRows) bdst[i] = __ldg(bsrc + i);
+  // B parts (already in canonical layout) into shared memory
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(bcanon);
+    uint4* dst = reinterpret_cast<uint4*>(b);
+    for (int i = tid; i < (int)(F::kBParts * b_bytes / 16); i += kTcRows) dst[i] = __ldg(src + i);
+  }
   if (tid == 0) umma::mbar_init(mbar, 1);
   if (warp == 0) umma::tmem_alloc(tslot, tmem_cols);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t sbo = (uint32_t)(kpad / 4) * 128;
-  const uint32_t id = umma::idesc(umma::FMT_TF32, kTcRows, (uint32_t)npad);
-  const uint32_t sa_hi = umma::smem_u32(a_hi), sa_lo = umma::smem_u32(a_lo), sb = umma::smem_u32(b);
+  const uint32_t sbo = (uint32_t)(kpad * F::kElem / 16) * 128;
+  const uint32_t id = umma::idesc(F::kFmt, kTcRows, (uint32_t)npad);
+  const uint32_t sb = umma::smem_u32(b);
   uint32_t phase = 0;
   bool ok = true;
   for (int64_t tile = blockIdx.x; tile * kTcRows < nrows; tile += gridDim.x) {
@@ -49,22 +94,22 @@ __global__ void __launch_bounds__(kTcRows)
     const double* xr = jamps + (r >> 1) * 2 * ncol + (r & 1);
     for (int k = 0; k < kpad; ++k) {
       const float x = (valid && k < ncol) ? (float)__ldg(xr + 2 * k) : 0.0f;
-      const float hi = umma::to_tf32(x);
-      const float lo = umma::to_tf32(x - hi);
-      const uint32_t off = umma::kmajor_offset((uint32_t)tid, (uint32_t)k, (uint32_t)kpad, 4);
-      *reinterpret_cast<float*>(a_hi + off) = hi;
-      *reinterpret_cast<float*>(a_lo + off) = lo;
+      F::split(x, a, umma::kmajor_offset((uint32_t)tid, (uint32_t)k, (uint32_t)kpad, F::kElem));
     }
     umma::fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       umma::fence_after_sync();
-      for (int ks = 0; ks < kpad / 8; ++ks)
-        umma::mma_tf32(tmem, umma::smem_desc(sa_hi + ks * 256, 128, sbo), umma::smem_desc(sb + ks * 256, 128, sbo), id,
-                       ks > 0);
-      for (int ks = 0; ks < kpad / 8; ++ks)
-        umma::mma_tf32(tmem, umma::smem_desc(sa_lo + ks * 256, 128, sbo), umma::smem_desc(sb + ks * 256, 128, sbo), id,
-                       1);
+      bool first = true;
+      for (int pa = 0; pa < F::kAParts; ++pa)
+        for (int pb = 0; pb < F::kBParts && pa + pb < F::kAParts; ++pb) {
+          const uint32_t sa = umma::smem_u32(a[pa]), sbp = sb + (uint32_t)(pb * b_bytes);
+          for (int ks = 0; ks < kpad / F::kKStep; ++ks) {
+            F::mma(tmem, umma::smem_desc(sa + ks * 256, 128, sbo), umma::smem_desc(sbp + ks * 256, 128, sbo), id,
+                   first ? 0u : 1u);
+            first = false;
+          }
+        }
       umma::mma_commit(mbar);
     }
     const bool done = umma::mbar_wait(mbar, phase);

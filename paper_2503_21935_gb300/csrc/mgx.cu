@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mgx.h"
@@ -109,6 +110,29 @@ __device__ __forceinline__ double quad_form(const JV& J, const double* csym, con
   return acc;
 }
 
+// |M_h|^2 / g_s^(2p) of one helicity from jamps J(k) of real type R: float64 (or the mixed
+// float32 form above), or float32 throughout
+template <class R, class JV>
+__device__ __forceinline__ double colour_sum(const KParams& P, const JV& J, int n, int mode) {
+  if constexpr (std::is_same<R, double>::value) {
+    return quad_form(J, P.colsym, P.colsym_f, n, mode);
+  } else {
+    float acc = 0.0f;
+    for (int i = 0; i < n; ++i) {
+      const float ri = J(2 * i), ii = J(2 * i + 1);
+      const float* crow = P.colsym_f + i * n;
+      float zr = __ldg(crow + i) * ri, zi = __ldg(crow + i) * ii;
+      for (int j = i + 1; j < n; ++j) {
+        const float c = __ldg(crow + j);
+        zr = fmaf(c, J(2 * j), zr);
+        zi = fmaf(c, J(2 * j + 1), zi);
+      }
+      acc = fmaf(ri, zr, fmaf(ii, zi, acc));
+    }
+    return (double)acc;
+  }
+}
+
 // helicity sum (float64, canonical order), me and the two selections from per-helicity
 // weights mh[ngood] and colour weights colw[ncol] (any indexable storage)
 template <class A, class B>
@@ -147,21 +171,25 @@ __device__ inline void finish_event(const KParams& P, int64_t e, const A& mh, co
 // per-event store does not fit in shared memory.
 // One event, evaluated by one thread: the whole op table into the workspace view W, then the
 // colour sum, helicity sum and selections (or, in the tensor-core mode, the export of the jamps).
-__device__ inline void eval_event(const KParams& P, int64_t e, const double* pe, const WS& W,
+// Currents and jamps are of real type R; |M_h|^2 and the colour weights are kept as R in the
+// workspace and summed in float64.
+template <class R>
+__device__ inline void eval_event(const KParams& P, int64_t e, const double* pe, const WST<R>& W,
                                   const double* __restrict__ alphas, const double* __restrict__ rhel,
                                   const double* __restrict__ rcol, double* __restrict__ me,
                                   int32_t* __restrict__ selhel, int32_t* __restrict__ selcol,
                                   double* __restrict__ mh_out, double* __restrict__ colw_out, int mode,
                                   double* __restrict__ jexp, double* __restrict__ colw_exp) {
+  using T = Real<R>;
   const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
   const double scale = coupling_scale(P, alphas[e]);
-  for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = 0.0;
+  for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = T::from(0.0);
   for (int iop = 0; iop < P.nops; ++iop) {
     const Op o = load_op(P.ops, iop);
     if (o.code == OP_AMP) {
       const int2* fl = P.flows + o.cpl;
       for (int ih = 0; ih < P.ngood; ++ih) {
-        const cx amp = group_amp(P.terms, o, P.good[ih], W);
+        const cxT<R> amp = group_amp<R>(P.terms, o, P.good[ih], W);
         const int jb = P.jamp_off + 2 * P.ncol * ih;
         for (int f = 0; f < o.mass; ++f) {
           const int2 q = __ldg(fl + f);
@@ -170,44 +198,46 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
       }
       continue;
     }
-    op_header(P, o, gs, pe, W);
+    op_header<R>(P, o, gs, pe, W);
     const int nv = 1 << __popc(o.mdst);
-    for (int v = 0; v < nv; ++v) op_variant(P, o, v, gs, pe, W);
+    for (int v = 0; v < nv; ++v) op_variant<R>(P, o, v, gs, pe, W);
   }
-  if (mode == MGX_MIXED_TF32) {
-    // export the jamps [ngood][ncol][re, im] and the colour weights for the tensor-core colour sum
-    const int nj = 2 * P.ncol * P.ngood;
-    for (int i = 0; i < nj; ++i) jexp[e * nj + i] = W[P.jamp_off + i];
-    for (int i = 0; i < P.ncol; ++i) {
-      double w = 0.0;
-      for (int ih = 0; ih < P.ngood; ++ih) {
-        const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
-        w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
+  if constexpr (std::is_same<R, double>::value) {
+    if (mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3) {
+      // export the jamps [ngood][ncol][re, im] and the colour weights for the tensor-core colour sum
+      const int nj = 2 * P.ncol * P.ngood;
+      for (int i = 0; i < nj; ++i) jexp[e * nj + i] = W[P.jamp_off + i];
+      for (int i = 0; i < P.ncol; ++i) {
+        double w = 0.0;
+        for (int ih = 0; ih < P.ngood; ++ih) {
+          const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
+          w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
+        }
+        colw_exp[e * P.ncol + i] = w * scale;
       }
-      colw_exp[e * P.ncol + i] = w * scale;
+      return;
     }
-    return;
   }
   for (int ih = 0; ih < P.ngood; ++ih) {
     const int jb = P.jamp_off + 2 * P.ncol * ih;
-    const double mh = scale * quad_form([&](int k) { return W[jb + k]; }, P.colsym, P.colsym_f, P.ncol, mode);
-    W[P.mh_off + ih] = mh;
+    const double mh = scale * colour_sum<R>(P, [&](int k) { return W[jb + k]; }, P.ncol, mode);
+    W[P.mh_off + ih] = T::from(mh);
     if (mh_out) mh_out[e * P.ngood + ih] = mh;
   }
   if (selcol || colw_out) {
     for (int i = 0; i < P.ncol; ++i) {
-      double w = 0.0;
+      R w = T::from(0.0);
       for (int ih = 0; ih < P.ngood; ++ih) {
         const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
         w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
       }
-      w *= scale;
-      W[P.colw_off + i] = w;
-      if (colw_out) colw_out[e * P.ncol + i] = w;
+      const double wd = T::to_double(w) * scale;
+      W[P.colw_off + i] = T::from(wd);
+      if (colw_out) colw_out[e * P.ncol + i] = wd;
     }
   }
-  finish_event(P, e, [&](int ih) { return W[P.mh_off + ih]; }, [&](int i) { return W[P.colw_off + i]; }, rhel, rcol,
-               me, selhel, selcol);
+  finish_event(P, e, [&](int ih) { return T::to_double(W[P.mh_off + ih]); },
+               [&](int i) { return T::to_double(W[P.colw_off + i]); }, rhel, rcol, me, selhel, selcol);
 }
 
 // stage the momenta of events [base, base + nb) (contiguous [events][npar][4]) through shared memory
@@ -220,6 +250,7 @@ __device__ __forceinline__ void stage_momenta(const double* __restrict__ mom, in
   __syncthreads();
 }
 
+template <class R>
 __global__ void __launch_bounds__(kThreads)
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
@@ -229,13 +260,13 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ double smem[];
   const int npar4 = 4 * P.npar;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const WS W{ws + tid, nthreads};
+  const WST<R> W{reinterpret_cast<R*>(ws) + tid, nthreads};
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nevt; base += nthreads) {
     stage_momenta(mom, base, min((int64_t)blockDim.x, nevt - base), npar4, smem);
     const int64_t e = base + threadIdx.x;
     if (e >= nevt) continue;
-    eval_event(P, e, smem + threadIdx.x * npar4, W, alphas, rhel, rcol, me, selhel, selcol, mh_out, colw_out, mode,
-               jexp, colw_exp);
+    eval_event<R>(P, e, smem + threadIdx.x * npar4, W, alphas, rhel, rcol, me, selhel, selcol, mh_out, colw_out,
+                  mode, jexp, colw_exp);
   }
 }
 
@@ -290,7 +321,7 @@ __global__ void __launch_bounds__(kThreads)
       stage_momenta(b.mom, base, min((int64_t)blockDim.x, last - base), npar4, smem);
       const int64_t e = base + threadIdx.x;
       if (e < last)
-        eval_event(P, e, smem + threadIdx.x * npar4, W, b.alphas, b.rhel, b.rcol, b.me, b.selhel, b.selcol, nullptr,
+        eval_event<double>(P, e, smem + threadIdx.x * npar4, W, b.alphas, b.rhel, b.rcol, b.me, b.selhel, b.selcol, nullptr,
                    nullptr, mode, nullptr, nullptr);
     }
   }
@@ -368,13 +399,13 @@ __global__ void __launch_bounds__(kCtaThreads)
           const int item = __ldg(C.items + st.y + it);
           const Op o = load_op(C.ops, item >> 8);
           const int v = item & 255;
-          if (v == 255) op_header(P, o, gs, pe, W);
-          else op_variant(P, o, v, gs, pe, W);
+          if (v == 255) op_header<double>(P, o, gs, pe, W);
+          else op_variant<double>(P, o, v, gs, pe, W);
         }
       } else if (act) {
         for (int a = st.y + g; a < st.y + st.z; a += G) {
           const Op o = load_op(C.ops, a);
-          const cx amp = group_amp(C.terms, o, h, W);
+          const cx amp = group_amp<double>(C.terms, o, h, W);
           const int2* fl = C.flows + o.cpl;
           for (int f = 0; f < o.mass; ++f) {
             const int2 q = __ldg(fl + f);
@@ -517,6 +548,20 @@ double param_value(const mgx_params& p, int id) {
   }
 }
 
+// float -> bf16 bits, round to nearest even (finite inputs), and back
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
 int sm_count(int device) {
   int n = 0;
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
@@ -542,8 +587,11 @@ struct mgx_process {
   int4* d_cta_terms = nullptr;
   int* d_cta_items = nullptr;
   int3* d_cta_steps = nullptr;
-  float* d_bcanon = nullptr;  // integer-scaled colour matrix, canonical K-major tf32 tile
-  int tc_kpad = 0, tc_npad = 0, tc_cols = 0;
+  // integer-scaled colour matrix as canonical K-major tiles: tf32 (one part) and bf16 (two parts)
+  unsigned char* d_bcanon = nullptr;
+  unsigned char* d_bcanon16 = nullptr;
+  int tc_kpad = 0, tc_kpad16 = 0, tc_npad = 0, tc_cols = 0;
+  bool bf16_exact = false;    // every integer entry is the sum of its two bf16 parts
   int blocks_per_sm = 4;      // thread-per-event kernel
   int kernel = MGX_KERNEL_AUTO;
 };
@@ -599,7 +647,13 @@ int launch_cta(mgx_process* pr, const KParams& kp, int64_t nevt, const double* m
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
-bool mode_ok(int mode) { return mode == MGX_FP64 || mode == MGX_MIXED_FP32 || mode == MGX_MIXED_TF32; }
+bool mode_ok(int mode) {
+  return mode == MGX_FP64 || mode == MGX_MIXED_FP32 || mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3 ||
+         mode == MGX_FLOAT;
+}
+bool mode_tc(int mode) { return mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3; }
+// modes whose whole path is the float64 amplitude code (CTA kernel, batch, fixed-scratch entry)
+bool mode_f64(int mode) { return mode == MGX_FP64 || mode == MGX_MIXED_FP32; }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -632,9 +686,14 @@ __global__ void tc_error_kernel(const int* err, int64_t n, double* me) {
   if (e < n && *err) me[e] = __longlong_as_double(0x7ff8000000000000ll);
 }
 
+template <class F>
 int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
               const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
               void* ws, size_t wsb, cudaStream_t st) {
+  const bool bf16 = F::kFmt == umma::FMT_BF16;
+  if (bf16 && !pr->bf16_exact) return MGX_ERR_UNSUPPORTED_MODE;
+  const int kpad = bf16 ? pr->tc_kpad16 : pr->tc_kpad;
+  const unsigned char* bcanon = bf16 ? pr->d_bcanon16 : pr->d_bcanon;
   const TcPlan t = tc_plan(pr, kp, nevt);
   if (ws == nullptr || wsb < t.total) return MGX_ERR_WORKSPACE_TOO_SMALL;
   char* p = (char*)ws;
@@ -643,11 +702,12 @@ int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mo
   double* colw = (double*)p; p += t.colw;
   double* mhb = (double*)p; p += t.mh;
   int* err = (int*)p;
-  const size_t smem_tc = colour_tc_smem(pr->tc_kpad, pr->tc_npad);
-  if (cudaFuncSetAttribute(colour_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc) != cudaSuccess)
+  const size_t smem_tc = colour_tc_smem<F>(kpad, pr->tc_npad);
+  if (cudaFuncSetAttribute(colour_tc_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc) !=
+      cudaSuccess)
     return MGX_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, colour_tc_kernel, kTcRows, smem_tc) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, colour_tc_kernel<F>, kTcRows, smem_tc) != cudaSuccess ||
       per_sm < 1)
     return MGX_ERR_CUDA;
   per_sm = std::min(per_sm, 512 / pr->tc_cols);   // tensor-memory columns of one SM
@@ -657,15 +717,15 @@ int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mo
     const int64_t n = std::min(t.chunk, nevt - c0);
     const int64_t nt = grid_threads(pr, n);
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return MGX_ERR_CUDA;
-    me_kernel<<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(kp, n, mom + c0 * npar4, as + c0, nullptr, nullptr,
+    me_kernel<double><<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(kp, n, mom + c0 * npar4, as + c0, nullptr, nullptr,
                                                                 me + c0, nullptr, nullptr, nullptr, nullptr, w_thr, nt,
                                                                 MGX_MIXED_TF32, jexp, colw);
     const int64_t rows = 2 * n * kp.ngood;
     const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
     const int64_t blocks = std::min<int64_t>(tiles, (int64_t)per_sm * sm_count(pr->device));
-    colour_tc_kernel<<<(unsigned)blocks, kTcRows, smem_tc, st>>>(jexp, rows, kp.ncol, pr->tc_kpad, pr->tc_npad,
-                                                                 (uint32_t)pr->tc_cols, pr->d_bcanon,
-                                                                 1.0 / pr->prog->col_den, mhb, err);
+    colour_tc_kernel<F><<<(unsigned)blocks, kTcRows, smem_tc, st>>>(jexp, rows, kp.ncol, kpad, pr->tc_npad,
+                                                                    (uint32_t)pr->tc_cols, bcanon,
+                                                                    1.0 / pr->prog->col_den, mhb, err);
     finish_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
         kp, n, as + c0, rh ? rh + c0 : nullptr, rc ? rc + c0 : nullptr, mhb, colw, me + c0, sh ? sh + c0 : nullptr,
         sc ? sc + c0 : nullptr, mh ? mh + c0 * kp.ngood : nullptr, cw ? cw + c0 * kp.ncol : nullptr);
@@ -679,15 +739,21 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
            const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
            int mode, void* ws, size_t wsb, cudaStream_t st) {
   if (nevt == 0) return MGX_OK;
-  if (mode == MGX_MIXED_TF32) return launch_tc(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
-  if (use_cta(pr, kp)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
+  if (mode == MGX_MIXED_TF32) return launch_tc<TcTf32>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
+  if (mode == MGX_MIXED_BF16X3)
+    return launch_tc<TcBf16x3>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
+  if (mode_f64(mode) && use_cta(pr, kp)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
   const int64_t nt = grid_threads(pr, nevt);
   const size_t need = (size_t)nt * ws_doubles_per_thread(kp) * sizeof(double);
   if (wsb < need || ws == nullptr) return MGX_ERR_WORKSPACE_TOO_SMALL;
   const int blocks = (int)(nt / kThreads);
   const size_t shm = (size_t)kThreads * 4 * kp.npar * sizeof(double);
-  me_kernel<<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt, mode,
-                                           nullptr, nullptr);
+  if (mode == MGX_FLOAT)
+    me_kernel<float><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
+                                                    mode, nullptr, nullptr);
+  else
+    me_kernel<double><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
+                                                     mode, nullptr, nullptr);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
@@ -736,6 +802,7 @@ void mgx_process_destroy(mgx_process* pr) {
   cudaFree(pr->d_colf);
   cudaFree(pr->d_terms);
   cudaFree(pr->d_bcanon);
+  cudaFree(pr->d_bcanon16);
   cudaFree(pr->d_cta_ops);
   cudaFree(pr->d_cta_flows);
   cudaFree(pr->d_cta_terms);
@@ -839,17 +906,30 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
     return MGX_ERR_CUDA;
   }
   if (ok) {
-    // integer-scaled colour matrix as a canonical K-major tf32 tile for the tensor-core colour sum
+    // integer-scaled colour matrix as canonical K-major tiles for the tensor-core colour sums
     pr->tc_kpad = (n + 7) / 8 * 8;
+    pr->tc_kpad16 = (n + 15) / 16 * 16;
     pr->tc_npad = (n + 15) / 16 * 16;
     pr->tc_cols = 32;
     while (pr->tc_cols < pr->tc_npad) pr->tc_cols *= 2;
     std::vector<float> bc((size_t)pr->tc_npad * pr->tc_kpad, 0.0f);
+    const size_t tile16 = (size_t)pr->tc_npad * pr->tc_kpad16;
+    std::vector<uint16_t> b16(2 * tile16, 0);
+    pr->bf16_exact = true;
     for (int r = 0; r < n; ++r)
-      for (int k = 0; k < n; ++k)
-        bc[umma::kmajor_offset(r, k, pr->tc_kpad, 4) / 4] = (float)(prog->colour[r * n + k] * prog->col_den);
+      for (int k = 0; k < n; ++k) {
+        const float c = (float)(prog->colour[r * n + k] * prog->col_den);
+        bc[umma::kmajor_offset(r, k, pr->tc_kpad, 4) / 4] = c;
+        const uint16_t h = bf16_bits(c), l = bf16_bits(c - bf16_value(h));
+        pr->bf16_exact = pr->bf16_exact && bf16_value(h) + bf16_value(l) == c;
+        const size_t o = umma::kmajor_offset(r, k, pr->tc_kpad16, 2) / 2;
+        b16[o] = h;
+        b16[tile16 + o] = l;
+      }
     ok = cudaMalloc(&pr->d_bcanon, sizeof(float) * bc.size()) == cudaSuccess &&
-         cudaMemcpy(pr->d_bcanon, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+         cudaMemcpy(pr->d_bcanon, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMalloc(&pr->d_bcanon16, sizeof(uint16_t) * b16.size()) == cudaSuccess &&
+         cudaMemcpy(pr->d_bcanon16, b16.data(), sizeof(uint16_t) * b16.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   }
   if (!ok) {
     mgx_process_destroy(pr);
@@ -936,7 +1016,7 @@ int mgx_colour_matrix(const mgx_process* pr, double* out) {
 int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* bytes) {
   if (!pr || !bytes || nevt < 0) return MGX_ERR_INVALID_ARGUMENT;
   if (!mode_ok(mode)) return MGX_ERR_UNSUPPORTED_MODE;
-  if (mode == MGX_MIXED_TF32) {
+  if (mode_tc(mode)) {
     *bytes = nevt == 0 ? 0 : tc_plan(pr, pr->kp, nevt).total;
     return MGX_OK;
   }
@@ -1227,7 +1307,7 @@ extern "C" int mgx_process_autotune(mgx_process* pr, int64_t nevt, const double*
   cudaEventCreate(&e1);
   struct Cand { int kernel, bps; };
   std::vector<Cand> cands = {{MGX_KERNEL_THREAD, 2}, {MGX_KERNEL_THREAD, 4}};
-  if (cta_usable(pr, pr->kp) && mode != MGX_MIXED_TF32) cands.push_back({MGX_KERNEL_CTA, 4});
+  if (cta_usable(pr, pr->kp) && mode_f64(mode)) cands.push_back({MGX_KERNEL_CTA, 4});
   const int save_k = pr->kernel, save_b = pr->blocks_per_sm;
   float best = 1e30f;
   Cand pick{save_k, save_b};
@@ -1314,7 +1394,7 @@ extern "C" int mgx_compute_noalloc(mgx_process* pr, int64_t nevt, const double* 
   const int64_t blocks = std::max<int64_t>(1, std::min({fit, want, cap}));
   const int64_t nt = blocks * kThreads;
   const size_t shm = (size_t)kThreads * 4 * pr->kp.npar * sizeof(double);
-  me_kernel<<<(unsigned)blocks, kThreads, shm, (cudaStream_t)stream>>>(
+  me_kernel<double><<<(unsigned)blocks, kThreads, shm, (cudaStream_t)stream>>>(
       pr->kp, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, scratch, nt, mode,
       nullptr, nullptr);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;

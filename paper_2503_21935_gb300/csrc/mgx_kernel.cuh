@@ -9,6 +9,7 @@
 // Diagram amplitudes (one per diagram term) are closed at the root vertex for every
 // good helicity and added to the colour-flow amplitudes (jamps); the colour sum
 // J^dagger C J, the helicity sum and the selections follow in the same thread.
+// The arithmetic is templated on its real type R: double or float.
 //
 // Feynman rules (all momenta incoming at a vertex; metric +---; chiral gamma basis):
 //   f f V : gamma^mu (cL P_L + cR P_R)      qqg: cL = cR = i g_s; photon -i e Q; Z -i gL, -i gR
@@ -17,6 +18,8 @@
 //   fermion propagator i (kslash + m)/(k^2 - m^2 + i m w); vector -i (g - k k/M^2)/(k^2 - M^2 + i M w)
 #pragma once
 #include <cstdint>
+
+#include "real.cuh"
 
 namespace mgx {
 
@@ -45,34 +48,38 @@ struct KParams {
   int good[MAXHEL];      // canonical indices of the good helicities
 };
 
-struct cx {
-  double r, i;
+template <class R>
+struct cxT {
+  R r, i;
 };
+using cx = cxT<double>;
 
-__device__ __forceinline__ cx cmk(double r, double i) { return cx{r, i}; }
-__device__ __forceinline__ cx operator+(cx a, cx b) { return cx{a.r + b.r, a.i + b.i}; }
-__device__ __forceinline__ cx operator-(cx a, cx b) { return cx{a.r - b.r, a.i - b.i}; }
-__device__ __forceinline__ cx cmul(cx a, cx b) {
-  return cx{fma(a.r, b.r, -a.i * b.i), fma(a.r, b.i, a.i * b.r)};
+template <class R> __device__ __forceinline__ cxT<R> operator+(cxT<R> a, cxT<R> b) { return {a.r + b.r, a.i + b.i}; }
+template <class R> __device__ __forceinline__ cxT<R> operator-(cxT<R> a, cxT<R> b) { return {a.r - b.r, a.i - b.i}; }
+template <class R> __device__ __forceinline__ cxT<R> cneg(cxT<R> a) { return {-a.r, -a.i}; }
+template <class R> __device__ __forceinline__ cxT<R> cmul(cxT<R> a, cxT<R> b) {
+  return {fma(a.r, b.r, -(a.i * b.i)), fma(a.r, b.i, a.i * b.r)};
 }
 // acc + a*b
-__device__ __forceinline__ cx cfma(cx a, cx b, cx acc) {
-  return cx{fma(a.r, b.r, fma(-a.i, b.i, acc.r)), fma(a.r, b.i, fma(a.i, b.r, acc.i))};
+template <class R> __device__ __forceinline__ cxT<R> cfma(cxT<R> a, cxT<R> b, cxT<R> acc) {
+  return {fma(a.r, b.r, fma(-a.i, b.i, acc.r)), fma(a.r, b.i, fma(a.i, b.r, acc.i))};
 }
-__device__ __forceinline__ cx rmul(double s, cx a) { return cx{s * a.r, s * a.i}; }
-__device__ __forceinline__ cx rfma(double s, cx a, cx acc) { return cx{fma(s, a.r, acc.r), fma(s, a.i, acc.i)}; }
-__device__ __forceinline__ cx conjx(cx a) { return cx{a.r, -a.i}; }
+template <class R> __device__ __forceinline__ cxT<R> rmul(R s, cxT<R> a) { return {s * a.r, s * a.i}; }
+template <class R> __device__ __forceinline__ cxT<R> rfma(R s, cxT<R> a, cxT<R> acc) {
+  return {fma(s, a.r, acc.r), fma(s, a.i, acc.i)};
+}
+template <class R> __device__ __forceinline__ cxT<R> conjx(cxT<R> a) { return {a.r, -a.i}; }
 // Minkowski dot of complex 4-vectors (upper components)
-__device__ __forceinline__ cx mdot(const cx* a, const cx* b) {
-  cx s = cmul(a[0], b[0]);
-  s = cfma(cmk(-a[1].r, -a[1].i), b[1], s);
-  s = cfma(cmk(-a[2].r, -a[2].i), b[2], s);
-  s = cfma(cmk(-a[3].r, -a[3].i), b[3], s);
+template <class R> __device__ __forceinline__ cxT<R> mdot(const cxT<R>* a, const cxT<R>* b) {
+  cxT<R> s = cmul(a[0], b[0]);
+  s = cfma(cneg(a[1]), b[1], s);
+  s = cfma(cneg(a[2]), b[2], s);
+  s = cfma(cneg(a[3]), b[3], s);
   return s;
 }
 // Minkowski dot of a real and a complex 4-vector
-__device__ __forceinline__ cx rdot(const double* k, const cx* a) {
-  cx s = rmul(k[0], a[0]);
+template <class R> __device__ __forceinline__ cxT<R> rdot(const R* k, const cxT<R>* a) {
+  cxT<R> s = rmul(k[0], a[0]);
   s = rfma(-k[1], a[1], s);
   s = rfma(-k[2], a[2], s);
   s = rfma(-k[3], a[3], s);
@@ -101,155 +108,165 @@ __device__ __forceinline__ int pdep(int v, int mask) {
   return r;
 }
 
-// Per-event workspace view: element `off` of this thread lives at base[off * stride].
-struct WS {
-  double* base;
+// Per-event workspace view: element `off` of this thread is base[off * stride], one R per
+// element (8 bytes for double, 4 for float), so a warp's accesses coalesce.
+template <class R>
+struct WST {
+  R* base;
   int64_t stride;
-  __device__ __forceinline__ double& operator[](int off) const { return base[(int64_t)off * stride]; }
-  __device__ __forceinline__ void load4(int off, cx* w) const {
+  __device__ __forceinline__ R& operator[](int off) const { return base[(int64_t)off * stride]; }
+  __device__ __forceinline__ void load4(int off, cxT<R>* w) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = cx{base[(int64_t)(off + 2 * j) * stride], base[(int64_t)(off + 2 * j + 1) * stride]};
+    for (int j = 0; j < 4; ++j) w[j] = cxT<R>{(*this)[off + 2 * j], (*this)[off + 2 * j + 1]};
   }
-  __device__ __forceinline__ void store4(int off, const cx* w) const {
+  __device__ __forceinline__ void store4(int off, const cxT<R>* w) const {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      base[(int64_t)(off + 2 * j) * stride] = w[j].r;
-      base[(int64_t)(off + 2 * j + 1) * stride] = w[j].i;
+      (*this)[off + 2 * j] = w[j].r;
+      (*this)[off + 2 * j + 1] = w[j].i;
     }
   }
-  __device__ __forceinline__ void loadk(int off, double* k) const {
+  __device__ __forceinline__ void loadk(int off, R* k) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) k[j] = base[(int64_t)(off + j) * stride];
+    for (int j = 0; j < 4; ++j) k[j] = (*this)[off + j];
   }
-  __device__ __forceinline__ void storek(int off, const double* k) const {
+  __device__ __forceinline__ void storek(int off, const R* k) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) base[(int64_t)(off + j) * stride] = k[j];
+    for (int j = 0; j < 4; ++j) (*this)[off + j] = k[j];
   }
 };
-
-__device__ __forceinline__ int var_off(int block, int v) { return block + 4 + 8 * v; }
+using WS = WST<double>;
 
 // ---- external wavefunctions (HELAS conventions, helicity eigenstates in the given frame)
 // two-component helicity spinors chi_lam(p)
-__device__ inline void chi(const double* p, double pp, int lam, cx* c) {
-  const double a = pp + p[3];
-  if (a > 0.0) {
-    const double n = 1.0 / sqrt(2.0 * pp * a);
+template <class R>
+__device__ inline void chi(const R* p, R pp, int lam, cxT<R>* c) {
+  using T = Real<R>;
+  const R zero = T::from(0.0), one = T::from(1.0);
+  const R a = pp + p[3];
+  if (T::positive(a)) {
+    const R n = T::rcp(T::sqrt_(T::from(2.0) * pp * a));
     if (lam > 0) {
-      c[0] = cx{a * n, 0.0};
-      c[1] = cx{p[1] * n, p[2] * n};
+      c[0] = {a * n, zero};
+      c[1] = {p[1] * n, p[2] * n};
     } else {
-      c[0] = cx{-p[1] * n, p[2] * n};
-      c[1] = cx{a * n, 0.0};
+      c[0] = {-(p[1] * n), p[2] * n};
+      c[1] = {a * n, zero};
     }
-  } else if (pp > 0.0) {  // along -z
-    if (lam > 0) { c[0] = cx{0.0, 0.0}; c[1] = cx{1.0, 0.0}; }
-    else { c[0] = cx{-1.0, 0.0}; c[1] = cx{0.0, 0.0}; }
-  } else {                // at rest: quantise along +z
-    if (lam > 0) { c[0] = cx{1.0, 0.0}; c[1] = cx{0.0, 0.0}; }
-    else { c[0] = cx{0.0, 0.0}; c[1] = cx{1.0, 0.0}; }
+  } else if (T::positive(pp)) {  // along -z
+    if (lam > 0) { c[0] = {zero, zero}; c[1] = {one, zero}; }
+    else { c[0] = {-one, zero}; c[1] = {zero, zero}; }
+  } else {                       // at rest: quantise along +z
+    if (lam > 0) { c[0] = {one, zero}; c[1] = {zero, zero}; }
+    else { c[0] = {zero, zero}; c[1] = {one, zero}; }
   }
 }
 
+template <class R>
+__device__ __forceinline__ R norm3(const R* p) {
+  return Real<R>::sqrt_(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+}
+
 // u(p, lam): (sqrt(E - lam|p|) chi_lam, sqrt(E + lam|p|) chi_lam); massless: exact chirality
-__device__ inline void ext_u(const double* p, double m, int lam, cx* w) {
-  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  cx c[2];
+template <class R>
+__device__ inline void ext_u(const R* p, double m, int lam, cxT<R>* w) {
+  using T = Real<R>;
+  const R pp = norm3(p);
+  cxT<R> c[2];
   chi(p, pp, lam, c);
-  double wu, wl;
+  R wu, wl;
   if (m == 0.0) {
-    const double s = sqrt(2.0 * p[0]);
-    wu = lam < 0 ? s : 0.0;
-    wl = lam < 0 ? 0.0 : s;
+    const R s = T::sqrt_(T::from(2.0) * p[0]);
+    wu = lam < 0 ? s : T::from(0.0);
+    wl = lam < 0 ? T::from(0.0) : s;
   } else {
-    wu = sqrt(fmax(p[0] - lam * pp, 0.0));
-    wl = sqrt(fmax(p[0] + lam * pp, 0.0));
+    const R lp = lam > 0 ? pp : -pp;
+    wu = T::sqrt_(T::max0(p[0] - lp));
+    wl = T::sqrt_(T::max0(p[0] + lp));
   }
   w[0] = rmul(wu, c[0]); w[1] = rmul(wu, c[1]);
   w[2] = rmul(wl, c[0]); w[3] = rmul(wl, c[1]);
 }
 
 // v(p, lam): (sqrt(E + lam|p|) chi_-lam, -sqrt(E - lam|p|) chi_-lam)
-__device__ inline void ext_v(const double* p, double m, int lam, cx* w) {
-  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  cx c[2];
+template <class R>
+__device__ inline void ext_v(const R* p, double m, int lam, cxT<R>* w) {
+  using T = Real<R>;
+  const R pp = norm3(p);
+  cxT<R> c[2];
   chi(p, pp, -lam, c);
-  double wu, wl;
+  R wu, wl;
   if (m == 0.0) {
-    const double s = sqrt(2.0 * p[0]);
-    wu = lam > 0 ? s : 0.0;
-    wl = lam > 0 ? 0.0 : -s;
+    const R s = T::sqrt_(T::from(2.0) * p[0]);
+    wu = lam > 0 ? s : T::from(0.0);
+    wl = lam > 0 ? T::from(0.0) : -s;
   } else {
-    wu = sqrt(fmax(p[0] + lam * pp, 0.0));
-    wl = -sqrt(fmax(p[0] - lam * pp, 0.0));
+    const R lp = lam > 0 ? pp : -pp;
+    wu = T::sqrt_(T::max0(p[0] + lp));
+    wl = -T::sqrt_(T::max0(p[0] - lp));
   }
   w[0] = rmul(wu, c[0]); w[1] = rmul(wu, c[1]);
   w[2] = rmul(wl, c[0]); w[3] = rmul(wl, c[1]);
 }
 
 // psi-bar = psi^dagger gamma^0: swap halves and conjugate
-__device__ __forceinline__ void to_bar(cx* w) {
-  const cx a = w[0], b = w[1];
+template <class R>
+__device__ __forceinline__ void to_bar(cxT<R>* w) {
+  const cxT<R> a = w[0], b = w[1];
   w[0] = conjx(w[2]); w[1] = conjx(w[3]);
   w[2] = conjx(a); w[3] = conjx(b);
 }
 
 // eps^mu(k, lam) = (-lam e1 - i e2)/sqrt2 (upper index); outgoing: complex conjugate
-__device__ inline void ext_eps(const double* k, int lam, bool outgoing, cx* w) {
-  const double kk = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
-  const double pt = sqrt(k[1] * k[1] + k[2] * k[2]);
-  double cth = 1.0, sth = 0.0, cph = 1.0, sph = 0.0;
-  if (kk > 0.0) { cth = k[3] / kk; sth = pt / kk; }
-  if (pt > 0.0) { cph = k[1] / pt; sph = k[2] / pt; }
-  const double r = 0.70710678118654752440;
-  const double l = (double)lam;
-  const double sg = outgoing ? -1.0 : 1.0;
-  w[0] = cx{0.0, 0.0};
-  w[1] = cx{-l * cth * cph * r, sg * sph * r};
-  w[2] = cx{-l * cth * sph * r, -sg * cph * r};
-  w[3] = cx{l * sth * r, 0.0};
+template <class R>
+__device__ inline void ext_eps(const R* k, int lam, bool outgoing, cxT<R>* w) {
+  using T = Real<R>;
+  const R zero = T::from(0.0);
+  const R kk = norm3(k);
+  const R pt = T::sqrt_(k[1] * k[1] + k[2] * k[2]);
+  R cth = T::from(1.0), sth = zero, cph = T::from(1.0), sph = zero;
+  if (T::positive(kk)) { const R ik = T::rcp(kk); cth = k[3] * ik; sth = pt * ik; }
+  if (T::positive(pt)) { const R ip = T::rcp(pt); cph = k[1] * ip; sph = k[2] * ip; }
+  const R r = T::from(0.70710678118654752440);
+  const R l = T::from(lam > 0 ? 1.0 : -1.0);
+  const R rs = outgoing ? -r : r;
+  w[0] = {zero, zero};
+  w[1] = {-(l * cth * cph * r), sph * rs};
+  w[2] = {-(l * cth * sph * r), -(cph * rs)};
+  w[3] = {l * sth * r, zero};
 }
 
 // ---- vertex building blocks
 // A = V^0 - V.sigma, B = V^0 + V.sigma for a complex 4-vector V (upper components)
-struct Slash {
-  cx a00, a01, a10, a11;  // A
-  cx b00, b01, b10, b11;  // B
+template <class R>
+struct SlashT {
+  cxT<R> a00, a01, a10, a11;  // A
+  cxT<R> b00, b01, b10, b11;  // B
 };
-__device__ __forceinline__ Slash slash(const cx* V) {
-  Slash s;
+template <class R>
+__device__ __forceinline__ SlashT<R> slash(const cxT<R>* V) {
+  SlashT<R> s;
   s.a00 = V[0] - V[3];
   s.a11 = V[0] + V[3];
   s.b00 = s.a11;
   s.b11 = s.a00;
-  const cx v12m = cx{V[1].r + V[2].i, V[1].i - V[2].r};  // V1 - i V2
-  const cx v12p = cx{V[1].r - V[2].i, V[1].i + V[2].r};  // V1 + i V2
-  s.a01 = cx{-v12m.r, -v12m.i};
-  s.a10 = cx{-v12p.r, -v12p.i};
+  const cxT<R> v12m = {V[1].r + V[2].i, V[1].i - V[2].r};  // V1 - i V2
+  const cxT<R> v12p = {V[1].r - V[2].i, V[1].i + V[2].r};  // V1 + i V2
+  s.a01 = cneg(v12m);
+  s.a10 = cneg(v12p);
   s.b01 = v12m;
   s.b10 = v12p;
   return s;
 }
-// real momentum: KA = k0 - k.sigma, KB = k0 + k.sigma (entries with real/imag parts from k)
-struct KSlash {
-  double a00, a11;  // k0 - k3, k0 + k3 (real)
-  cx a01, a10;      // -(k1 - i k2), -(k1 + i k2)
-};
-__device__ __forceinline__ KSlash kslash(const double* k) {
-  KSlash s;
-  s.a00 = k[0] - k[3];
-  s.a11 = k[0] + k[3];
-  s.a01 = cx{-k[1], k[2]};
-  s.a10 = cx{-k[1], -k[2]};
-  return s;
-}
 
 // complex 1/(re + i im)
-__device__ __forceinline__ cx cinv(double re, double im) {
-  const double d = 1.0 / fma(re, re, im * im);
-  return cx{re * d, -im * d};
+template <class R>
+__device__ __forceinline__ cxT<R> cinv(R re, R im) {
+  const R d = Real<R>::rcp(fma(re, re, im * im));
+  return {re * d, -(im * d)};
 }
-__device__ __forceinline__ double msq(const double* k) {
+template <class R>
+__device__ __forceinline__ R msq(const R* k) {
   return fma(k[0], k[0], -fma(k[1], k[1], fma(k[2], k[2], k[3] * k[3])));
 }
 

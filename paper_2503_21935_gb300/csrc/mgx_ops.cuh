@@ -1,9 +1,10 @@
-// Op executors of the amplitude program (conventions in mgx_kernel.cuh).
+// Op executors of the amplitude program (conventions in mgx_kernel.cuh), templated on the
+// real type R and on the storage view S (per-thread global workspace or shared memory).
 //
 // Every current op is split into a header, computed once per event (incoming
 // momentum, propagator prefactor and derived momenta), and one variant per
 // helicity state of its legs.  A current's storage block is
-//   [header (H(kind) doubles) | variant 0 (4 complex) | variant 1 | ...]
+//   [header (H(kind) slots) | variant 0 (4 complex) | variant 1 | ...]
 // The op table carries the child block offsets (momenta at +0) and the child
 // variant bases (fields 13-15), so no op needs to know its children's kinds.
 #pragma once
@@ -21,109 +22,130 @@ __device__ __forceinline__ Op load_op(const int4* ops, int i) {
   return Op{x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, z.x, z.y, z.z, z.w, w.x, w.y, w.z, w.w};
 }
 
-// header sizes (doubles) per op kind
-__host__ __device__ constexpr int header_size(int code) {
-  return code == OP_EXT ? 4 : (code == OP_VVV ? 18 : 6);
-}
-
-// Shared-memory storage view (contiguous).
-struct SS {
-  double* base;
-  __device__ __forceinline__ double& operator[](int off) const { return base[off]; }
-  __device__ __forceinline__ void load4(int off, cx* w) const {
+// Shared-memory storage view (contiguous 8-byte slots).
+template <class R>
+struct SST {
+  R* base;
+  __device__ __forceinline__ R& operator[](int off) const { return base[off]; }
+  __device__ __forceinline__ void load4(int off, cxT<R>* w) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = cx{base[off + 2 * j], base[off + 2 * j + 1]};
+    for (int j = 0; j < 4; ++j) w[j] = cxT<R>{(*this)[off + 2 * j], (*this)[off + 2 * j + 1]};
   }
-  __device__ __forceinline__ void store4(int off, const cx* w) const {
+  __device__ __forceinline__ void store4(int off, const cxT<R>* w) const {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      base[off + 2 * j] = w[j].r;
-      base[off + 2 * j + 1] = w[j].i;
+      (*this)[off + 2 * j] = w[j].r;
+      (*this)[off + 2 * j + 1] = w[j].i;
     }
   }
-  __device__ __forceinline__ void loadk(int off, double* k) const {
+  __device__ __forceinline__ void loadk(int off, R* k) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) k[j] = base[off + j];
+    for (int j = 0; j < 4; ++j) k[j] = (*this)[off + j];
   }
-  __device__ __forceinline__ void storek(int off, const double* k) const {
+  __device__ __forceinline__ void storek(int off, const R* k) const {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) base[off + j] = k[j];
+    for (int j = 0; j < 4; ++j) (*this)[off + j] = k[j];
   }
 };
+using SS = SST<double>;
 
 // coupling (cL, cR) of an op, g_s applied when flagged
-__device__ __forceinline__ void coupling(const KParams& P, int ci, double gs, cx& cl, cx& cr, bool& chiral) {
+template <class R>
+__device__ __forceinline__ void coupling(const KParams& P, int ci, double gs, cxT<R>& cl, cxT<R>& cr,
+                                         bool& chiral) {
+  using T = Real<R>;
   const double s = (P.cplflags[ci] & CPL_GS) ? gs : 1.0;
-  cl = cx{s * P.cpl[ci][0], s * P.cpl[ci][1]};
-  cr = cx{s * P.cpl[ci][2], s * P.cpl[ci][3]};
+  cl = {T::from(s * P.cpl[ci][0]), T::from(s * P.cpl[ci][1])};
+  cr = {T::from(s * P.cpl[ci][2]), T::from(s * P.cpl[ci][3])};
   chiral = (P.cplflags[ci] & CPL_CHIRAL) != 0;
 }
 
+// out = pref * x for the prefactor of a root bilinear: exactly i (QCD vertex) and pure
+// imaginary prefactors skip the complex multiply
+template <class R>
+__device__ __forceinline__ void apply_pref(cxT<R> pref, const cxT<R>* x, cxT<R>* out) {
+  using T = Real<R>;
+  if (T::is_zero(pref.r) && T::is_one(pref.i)) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = {-x[j].i, x[j].r};
+  } else if (T::is_zero(pref.r)) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = {-(pref.i * x[j].i), pref.i * x[j].r};
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = cmul(pref, x[j]);
+  }
+}
+
 // ================================================================ headers
-template <class S>
+template <class R, class S>
 __device__ inline void op_header(const KParams& P, const Op& o, double gs, const double* pe, const S& W) {
+  using T = Real<R>;
   if (o.code == OP_EXT) {
     const double* p = pe + 4 * o.aux;
     const double sgn = o.aux < P.nin ? 1.0 : -1.0;  // incoming momentum
-    double k[4] = {sgn * p[0], sgn * p[1], sgn * p[2], sgn * p[3]};
+    R k[4] = {T::from(sgn * p[0]), T::from(sgn * p[1]), T::from(sgn * p[2]), T::from(sgn * p[3])};
     W.storek(o.dst, k);
     return;
   }
   if (o.code == OP_BIL || o.code == OP_RBIL) {
-    // root bilinears: no propagator; a non-chiral coupling is folded into the prefactor
-    cx cl, cr;
+    // root bilinears: no propagator; a non-chiral coupling is the prefactor
+    cxT<R> cl, cr;
     bool chiral;
-    coupling(P, o.cpl, gs, cl, cr, chiral);
-    W[o.dst + 4] = chiral ? 1.0 : cl.r;
-    W[o.dst + 5] = chiral ? 0.0 : cl.i;
+    coupling<R>(P, o.cpl, gs, cl, cr, chiral);
+    W[o.dst + 4] = chiral ? T::from(1.0) : cl.r;
+    W[o.dst + 5] = chiral ? T::from(0.0) : cl.i;
     return;
   }
-  double ka[4], kb[4], k[4];
+  R ka[4], kb[4], k[4];
   W.loadk(o.a, ka);
   W.loadk(o.b, kb);
 #pragma unroll
   for (int j = 0; j < 4; ++j) k[j] = ka[j] + kb[j];
   if (o.code == OP_VVVV) {
-    double kc[4];
+    R kc[4];
     W.loadk(o.c, kc);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) k[j] += kc[j];
+    for (int j = 0; j < 4; ++j) k[j] = k[j] + kc[j];
     W.storek(o.dst, k);
-    W[o.dst + 4] = -gs * gs / msq(k);  // (-i)(-i g_s^2)/P^2
+    W[o.dst + 4] = -(T::from(gs * gs) * T::rcp(msq(k)));  // (-i)(-i g_s^2)/P^2
     return;
   }
   W.storek(o.dst, k);
   if (o.code == OP_VVV) {
     // prefactor -i g_s/P^2 = i s, s folded into the momentum combinations of the vertex
-    const double s = -gs / msq(k);
+    const R s = -(T::from(gs) * T::rcp(msq(k)));
+    const R two = T::from(2.0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      W[o.dst + 6 + j] = s * (ka[j] - kb[j]);               // s (k1 - k2)
-      W[o.dst + 10 + j] = s * fma(2.0, kb[j], ka[j]);       // s (k2 - k3) = s (k1 + 2 k2)
-      W[o.dst + 14 + j] = -s * fma(2.0, ka[j], kb[j]);      // s (k3 - k1) = -s (2 k1 + k2)
+      W[o.dst + 6 + j] = s * (ka[j] - kb[j]);            // s (k1 - k2)
+      W[o.dst + 10 + j] = s * fma(two, kb[j], ka[j]);    // s (k2 - k3) = s (k1 + 2 k2)
+      W[o.dst + 14 + j] = -(s * fma(two, ka[j], kb[j])); // s (k3 - k1) = -s (2 k1 + k2)
     }
     return;
   }
   // f f V currents: fermion propagator i/(k^2 - m^2 + i m w) (row current uses -k, same k^2),
   // vector propagator -i/(k^2 - M^2 + i M w); non-chiral couplings folded in
   const double m = P.mass[o.mass], w = P.width[o.mass];
-  const cx inv = cinv(msq(k) - m * m, m * w);
-  cx pref = o.code == OP_FFV_V ? cx{inv.i, -inv.r} : cx{-inv.i, inv.r};
-  cx cl, cr;
+  const cxT<R> inv = cinv(msq(k) - T::from(m * m), T::from(m * w));
+  cxT<R> pref = o.code == OP_FFV_V ? cxT<R>{inv.i, -inv.r} : cxT<R>{-inv.i, inv.r};
+  cxT<R> cl, cr;
   bool chiral;
-  coupling(P, o.cpl, gs, cl, cr, chiral);
+  coupling<R>(P, o.cpl, gs, cl, cr, chiral);
   if (!chiral) pref = cmul(pref, cl);
   W[o.dst + 4] = pref.r;
   W[o.dst + 5] = pref.i;
 }
 
 // ================================================================ variants
-template <class S>
+template <class R, class S>
 __device__ inline void var_ext(const KParams& P, const Op& o, int v, const double* pe, const S& W) {
-  const double* p = pe + 4 * o.aux;
+  using T = Real<R>;
+  const double* pd = pe + 4 * o.aux;
+  const R p[4] = {T::from(pd[0]), T::from(pd[1]), T::from(pd[2]), T::from(pd[3])};
   const double m = P.mass[o.mass];
   const int lam = v ? 1 : -1;
-  cx w[4];
+  cxT<R> w[4];
   switch (o.aux2) {
     case EXT_U: ext_u(p, m, lam, w); break;
     case EXT_V: ext_v(p, m, lam, w); break;
@@ -136,100 +158,105 @@ __device__ inline void var_ext(const KParams& P, const Op& o, int v, const doubl
 }
 
 // psi' = pref (kslash + m) Vslash (cL PL + cR PR) psi
-template <class S>
+template <class R, class S>
 __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs, const S& W) {
+  using T = Real<R>;
   const int hb = pdep(v, o.mdst);
-  cx psi[4], V[4];
+  cxT<R> psi[4], V[4];
   W.load4(o.va + 8 * pext(hb, o.ma), psi);
   W.load4(o.vb + 8 * pext(hb, o.mb), V);
-  double k[4];
+  R k[4];
   W.loadk(o.dst, k);
-  const cx pref = cx{W[o.dst + 4], W[o.dst + 5]};
-  const double m = P.mass[o.mass];
-  const double a00 = k[0] - k[3], a11 = k[0] + k[3];
-  const Slash Sl = slash(V);
-  cx u0 = cfma(Sl.a01, psi[3], cmul(Sl.a00, psi[2]));
-  cx u1 = cfma(Sl.a11, psi[3], cmul(Sl.a10, psi[2]));
-  cx l0 = cfma(Sl.b01, psi[1], cmul(Sl.b00, psi[0]));
-  cx l1 = cfma(Sl.b11, psi[1], cmul(Sl.b10, psi[0]));
+  const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
+  const double md = P.mass[o.mass];
+  const R a00 = k[0] - k[3], a11 = k[0] + k[3];
+  const SlashT<R> Sl = slash(V);
+  cxT<R> u0 = cfma(Sl.a01, psi[3], cmul(Sl.a00, psi[2]));
+  cxT<R> u1 = cfma(Sl.a11, psi[3], cmul(Sl.a10, psi[2]));
+  cxT<R> l0 = cfma(Sl.b01, psi[1], cmul(Sl.b00, psi[0]));
+  cxT<R> l1 = cfma(Sl.b11, psi[1], cmul(Sl.b10, psi[0]));
   if (P.cplflags[o.cpl] & CPL_CHIRAL) {
-    cx cl, cr;
+    cxT<R> cl, cr;
     bool ch;
-    coupling(P, o.cpl, gs, cl, cr, ch);
+    coupling<R>(P, o.cpl, gs, cl, cr, ch);
     u0 = cmul(cr, u0); u1 = cmul(cr, u1);
     l0 = cmul(cl, l0); l1 = cmul(cl, l1);
   }
   // upper = m phi_u + KA phi_l, lower = KB phi_u + m phi_l; KA = [[a00, -(k1-ik2)], [-(k1+ik2), a11]]
-  const cx ka01 = cx{-k[1], k[2]}, ka10 = cx{-k[1], -k[2]};
-  cx o0 = cfma(ka01, l1, rmul(a00, l0));
-  cx o1 = cfma(ka10, l0, rmul(a11, l1));
-  cx o2 = cfma(cx{k[1], -k[2]}, u1, rmul(a11, u0));
-  cx o3 = cfma(cx{k[1], k[2]}, u0, rmul(a00, u1));
-  if (m != 0.0) {
+  const cxT<R> ka01 = {-k[1], k[2]}, ka10 = {-k[1], -k[2]};
+  cxT<R> o0 = cfma(ka01, l1, rmul(a00, l0));
+  cxT<R> o1 = cfma(ka10, l0, rmul(a11, l1));
+  cxT<R> o2 = cfma(cxT<R>{k[1], -k[2]}, u1, rmul(a11, u0));
+  cxT<R> o3 = cfma(cxT<R>{k[1], k[2]}, u0, rmul(a00, u1));
+  if (md != 0.0) {
+    const R m = T::from(md);
     o0 = rfma(m, u0, o0); o1 = rfma(m, u1, o1);
     o2 = rfma(m, l0, o2); o3 = rfma(m, l1, o3);
   }
-  cx out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
+  cxT<R> out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
 // psibar' = pref psibar Vslash (cL PL + cR PR) (kslash' + m),  kslash' built from -k
-template <class S>
+template <class R, class S>
 __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double gs, const S& W) {
+  using T = Real<R>;
   const int hb = pdep(v, o.mdst);
-  cx pb[4], V[4];
+  cxT<R> pb[4], V[4];
   W.load4(o.va + 8 * pext(hb, o.ma), pb);
   W.load4(o.vb + 8 * pext(hb, o.mb), V);
-  double kin[4];
+  R kin[4];
   W.loadk(o.dst, kin);
-  const double k[4] = {-kin[0], -kin[1], -kin[2], -kin[3]};
-  const cx pref = cx{W[o.dst + 4], W[o.dst + 5]};
-  const double m = P.mass[o.mass];
-  const double a00 = k[0] - k[3], a11 = k[0] + k[3];
-  const cx ka01 = cx{-k[1], k[2]}, ka10 = cx{-k[1], -k[2]};
-  const Slash Sl = slash(V);
-  cx xu0 = cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00));
-  cx xu1 = cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01));
-  cx xl0 = cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00));
-  cx xl1 = cfma(pb[1], Sl.a11, cmul(pb[0], Sl.a01));
+  const R k[4] = {-kin[0], -kin[1], -kin[2], -kin[3]};
+  const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
+  const double md = P.mass[o.mass];
+  const R a00 = k[0] - k[3], a11 = k[0] + k[3];
+  const cxT<R> ka01 = {-k[1], k[2]}, ka10 = {-k[1], -k[2]};
+  const SlashT<R> Sl = slash(V);
+  cxT<R> xu0 = cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00));
+  cxT<R> xu1 = cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01));
+  cxT<R> xl0 = cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00));
+  cxT<R> xl1 = cfma(pb[1], Sl.a11, cmul(pb[0], Sl.a01));
   if (P.cplflags[o.cpl] & CPL_CHIRAL) {
-    cx cl, cr;
+    cxT<R> cl, cr;
     bool ch;
-    coupling(P, o.cpl, gs, cl, cr, ch);
+    coupling<R>(P, o.cpl, gs, cl, cr, ch);
     xu0 = cmul(cl, xu0); xu1 = cmul(cl, xu1);
     xl0 = cmul(cr, xl0); xl1 = cmul(cr, xl1);
   }
   // x (kslash + m) = (m x_u + x_l KB, x_u KA + m x_l)
-  cx o0 = cfma(xl1, cx{-ka10.r, -ka10.i}, rmul(a11, xl0));
-  cx o1 = cfma(xl0, cx{-ka01.r, -ka01.i}, rmul(a00, xl1));
-  cx o2 = cfma(xu1, ka10, rmul(a00, xu0));
-  cx o3 = cfma(xu0, ka01, rmul(a11, xu1));
-  if (m != 0.0) {
+  cxT<R> o0 = cfma(xl1, cneg(ka10), rmul(a11, xl0));
+  cxT<R> o1 = cfma(xl0, cneg(ka01), rmul(a00, xl1));
+  cxT<R> o2 = cfma(xu1, ka10, rmul(a00, xu0));
+  cxT<R> o3 = cfma(xu0, ka01, rmul(a11, xu1));
+  if (md != 0.0) {
+    const R m = T::from(md);
     o0 = rfma(m, xu0, o0); o1 = rfma(m, xu1, o1);
     o2 = rfma(m, xl0, o2); o3 = rfma(m, xl1, o3);
   }
-  cx out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
+  cxT<R> out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
 // J = pref (C - k (k.C)/M^2),  C^mu = cL rbar_l sigmabar^mu c_L + cR rbar_u sigma^mu c_R
-template <class S>
+// (also the column root bilinear, without propagator)
+template <class R, class S>
 __device__ inline void var_ffv_v(const KParams& P, const Op& o, int v, double gs, const S& W) {
+  using T = Real<R>;
   const int hb = pdep(v, o.mdst);
-  cx r[4], c[4];
+  cxT<R> r[4], c[4];
   W.load4(o.va + 8 * pext(hb, o.ma), r);
   W.load4(o.vb + 8 * pext(hb, o.mb), c);
-  const cx pref = cx{W[o.dst + 4], W[o.dst + 5]};
-  const cx R00 = cmul(r[0], c[2]), R11 = cmul(r[1], c[3]), R01 = cmul(r[0], c[3]), R10 = cmul(r[1], c[2]);
-  const cx L00 = cmul(r[2], c[0]), L11 = cmul(r[3], c[1]), L01 = cmul(r[2], c[1]), L10 = cmul(r[3], c[0]);
-  const cx Rv[4] = {R00 + R11, R01 + R10, cx{-(R10.i - R01.i), R10.r - R01.r}, R00 - R11};
-  const cx Lv[4] = {L00 + L11, cx{-(L01.r + L10.r), -(L01.i + L10.i)}, cx{L10.i - L01.i, -(L10.r - L01.r)},
-                    cx{-(L00.r - L11.r), -(L00.i - L11.i)}};
-  cx C[4];
+  const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
+  const cxT<R> R00 = cmul(r[0], c[2]), R11 = cmul(r[1], c[3]), R01 = cmul(r[0], c[3]), R10 = cmul(r[1], c[2]);
+  const cxT<R> L00 = cmul(r[2], c[0]), L11 = cmul(r[3], c[1]), L01 = cmul(r[2], c[1]), L10 = cmul(r[3], c[0]);
+  const cxT<R> Rv[4] = {R00 + R11, R01 + R10, cxT<R>{-(R10.i - R01.i), R10.r - R01.r}, R00 - R11};
+  const cxT<R> Lv[4] = {L00 + L11, cneg(L01 + L10), cxT<R>{L10.i - L01.i, -(L10.r - L01.r)}, cneg(L00 - L11)};
+  cxT<R> C[4];
   if (P.cplflags[o.cpl] & CPL_CHIRAL) {
-    cx cl, cr;
+    cxT<R> cl, cr;
     bool ch;
-    coupling(P, o.cpl, gs, cl, cr, ch);
+    coupling<R>(P, o.cpl, gs, cl, cr, ch);
 #pragma unroll
     for (int j = 0; j < 4; ++j) C[j] = cfma(cl, Lv[j], cmul(cr, Rv[j]));
   } else {
@@ -238,129 +265,112 @@ __device__ inline void var_ffv_v(const KParams& P, const Op& o, int v, double gs
   }
   const double M = P.mass[o.mass];
   if (M > 0.0) {
-    double k[4];
+    R k[4];
     W.loadk(o.dst, k);
-    const cx f = rmul(1.0 / (M * M), rdot(k, C));
+    const cxT<R> f = rmul(T::from(1.0 / (M * M)), rdot(k, C));
 #pragma unroll
     for (int j = 0; j < 4; ++j) C[j] = C[j] - rmul(k[j], f);
   }
-  cx out[4];
-  if (pref.r == 0.0 && pref.i == 1.0) {            // pure i (QCD root bilinear): no multiply
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cx{-C[j].i, C[j].r};
-  } else if (pref.r == 0.0) {                        // pure imaginary
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cx{-pref.i * C[j].i, pref.i * C[j].r};
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cmul(pref, C[j]);
-  }
+  cxT<R> out[4];
+  apply_pref(pref, C, out);
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
 // row bilinear R = pref psibar_root Vslash (cL PL + cR PR): a row spinor, closed later by R . psi
-template <class S>
+template <class R, class S>
 __device__ inline void var_rbil(const KParams& P, const Op& o, int v, double gs, const S& W) {
   const int hb = pdep(v, o.mdst);
-  cx pb[4], V[4];
+  cxT<R> pb[4], V[4];
   W.load4(o.va + 8 * pext(hb, o.ma), pb);
   W.load4(o.vb + 8 * pext(hb, o.mb), V);
-  const cx pref = cx{W[o.dst + 4], W[o.dst + 5]};
-  const Slash Sl = slash(V);
+  const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
+  const SlashT<R> Sl = slash(V);
   // psibar Vslash = (psibar_l B, psibar_u A)
-  cx x[4] = {cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00)), cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01)),
-             cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00)), cfma(pb[1], Sl.a11, cmul(pb[0], Sl.a01))};
+  cxT<R> x[4] = {cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00)), cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01)),
+                 cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00)), cfma(pb[1], Sl.a11, cmul(pb[0], Sl.a01))};
   if (P.cplflags[o.cpl] & CPL_CHIRAL) {
-    cx cl, cr;
+    cxT<R> cl, cr;
     bool ch;
-    coupling(P, o.cpl, gs, cl, cr, ch);
+    coupling<R>(P, o.cpl, gs, cl, cr, ch);
     x[0] = cmul(cl, x[0]); x[1] = cmul(cl, x[1]);
     x[2] = cmul(cr, x[2]); x[3] = cmul(cr, x[3]);
   }
-  cx out[4];
-  if (pref.r == 0.0 && pref.i == 1.0) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cx{-x[j].i, x[j].r};
-  } else if (pref.r == 0.0) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cx{-pref.i * x[j].i, pref.i * x[j].r};
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cmul(pref, x[j]);
-  }
+  cxT<R> out[4];
+  apply_pref(pref, x, out);
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
 // J^r = i [ (e1.e2) s(k1-k2)^r + e2^r (s(k2-k3).e1) + e1^r (s(k3-k1).e2) ],  s = -g_s/P^2
-template <class S>
+template <class R, class S>
 __device__ inline void var_vvv(const KParams& P, const Op& o, int v, const S& W) {
   const int hb = pdep(v, o.mdst);
-  cx e1[4], e2[4];
+  cxT<R> e1[4], e2[4];
   W.load4(o.va + 8 * pext(hb, o.ma), e1);
   W.load4(o.vb + 8 * pext(hb, o.mb), e2);
-  double d[4], q1[4], q2[4];
+  R d[4], q1[4], q2[4];
   W.loadk(o.dst + 6, d);
   W.loadk(o.dst + 10, q1);
   W.loadk(o.dst + 14, q2);
-  const cx s12 = mdot(e1, e2);
-  const cx a1 = rdot(q1, e1);
-  const cx a2 = rdot(q2, e2);
-  cx out[4];
+  const cxT<R> s12 = mdot(e1, e2);
+  const cxT<R> a1 = rdot(q1, e1);
+  const cxT<R> a2 = rdot(q2, e2);
+  cxT<R> out[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const cx t = cfma(e1[j], a2, cfma(e2[j], a1, rmul(d[j], s12)));
-    out[j] = cx{-t.i, t.r};
+    const cxT<R> t = cfma(e1[j], a2, cfma(e2[j], a1, rmul(d[j], s12)));
+    out[j] = {-t.i, t.r};
   }
   W.store4(o.dst + 18 + 8 * v, out);
 }
 
 // J = s { j=0: (e1.e3) e2 - (e2.e3) e1 ; j=1: (e1.e2) e3 - (e2.e3) e1 ; j=2: (e1.e2) e3 - (e1.e3) e2 }
-template <class S>
+template <class R, class S>
 __device__ inline void var_vvvv(const KParams& P, const Op& o, int v, const S& W) {
   const int hb = pdep(v, o.mdst);
-  cx e1[4], e2[4], e3[4];
+  cxT<R> e1[4], e2[4], e3[4];
   W.load4(o.va + 8 * pext(hb, o.ma), e1);
   W.load4(o.vb + 8 * pext(hb, o.mb), e2);
   W.load4(o.vc + 8 * pext(hb, o.mc), e3);
-  const double s = W[o.dst + 4];
-  cx out[4];
+  const R s = W[o.dst + 4];
+  cxT<R> out[4];
   if (o.aux == 0) {
-    const cx x = rmul(s, mdot(e1, e3)), y = rmul(-s, mdot(e2, e3));
+    const cxT<R> x = rmul(s, mdot(e1, e3)), y = rmul(-s, mdot(e2, e3));
 #pragma unroll
     for (int j = 0; j < 4; ++j) out[j] = cfma(x, e2[j], cmul(y, e1[j]));
   } else if (o.aux == 1) {
-    const cx x = rmul(s, mdot(e1, e2)), y = rmul(-s, mdot(e2, e3));
+    const cxT<R> x = rmul(s, mdot(e1, e2)), y = rmul(-s, mdot(e2, e3));
 #pragma unroll
     for (int j = 0; j < 4; ++j) out[j] = cfma(x, e3[j], cmul(y, e1[j]));
   } else {
-    const cx x = rmul(s, mdot(e1, e2)), y = rmul(-s, mdot(e1, e3));
+    const cxT<R> x = rmul(s, mdot(e1, e2)), y = rmul(-s, mdot(e1, e3));
 #pragma unroll
     for (int j = 0; j < 4; ++j) out[j] = cfma(x, e3[j], cmul(y, e2[j]));
   }
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
-template <class S>
+template <class R, class S>
 __device__ inline void op_variant(const KParams& P, const Op& o, int v, double gs, const double* pe, const S& W) {
   switch (o.code) {
-    case OP_EXT: var_ext(P, o, v, pe, W); break;
-    case OP_FFV_F: var_ffv_f(P, o, v, gs, W); break;
-    case OP_FFV_FB: var_ffv_fb(P, o, v, gs, W); break;
+    case OP_EXT: var_ext<R>(P, o, v, pe, W); break;
+    case OP_FFV_F: var_ffv_f<R>(P, o, v, gs, W); break;
+    case OP_FFV_FB: var_ffv_fb<R>(P, o, v, gs, W); break;
     case OP_FFV_V:
-    case OP_BIL: var_ffv_v(P, o, v, gs, W); break;   // the bilinear is the vertex current without propagator
-    case OP_RBIL: var_rbil(P, o, v, gs, W); break;
-    case OP_VVV: var_vvv(P, o, v, W); break;
-    default: var_vvvv(P, o, v, W); break;
+    case OP_BIL: var_ffv_v<R>(P, o, v, gs, W); break;   // the column bilinear is the vertex current without propagator
+    case OP_RBIL: var_rbil<R>(P, o, v, gs, W); break;
+    case OP_VVV: var_vvv<R>(P, o, v, W); break;
+    default: var_vvvv<R>(P, o, v, W); break;
   }
 }
 
 // add phase(code) * a to (re, im)
-__device__ __forceinline__ void add_phase(double& jr, double& ji, int code, cx a) {
+template <class R>
+__device__ __forceinline__ void add_phase(R& jr, R& ji, int code, cxT<R> a) {
   switch (code) {
-    case 0: jr += a.r; ji += a.i; break;   // +1
-    case 1: jr -= a.i; ji += a.r; break;   // +i
-    case 2: jr -= a.r; ji -= a.i; break;   // -1
-    default: jr += a.i; ji -= a.r; break;  // -i
+    case 0: jr = jr + a.r; ji = ji + a.i; break;   // +1
+    case 1: jr = jr - a.i; ji = ji + a.r; break;   // +i
+    case 2: jr = jr - a.r; ji = ji - a.i; break;   // -1
+    default: jr = jr + a.i; ji = ji - a.r; break;  // -i
   }
 }
 
@@ -370,16 +380,17 @@ __device__ __forceinline__ void add_phase(double& jr, double& ji, int code, cx a
 // of the term's column current, Minkowski dot with its vector current) or amp_t = R . psi_C
 // (kind 1: row bilinear R = psibar Vslash (..), spinor dot with the column current); couplings
 // are inside the bilinears.  AMP op fields: aux = first term, aux2 = terms, cpl = first flow, mass = flows.
-template <class S>
-__device__ __forceinline__ cx group_amp(const int4* terms, const Op& o, int h, const S& W) {
-  cx acc{0.0, 0.0};
+template <class R, class S>
+__device__ __forceinline__ cxT<R> group_amp(const int4* terms, const Op& o, int h, const S& W) {
+  const R zero = Real<R>::from(0.0);
+  cxT<R> acc{zero, zero};
   for (int t = 0; t < o.aux2; ++t) {
     const int4 a = __ldg(terms + 2 * (o.aux + t));
     const int4 b = __ldg(terms + 2 * (o.aux + t) + 1);
-    cx X[4], Y[4];
+    cxT<R> X[4], Y[4];
     W.load4(a.x + 8 * pext(h, a.y), X);
     W.load4(a.z + 8 * pext(h, a.w), Y);
-    cx amp;
+    cxT<R> amp;
     if (b.y == 0) {
       amp = mdot(X, Y);
     } else {
