@@ -386,8 +386,6 @@ def run_gpu(args):
         achieved = flops / launch_s / 1e12
         peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
         peak_inst = FP32_PEAK_GINST if f32 else FP64_PEAK_GINST
-        tc_chunks = -(-nevt * proc.ngood * proc.ncol * 16 // (2 << 30)) if args.mode.startswith("mixed_") and \
-            args.mode != "mixed_fp32" else 0
         per_evt = _traffic_per_event("me_kernel", WORKLOAD)
         line = {"metric": METRIC.replace("FP64", {"fp64": "FP64", "mixed_fp32": "mixed FP32 colour sum",
                                                    "mixed_tf32": "tcgen05 TF32 colour sum",
@@ -412,7 +410,7 @@ def run_gpu(args):
                              "flops_per_event": flops / nevt},
                 "e2e": {"value": world * nevt / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": args.steps * (4 * tc_chunks if tc_chunks else 1),
+                "gpu_launches": args.steps * proc.kernel_launches(nevt, mode),
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu,
                 "wall_s_timed": wall}

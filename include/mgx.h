@@ -208,6 +208,11 @@ int mgx_process_autotune(mgx_process* proc, int64_t nevt, const double* momenta,
 double mgx_fp64_ops_per_event(const mgx_process* proc, int mode);
 double mgx_fp64_flops_per_event(const mgx_process* proc, int mode);
 
+/* Number of this library's kernels one mgx_compute of nevt events in `mode` launches with the
+ * process's current settings (1, or 4 per chunk in the tensor-core modes); -1 on invalid
+ * arguments. */
+int mgx_kernel_launches(const mgx_process* proc, int64_t nevt, int mode);
+
 /* Allocation-free variant of mgx_compute.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory where they evaluate matrix elements,
  * e.g. a Fortran event-generation loop with no CUDA allocator of its own, or a plugin inside a

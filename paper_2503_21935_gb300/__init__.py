@@ -60,6 +60,7 @@ def lib():
             "mgx_compute_host": (I, [P, I64, P, P, P, P, P, P, P, I, P, SZ, P]),
             "mgx_fp64_ops_per_event": (D, [P, I]),
             "mgx_fp64_flops_per_event": (D, [P, I]),
+            "mgx_kernel_launches": (I, [P, I64, I]),
             "mgx_process_set_kernel": (I, [P, I]),
             "mgx_process_get_kernel": (I, [P]),
             "mgx_process_set_blocks_per_sm": (I, [P, I]),
@@ -396,6 +397,13 @@ class Process:
     def fp64_flops_per_event(self, mode=MGX_FP64):
         """Float64 flops per event (fma counted as two)."""
         return lib().mgx_fp64_flops_per_event(self._h, mode)
+
+    def kernel_launches(self, nevt, mode=MGX_FP64):
+        """Kernels one compute() of nevt events launches."""
+        n = lib().mgx_kernel_launches(self._h, nevt, mode)
+        if n < 0:
+            raise MgxError("mgx_kernel_launches: invalid argument")
+        return n
 
     def compute(self, momenta, alpha_s, rnd_hel=None, rnd_col=None, mode=MGX_FP64, mh=False, colw=False,
                 stream=None, out=None):

@@ -1,7 +1,8 @@
 // Tensor-core colour sum (modes MGX_MIXED_TF32 and MGX_MIXED_BF16X3), the one dense
 // contraction of the path.
 //
-// The jamps of a batch form a real matrix X with one row per (event, good helicity, Re/Im):
+// The jamps of a batch (rounded to float32) form a real matrix X with one row per (event, good
+// helicity, Re/Im):
 // row r = 2 (e ngood + ih) + part, K = ncol.  With the colour matrix scaled to integers,
 // Cs = den C, Y = X Cs is a tcgen05.mma tile of M = 128 rows (f32 accumulate in tensor memory)
 // and |M_h|^2 = (x_Re . y_Re + x_Im . y_Im) / den.  Both operands are split into sums of
@@ -59,7 +60,7 @@ __host__ __device__ inline size_t colour_tc_smem(int kpad, int npad) {
 
 template <class F>
 __global__ void __launch_bounds__(kTcRows)
-    colour_tc_kernel(const double* __restrict__ jamps, int64_t nrows, int ncol, int kpad, int npad,
+    colour_tc_kernel(const float* __restrict__ jamps, int64_t nrows, int ncol, int kpad, int npad,
                      uint32_t tmem_cols, const unsigned char* __restrict__ bcanon, double inv_den,
                      double* __restrict__ mh, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -91,9 +92,9 @@ __global__ void __launch_bounds__(kTcRows)
   for (int64_t tile = blockIdx.x; tile * kTcRows < nrows; tile += gridDim.x) {
     const int64_t r = tile * kTcRows + tid;
     const bool valid = r < nrows;
-    const double* xr = jamps + (r >> 1) * 2 * ncol + (r & 1);
+    const float* xr = jamps + (r >> 1) * 2 * ncol + (r & 1);
     for (int k = 0; k < kpad; ++k) {
-      const float x = (valid && k < ncol) ? (float)__ldg(xr + 2 * k) : 0.0f;
+      const float x = (valid && k < ncol) ? __ldg(xr + 2 * k) : 0.0f;
       F::split(x, a, umma::kmajor_offset((uint32_t)tid, (uint32_t)k, (uint32_t)kpad, F::kElem));
     }
     umma::fence_proxy_async_smem();
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kTcRows)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int k = c0 + j;
-        if (valid && k < ncol) acc = fmaf((float)__ldg(xr + 2 * k), y[j], acc);
+        if (valid && k < ncol) acc = fmaf(__ldg(xr + 2 * k), y[j], acc);
       }
     }
     const float other = __shfl_xor_sync(0xffffffffu, acc, 1);

@@ -36,7 +36,8 @@ struct mgx_program_desc {
   int ws_doubles, ndiag, nterm, avg_den;
   int gs_power;          // power of g_s of every amplitude (vertices are evaluated with g_s = 1)
   int col_den;           // common denominator of the colour matrix
-  int counts[11];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows, groups
+  int counts[12];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows,
+                         // groups, runs (terms sharing one bilinear within a group)
   struct {
     int nops;
     const int32_t* ops;
@@ -179,7 +180,7 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
                                   const double* __restrict__ rcol, double* __restrict__ me,
                                   int32_t* __restrict__ selhel, int32_t* __restrict__ selcol,
                                   double* __restrict__ mh_out, double* __restrict__ colw_out, int mode,
-                                  double* __restrict__ jexp, double* __restrict__ colw_exp) {
+                                  float* __restrict__ jexp, double* __restrict__ colw_exp) {
   using T = Real<R>;
   const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
   const double scale = coupling_scale(P, alphas[e]);
@@ -204,9 +205,10 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
   }
   if constexpr (std::is_same<R, double>::value) {
     if (mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3) {
-      // export the jamps [ngood][ncol][re, im] and the colour weights for the tensor-core colour sum
+      // export the jamps [ngood][ncol][re, im] rounded to float32 (as in the mixed mode: the
+      // tensor-core kernel then needs no float64 conversions) and the colour weights
       const int nj = 2 * P.ncol * P.ngood;
-      for (int i = 0; i < nj; ++i) jexp[e * nj + i] = W[P.jamp_off + i];
+      for (int i = 0; i < nj; ++i) jexp[e * nj + i] = (float)W[P.jamp_off + i];
       for (int i = 0; i < P.ncol; ++i) {
         double w = 0.0;
         for (int ih = 0; ih < P.ngood; ++ih) {
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(kThreads)
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
               int32_t* __restrict__ selhel, int32_t* __restrict__ selcol, double* __restrict__ mh_out,
               double* __restrict__ colw_out, double* __restrict__ ws, int64_t nthreads, int mode,
-              double* __restrict__ jexp, double* __restrict__ colw_exp) {
+              float* __restrict__ jexp, double* __restrict__ colw_exp) {
   extern __shared__ double smem[];
   const int npar4 = 4 * P.npar;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -667,10 +669,12 @@ struct TcPlan {
 
 TcPlan tc_plan(const mgx_process* pr, const KParams& kp, int64_t nevt) {
   TcPlan t;
-  const size_t per_evt = (size_t)kp.ngood * kp.ncol * 2 * sizeof(double);
+  const size_t per_evt = (size_t)kp.ngood * kp.ncol * 2 * sizeof(float);
+  // a chunk is a whole number of passes of the persistent grid (a partial pass would leave most
+  // threads idle), as many as about 4 GiB of exported jamps allow
   const int64_t full = grid_threads(pr, std::max<int64_t>(nevt, 1));
-  const int64_t budget = (int64_t)(((size_t)2 << 30) / per_evt);       // about 2 GiB of exported jamps
-  t.chunk = std::min<int64_t>(std::max<int64_t>(nevt, 1), std::max<int64_t>(full, budget / kThreads * kThreads));
+  const int64_t budget = (int64_t)(((size_t)4 << 30) / per_evt);
+  t.chunk = std::min<int64_t>(std::max<int64_t>(nevt, 1), std::max<int64_t>(1, budget / full) * full);
   t.ws = align256((size_t)grid_threads(pr, t.chunk) * kp.ws_doubles * sizeof(double));
   t.jexp = align256((size_t)t.chunk * per_evt);
   t.colw = align256((size_t)t.chunk * kp.ncol * sizeof(double));
@@ -698,7 +702,7 @@ int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mo
   if (ws == nullptr || wsb < t.total) return MGX_ERR_WORKSPACE_TOO_SMALL;
   char* p = (char*)ws;
   double* w_thr = (double*)p; p += t.ws;
-  double* jexp = (double*)p; p += t.jexp;
+  float* jexp = (float*)p; p += t.jexp;
   double* colw = (double*)p; p += t.colw;
   double* mhb = (double*)p; p += t.mh;
   int* err = (int*)p;
@@ -865,6 +869,7 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
   for (int i = 0; i < prog->nmass && i < MAXMASS; ++i) {
     kp.mass[i] = param_value(prm, prog->mass[2 * i]);
     kp.width[i] = param_value(prm, prog->mass[2 * i + 1]);
+    kp.massive[i] = kp.mass[i] > 0.0 ? 1 : 0;
   }
   // device tables
   const int n = prog->ncol;
@@ -1123,15 +1128,25 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   const double n = pr->prog->ncol;
   struct K { double fma, mul, add; };
   const K ffv_f{56, 24, 10}, ffv_v{24, 24, 24}, bil{16, 16, 24}, rbil{24, 8, 8}, vvv{58, 14, 0},
-      vvvv{52, 16, 0}, term{14, 2, 2}, flow{0, 0, 2};
+      vvvv{52, 16, 0}, run{14, 2, 0}, term_add{0, 0, 8}, run_add{0, 0, 2}, flow{0, 0, 2};
   auto w = [&](const K& k) { return flops ? 2 * k.fma + k.mul + k.add : k.fma + k.mul + k.add; };
   double t = w(ffv_f) * (c[0] + c[1]) + w(ffv_v) * c[2] + w(vvv) * c[3] + w(vvvv) * c[4] + w(bil) * c[5] +
              w(rbil) * c[6];
-  t += ngood * (w(term) * c[8] + w(flow) * c[9]);
+  // per good helicity: one product per run, a 4-vector add per further term of a run, an add per
+  // further run of a group, and an add per (group, flow)
+  t += ngood * (w(run) * c[11] + w(term_add) * (c[8] - c[11]) + w(run_add) * (c[11] - c[10]) + w(flow) * c[9]);
   if (mode == MGX_FP64) t += ngood * (flops ? 2 * n * n + 4 * n : n * n + 3 * n);  // quadratic form
   else if (!flops) t += ngood * 2 * n;                                              // f64 -> f32 conversions
   t += ngood * (flops ? 4 * n : 2 * n);                                             // colour weights
   return t;
+}
+
+int mgx_kernel_launches(const mgx_process* pr, int64_t nevt, int mode) {
+  if (!pr || nevt < 0 || !mode_ok(mode)) return -1;
+  if (nevt == 0) return 0;
+  if (!mode_tc(mode)) return 1;
+  const int64_t chunk = tc_plan(pr, pr->kp, nevt).chunk;
+  return (int)(4 * ((nevt + chunk - 1) / chunk));   // amplitudes, colour sum, finish, error mark
 }
 
 double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) { return pr ? fp64_work(pr, mode, false) : 0.0; }

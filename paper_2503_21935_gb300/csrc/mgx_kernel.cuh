@@ -45,6 +45,7 @@ struct KParams {
   double cpl[MAXCPL][4]; // cL.re cL.im cR.re cR.im
   int cplflags[MAXCPL];
   double mass[MAXMASS], width[MAXMASS];
+  int massive[MAXMASS];  // mass[i] > 0, tested without a float64 compare
   int good[MAXHEL];      // canonical indices of the good helicities
 };
 

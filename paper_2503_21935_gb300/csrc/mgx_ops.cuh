@@ -61,13 +61,13 @@ __device__ __forceinline__ void coupling(const KParams& P, int ci, double gs, cx
 }
 
 // out = pref * x for the prefactor of a root bilinear: exactly i (QCD vertex) and pure
-// imaginary prefactors skip the complex multiply
+// imaginary prefactors skip the complex multiply (an exact +0.0 real part is tested by bits)
 template <class R>
 __device__ __forceinline__ void apply_pref(cxT<R> pref, const cxT<R>* x, cxT<R>* out) {
   using T = Real<R>;
   if (T::is_zero(pref.r) && T::is_one(pref.i)) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = {-x[j].i, x[j].r};
+    for (int j = 0; j < 4; ++j) out[j] = {T::neg(x[j].i), x[j].r};
   } else if (T::is_zero(pref.r)) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) out[j] = {-(pref.i * x[j].i), pref.i * x[j].r};
@@ -188,7 +188,7 @@ __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs
   cxT<R> o1 = cfma(ka10, l0, rmul(a11, l1));
   cxT<R> o2 = cfma(cxT<R>{k[1], -k[2]}, u1, rmul(a11, u0));
   cxT<R> o3 = cfma(cxT<R>{k[1], k[2]}, u0, rmul(a00, u1));
-  if (md != 0.0) {
+  if (P.massive[o.mass]) {
     const R m = T::from(md);
     o0 = rfma(m, u0, o0); o1 = rfma(m, u1, o1);
     o2 = rfma(m, l0, o2); o3 = rfma(m, l1, o3);
@@ -229,7 +229,7 @@ __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double g
   cxT<R> o1 = cfma(xl0, cneg(ka01), rmul(a00, xl1));
   cxT<R> o2 = cfma(xu1, ka10, rmul(a00, xu0));
   cxT<R> o3 = cfma(xu0, ka01, rmul(a11, xu1));
-  if (md != 0.0) {
+  if (P.massive[o.mass]) {
     const R m = T::from(md);
     o0 = rfma(m, xu0, o0); o1 = rfma(m, xu1, o1);
     o2 = rfma(m, xl0, o2); o3 = rfma(m, xl1, o3);
@@ -264,7 +264,7 @@ __device__ inline void var_ffv_v(const KParams& P, const Op& o, int v, double gs
     for (int j = 0; j < 4; ++j) C[j] = Lv[j] + Rv[j];
   }
   const double M = P.mass[o.mass];
-  if (M > 0.0) {
+  if (P.massive[o.mass]) {
     R k[4];
     W.loadk(o.dst, k);
     const cxT<R> f = rmul(T::from(1.0 / (M * M)), rdot(k, C));
@@ -318,7 +318,7 @@ __device__ inline void var_vvv(const KParams& P, const Op& o, int v, const S& W)
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const cxT<R> t = cfma(e1[j], a2, cfma(e2[j], a1, rmul(d[j], s12)));
-    out[j] = {-t.i, t.r};
+    out[j] = {Real<R>::neg(t.i), t.r};
   }
   W.store4(o.dst + 18 + 8 * v, out);
 }
@@ -375,31 +375,62 @@ __device__ __forceinline__ void add_phase(R& jr, R& ji, int code, cxT<R> a) {
 }
 
 // ================================================================ diagram amplitudes
+// phase(code) * a, code 0..3 for 1, i, -1, -i: a swap of the parts and sign flips done on the
+// sign bits (integer operations, no floating-point arithmetic)
+__device__ __forceinline__ double neg_if(double x, bool c) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
+}
+__device__ __forceinline__ float neg_if(float x, bool c) {
+  return __int_as_float(__float_as_int(x) ^ ((int)c << 31));
+}
+template <class R>
+__device__ __forceinline__ cxT<R> rot_phase(int code, cxT<R> a) {
+  const bool swap = code & 1;
+  const R r = swap ? a.i : a.r, i = swap ? a.r : a.i;
+  return {neg_if(r, code == 1 || code == 2), neg_if(i, code >= 2)};
+}
+
 // A group of diagram terms sharing one colour vector (up to a phase): sum over the group of
-// phase_t * amp_t(h), where amp_t = Q . V (kind 0: column bilinear Q^mu = psibar gamma^mu (..) psi_C
-// of the term's column current, Minkowski dot with its vector current) or amp_t = R . psi_C
-// (kind 1: row bilinear R = psibar Vslash (..), spinor dot with the column current); couplings
-// are inside the bilinears.  AMP op fields: aux = first term, aux2 = terms, cpl = first flow, mass = flows.
+// phase_t * amp_t(h), where amp_t = X_t . Y_t with X_t a root bilinear and Y_t the term's other
+// current: kind 0, Q . V (column bilinear Q^mu = psibar gamma^mu (..) psi_C, Minkowski dot with
+// the vector current) or kind 1, R . psi_C (row bilinear R = psibar Vslash (..), spinor dot with
+// the column current); couplings are inside the bilinears.  Terms sharing a bilinear are adjacent
+// (a run): the run's phased Y_t are summed first and closed with one product.
+// AMP op fields: aux = first term, aux2 = terms, cpl = first flow, mass = flows.
+// Term entry: (X base, X mask, Y base, Y mask), (phase, kind, run start, run end).
 template <class R, class S>
 __device__ __forceinline__ cxT<R> group_amp(const int4* terms, const Op& o, int h, const S& W) {
   const R zero = Real<R>::from(0.0);
-  cxT<R> acc{zero, zero};
+  cxT<R> acc{zero, zero}, sum[4];
+  bool first_run = true;
   for (int t = 0; t < o.aux2; ++t) {
     const int4 a = __ldg(terms + 2 * (o.aux + t));
     const int4 b = __ldg(terms + 2 * (o.aux + t) + 1);
-    cxT<R> X[4], Y[4];
-    W.load4(a.x + 8 * pext(h, a.y), X);
+    cxT<R> Y[4];
     W.load4(a.z + 8 * pext(h, a.w), Y);
-    cxT<R> amp;
-    if (b.y == 0) {
-      amp = mdot(X, Y);
+    if (b.z) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sum[j] = rot_phase(b.x, Y[j]);
     } else {
-      amp = cmul(X[0], Y[0]);
-      amp = cfma(X[1], Y[1], amp);
-      amp = cfma(X[2], Y[2], amp);
-      amp = cfma(X[3], Y[3], amp);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sum[j] = sum[j] + rot_phase(b.x, Y[j]);
     }
-    add_phase(acc.r, acc.i, b.x, amp);
+    if (b.w) {
+      cxT<R> X[4];
+      W.load4(a.x + 8 * pext(h, a.y), X);
+      cxT<R> amp;
+      if (b.y == 0) {
+        amp = mdot(X, sum);
+      } else {
+        amp = cmul(X[0], sum[0]);
+        amp = cfma(X[1], sum[1], amp);
+        amp = cfma(X[2], sum[2], amp);
+        amp = cfma(X[3], sum[3], amp);
+      }
+      if (first_run) acc = amp;
+      else acc = acc + amp;
+      first_run = false;
+    }
   }
   return acc;
 }

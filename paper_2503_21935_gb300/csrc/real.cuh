@@ -16,8 +16,13 @@ template <> struct Real<double> {
   __device__ __forceinline__ static double sqrt_(double x) { return ::sqrt(x); }
   __device__ __forceinline__ static double max0(double x) { return x > 0.0 ? x : 0.0; }
   __device__ __forceinline__ static bool positive(double x) { return x > 0.0; }
-  __device__ __forceinline__ static bool is_zero(double x) { return x == 0.0; }
-  __device__ __forceinline__ static bool is_one(double x) { return x == 1.0; }
+  // exact +0.0 / 1.0 and sign flips as bit operations on the integer pipe (the float64 pipe is
+  // the bottleneck of the amplitude code)
+  __device__ __forceinline__ static bool is_zero(double x) { return __double_as_longlong(x) == 0ll; }
+  __device__ __forceinline__ static bool is_one(double x) { return __double_as_longlong(x) == 0x3FF0000000000000ll; }
+  __device__ __forceinline__ static double neg(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+  }
 };
 
 template <> struct Real<float> {
@@ -27,8 +32,9 @@ template <> struct Real<float> {
   __device__ __forceinline__ static float sqrt_(float x) { return sqrtf(x); }
   __device__ __forceinline__ static float max0(float x) { return x > 0.0f ? x : 0.0f; }
   __device__ __forceinline__ static bool positive(float x) { return x > 0.0f; }
-  __device__ __forceinline__ static bool is_zero(float x) { return x == 0.0f; }
-  __device__ __forceinline__ static bool is_one(float x) { return x == 1.0f; }
+  __device__ __forceinline__ static bool is_zero(float x) { return __float_as_int(x) == 0; }
+  __device__ __forceinline__ static bool is_one(float x) { return __float_as_int(x) == 0x3F800000; }
+  __device__ __forceinline__ static float neg(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
 };
 
 }  // namespace mgx

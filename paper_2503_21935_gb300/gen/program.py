@@ -222,19 +222,25 @@ class _Builder:
         return op
 
     def amp_row(self, group, offset, flows, terms):
-        """One AMP row per term group: term table entries (bil base, bil mask, vec base, vec mask,
-        phase, 0, 0, 0) and the group's (flow, phase) list."""
+        """One AMP row per term group: term table entries (bil base, bil mask, other base, other mask,
+        phase, kind, run start, run end) and the group's (flow, phase) list.  Terms closing on the same
+        bilinear are adjacent and form a run: the kernel sums the run's phased other operands first
+        and takes one product with the bilinear per run (distributivity)."""
         D = self.D
         tis, phases, fl = group
         op = [0] * NFIELD
         op[0] = OP_AMP
         op[11] = len(terms) // 8
         op[12] = len(tis)
-        for ti, ph in zip(tis, phases):
+        key = lambda ti: (D.terms[ti].bil, D.terms[ti].kind)
+        items = sorted(zip(tis, phases), key=lambda x: key(x[0]))
+        for k, (ti, ph) in enumerate(items):
             t = D.terms[ti]
             bil, oth = D.currents[t.bil], D.currents[t.other]
+            start = k == 0 or key(items[k - 1][0]) != key(ti)
+            end = k == len(items) - 1 or key(items[k + 1][0]) != key(ti)
             terms += [self.varbase(t.bil, offset), self.hmask(bil.mask), self.varbase(t.other, offset),
-                      self.hmask(oth.mask), ph, t.kind, 0, 0]
+                      self.hmask(oth.mask), ph, t.kind, int(start), int(end)]
         op[9] = len(flows) // 2
         op[10] = len(fl)
         for f, ph in fl:
@@ -499,6 +505,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
         if op[0] == OP_AMP:
             counts["amp_flows"] += op[10]
             counts["amp_terms"] = counts.get("amp_terms", 0) + op[12]
+            counts["amp_runs"] = counts.get("amp_runs", 0) + sum(terms[8 * (op[11] + k) + 6] for k in range(op[12]))
         elif op[0] != OP_EXT:
             counts["var_" + k] += 1 << bin(op[5]).count("1")
     # CTA schedule: largest chunk whose store fits the shared-memory budget
