@@ -104,6 +104,30 @@ class MatrixElement:
             out["selcol"] = select(out["colw"], rnd_col)
         return out
 
+    def condition(self, p, alpha_s, trials=4, seed=0):
+        """Relative condition estimate of me per event (reading P11 of the hot-path scope table):
+        the larger of
+          kappa_terms = sum_h sum_ij |C_ij| a_i(h) a_j(h) / sum_h |M_h|^2, a_i(h) = sum_t |k_ti A_t(h)|
+            (relative perturbations eps of every diagram term move me by at most ~2 eps kappa_terms),
+          kappa_in = max over `trials` random one-ulp sign perturbations of every momentum component
+            of |me' / me - 1| / 2^-52 (the sensitivity to the rounding of the summed momenta that
+            propagator denominators and vertices see, which kappa_terms does not measure).
+        An event with kappa * 1e-16 > 1e-12 cannot be expected to agree to 1e-12 between two
+        float64 evaluation orders: it is cancellation-limited."""
+        A = self.p.term_amplitudes(p, alpha_s)               # [nterm, nevt, nhel]
+        a = np.einsum("tes,tc->esc", np.abs(A), np.abs(self.k))
+        bound = np.einsum("esc,cd,esd->e", a, np.abs(self.C), a)
+        J = np.einsum("tes,tc->esc", A, self.k)
+        me = self.helicity_weights(J).sum(axis=1)
+        kappa = bound / me
+        rng = np.random.default_rng(seed)
+        ulp = 2.0 ** -52
+        for _ in range(trials):
+            q = p * (1.0 + ulp * rng.choice([-1.0, 1.0], size=p.shape))
+            me2 = self.helicity_weights(self.jamps(q, alpha_s)).sum(axis=1)
+            kappa = np.maximum(kappa, np.abs(me2 / me - 1.0) / ulp)
+        return kappa
+
     def me_bruteforce_colour(self, p, alpha_s):
         """Explicit sum over every colour configuration (small processes only)."""
         P = self.p

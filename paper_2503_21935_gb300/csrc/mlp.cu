@@ -8,8 +8,8 @@
 //   backward  dZ_prev = (dZ W) * silu'(Z_prev)          (A = dZ, B = W^T)
 //   weights   dW = dZ^T X                                (A = dZ^T, B = X^T; contraction over the batch)
 // The output layer (256 -> 1), the loss, bias gradients and Adam are plain SIMT kernels.
-// Two-stage unweighting uses the surrogate as described by Danziger, Janssen, Schumann and
-// Siegert (arXiv:2109.11964); see mgx_unweight_* below.
+// The two-stage unweighting that uses the surrogate (Danziger, Janssen, Schumann, Siegert,
+// arXiv:2109.11964) is in unweight.cu.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

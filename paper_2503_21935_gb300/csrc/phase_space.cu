@@ -85,11 +85,45 @@ __global__ void rambo_kernel(int64_t n, int64_t first, double sqrts, int nf, con
       xi -= step;
       if (fabs(step) <= 1e-15 * xi) break;
     }
-    double sk = 0.0, prod = 1.0, sk2e = 0.0;
     for (int j = 0; j < nf; ++j) {
       const double e0 = p[j][0];
       p[j][0] = sqrt(masses[j] * masses[j] + xi * xi * e0 * e0);
       for (int k = 1; k < 4; ++k) p[j][k] *= xi;
+    }
+  }
+  // Repair: the boost loses digits when the generated momenta are nearly collinear, so remove
+  // the residual three-momentum in proportion to the energies, rescale the three-momenta so the
+  // energies (recomputed from them) add up to sqrt(s), and put every particle on its mass shell.
+  {
+    double r[3] = {0.0, 0.0, 0.0}, esum = 0.0;
+    for (int j = 0; j < nf; ++j) {
+      esum += p[j][0];
+      for (int k = 0; k < 3; ++k) r[k] += p[j][1 + k];
+    }
+    double k2[kMaxFinal];
+    for (int j = 0; j < nf; ++j) {
+      const double f = p[j][0] / esum;
+      for (int k = 0; k < 3; ++k) p[j][1 + k] -= r[k] * f;
+      k2[j] = p[j][1] * p[j][1] + p[j][2] * p[j][2] + p[j][3] * p[j][3];
+    }
+    double xi = 1.0;
+    for (int it = 0; it < 8; ++it) {
+      double fv = -sqrts, df = 0.0;
+      for (int j = 0; j < nf; ++j) {
+        const double en = sqrt(masses[j] * masses[j] + xi * xi * k2[j]);
+        fv += en;
+        df += xi * k2[j] / en;
+      }
+      xi -= fv / df;
+    }
+    for (int j = 0; j < nf; ++j) {
+      for (int k = 1; k < 4; ++k) p[j][k] *= xi;
+      p[j][0] = sqrt(masses[j] * masses[j] + p[j][1] * p[j][1] + p[j][2] * p[j][2] + p[j][3] * p[j][3]);
+    }
+  }
+  if (massive) {
+    double sk = 0.0, prod = 1.0, sk2e = 0.0;
+    for (int j = 0; j < nf; ++j) {
       const double kabs = sqrt(p[j][1] * p[j][1] + p[j][2] * p[j][2] + p[j][3] * p[j][3]);
       sk += kabs;
       prod *= kabs / p[j][0];

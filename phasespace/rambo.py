@@ -4,7 +4,8 @@
 Momenta are returned as float64 arrays [nevt, n, 4] holding (E, px, py, pz) in GeV
 in the partonic centre-of-mass frame.  Massive final states are obtained from
 the massless configuration by the common rescaling factor xi solved with Newton
-iterations, as in the RAMBO paper.
+iterations, as in the RAMBO paper.  A final repair step restores momentum
+conservation and the mass shells to rounding level.
 """
 import math
 import numpy as np
@@ -26,6 +27,29 @@ def rambo_massless_weight(n, sqrts):
     po2 = 0.5 * math.pi
     w = po2 ** (n - 1) * sqrts ** (2 * n - 4) / (math.gamma(n) * math.gamma(n - 1))
     return w * (2.0 * math.pi) ** (4 - 3 * n)
+
+
+def _repair(p, masses, sqrts):
+    """Restore exact kinematics to rounding level.  The RAMBO boost loses digits when the
+    generated massless momenta are nearly collinear (Q nearly lightlike): the outgoing momenta
+    then miss momentum conservation and the mass shell by up to ~1e-11 relative, and amplitudes
+    evaluated from them depend at that level on which momenta a formula uses.  Step 1 removes
+    the residual three-momentum in proportion to the energies; step 2 rescales all
+    three-momenta by the factor xi with sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = sqrt(s) (Newton,
+    from xi = 1) and recomputes every energy from its three-momentum."""
+    p = p.copy()
+    r = p[..., 1:].sum(axis=1)
+    p[..., 1:] -= r[:, None, :] * (p[..., 0] / p[..., 0].sum(axis=1, keepdims=True))[..., None]
+    k2 = (p[..., 1:] ** 2).sum(axis=-1)
+    m2 = np.asarray(masses, dtype=np.float64)[None, :] ** 2
+    xi = np.ones(p.shape[0])
+    for _ in range(8):
+        e = np.sqrt(m2 + xi[:, None] ** 2 * k2)
+        step = (e.sum(axis=1) - sqrts) / (xi[:, None] * k2 / e).sum(axis=1)
+        xi = xi - step
+    p[..., 1:] *= xi[:, None, None]
+    p[..., 0] = np.sqrt(m2 + (p[..., 1:] ** 2).sum(axis=-1))
+    return p
 
 
 def rambo(nevt, sqrts, masses, seed, stream=0):
@@ -56,7 +80,7 @@ def rambo(nevt, sqrts, masses, seed, stream=0):
                                      + a[:, None, None] * bq[..., None] * b[:, None, :])
     w = np.full(nevt, rambo_massless_weight(n, sqrts))
     if not np.any(masses > 0.0):
-        return p, w
+        return _repair(p, masses, sqrts), w
     if masses.sum() >= sqrts:
         raise ValueError("final-state masses exceed sqrt(s)")
     # Newton iteration for xi: sum_i sqrt(m_i^2 + xi^2 E_i^2) = sqrts (massless |p_i| = E_i)
@@ -74,6 +98,7 @@ def rambo(nevt, sqrts, masses, seed, stream=0):
     k = np.empty_like(p)
     k[..., 1:] = xi[:, None, None] * p[..., 1:]
     k[..., 0] = np.sqrt(m2 + (xi[:, None] * e0) ** 2)
+    k = _repair(k, masses, sqrts)
     kabs = np.sqrt((k[..., 1:] ** 2).sum(axis=-1))
     wt = (kabs.sum(axis=1) / sqrts) ** (2 * n - 3)
     wt = wt * np.prod(kabs / k[..., 0], axis=1) * sqrts / (kabs ** 2 / k[..., 0]).sum(axis=1)

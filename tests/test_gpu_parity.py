@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path through the C ABI against the float64 oracle, element by element.
 
 Bar (float64 path): per-event relative deviation of me, and of every per-helicity
-|M_h|^2 and colour weight relative to the event total, at most 1e-12; helicity and
-colour selection bit-exact except where a cumulative weight lies within 1e-12 of
+|M_h|^2 and colour weight relative to the event total, at most 1e-12, except for events
+the oracle's condition estimate marks cancellation-limited (reported, held to 1e-14 x kappa);
+helicity and colour selection bit-exact except where a cumulative weight lies within 1e-12 of
 the random threshold.
 """
 import numpy as np
@@ -14,6 +15,23 @@ from oracle.matrix_element import get as oracle_get, near_tie
 TOL = 1e-12
 
 pytestmark = pytest.mark.gpu
+
+
+def _bounds(process, mom, a, rel):
+    """Per-event bound on a relative deviation: TOL, except for events the oracle marks
+    cancellation-limited (condition estimate kappa with kappa * 1e-16 > TOL, reading P11), which
+    are reported and held to 100 x 1e-16 x kappa instead.  Such events must stay rare."""
+    bound = np.full(rel.shape[0], TOL)
+    bad = np.flatnonzero(rel.reshape(rel.shape[0], -1).max(axis=1) > TOL)
+    if bad.size:
+        kappa = oracle_get(process).condition(mom[bad], a[bad])
+        limited = kappa * 1e-16 > TOL
+        for e, k in zip(bad, kappa):
+            print(f"{process}: event {e} deviates {rel[e].max():.2e}, condition estimate {k:.3g}"
+                  + (" (cancellation-limited)" if k * 1e-16 > TOL else ""))
+        bound[bad[limited]] = 1e-14 * kappa[limited]
+        assert limited.sum() <= max(1, rel.shape[0] // 50), "too many cancellation-limited events"
+    return bound if rel.ndim == 1 else bound[:, None]
 
 _procs = {}
 
@@ -56,13 +74,15 @@ def test_parity_fp64(name, nevt, kernel):
         proc.set_kernel(0)
     ref = oracle_get(wl.process).evaluate(mom, a, rh, rc)
     rel = np.abs(got["me"] / ref["me"] - 1.0)
-    assert rel.max() <= TOL, f"me: max rel {rel.max():.3e}"
+    assert np.all(rel <= _bounds(wl.process, mom, a, rel)), f"me: max rel {rel.max():.3e}"
     tot = ref["mh"].sum(axis=1, keepdims=True)
     good = proc.good_helicities
     assert np.abs(ref["mh"][:, [h for h in range(proc.nhel) if h not in good]]).max(initial=0.0) == 0.0
-    assert (np.abs(got["mh"] - ref["mh"][:, good]) / tot).max() <= TOL
+    dmh = np.abs(got["mh"] - ref["mh"][:, good]) / tot
+    assert np.all(dmh <= _bounds(wl.process, mom, a, dmh))
     ctot = ref["colw"].sum(axis=1, keepdims=True)
-    assert (np.abs(got["colw"] - ref["colw"]) / ctot).max() <= TOL
+    dcw = np.abs(got["colw"] - ref["colw"]) / ctot
+    assert np.all(dcw <= _bounds(wl.process, mom, a, dcw))
     tie_h = near_tie(ref["mh"], rh, TOL)
     tie_c = near_tie(ref["colw"], rc, TOL)
     assert np.array_equal(got["selhel"][~tie_h], ref["selhel"][~tie_h])
@@ -104,7 +124,8 @@ def test_parity_tensor_core_colour_sum(name, nevt, bound, mode):
     tot = ref["mh"].sum(axis=1, keepdims=True)
     assert (np.abs(got["mh"] - ref["mh"][:, proc.good_helicities]) / tot).max() <= bound
     # colour weights come from the float64 jamps in every mode
-    assert (np.abs(got["colw"] - ref["colw"]) / ref["colw"].sum(axis=1, keepdims=True)).max() <= TOL
+    dcw = np.abs(got["colw"] - ref["colw"]) / ref["colw"].sum(axis=1, keepdims=True)
+    assert np.all(dcw <= _bounds(wl.process, mom, a, dcw))
     tie_c = near_tie(ref["colw"], rc, TOL)
     assert np.array_equal(got["selcol"][~tie_c], ref["selcol"][~tie_c])
 
@@ -157,7 +178,8 @@ def test_ragged_sizes(nevt):
     mom, a, rh, rc = make_inputs(wl, nevt)
     got = _run(_proc(wl.process), mom, a, rh, rc)
     ref = oracle_get(wl.process).evaluate(mom, a)
-    assert np.abs(got["me"] / ref["me"] - 1.0).max() <= TOL
+    rel = np.abs(got["me"] / ref["me"] - 1.0)
+    assert np.all(rel <= _bounds(wl.process, mom, a, rel))
 
 
 def test_empty_batch_and_errors():

@@ -38,12 +38,12 @@ def test_rambo_matches_host(masses):
     cond = Q[:, 0] ** 2 / (Q[:, 0] ** 2 - (Q[:, 1:] ** 2).sum(1))
     assert np.all(dev <= np.maximum(1e-13, 1e-15 * cond))
     assert np.abs(wt.cpu().numpy() / hw[100:] - 1).max() < 1e-9
-    # the device momenta themselves are physical: conservation and mass shells
-    assert np.abs(d[:, 2:].sum(1) - d[:, :2].sum(1)).max() < 1e-9 * sqrts
+    # the device momenta themselves are physical: after the repair step, conservation and mass
+    # shells hold to rounding whatever the boost's conditioning
+    assert np.abs(d[:, 2:].sum(1) - d[:, :2].sum(1)).max() < 1e-14 * sqrts
     m2 = d[:, 2:, 0] ** 2 - (d[:, 2:, 1:] ** 2).sum(-1)
-    # the same conditioning limits how well massless outputs sit on m = 0
     rel = np.abs(m2 - np.asarray(masses) ** 2) / d[:, 2:, 0] ** 2
-    assert np.all(rel.max(axis=1) <= np.maximum(1e-13, 1e-14 * cond))
+    assert rel.max() <= 1e-14
 
 
 def test_cuts_match_numpy():

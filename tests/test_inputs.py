@@ -21,13 +21,14 @@ def test_philox_known_answers():
 
 @pytest.mark.parametrize("masses", [[0.0, 0.0, 0.0, 0.0], [173.0, 173.0, 0.0, 0.0, 0.0]])
 def test_rambo_conservation_and_shell(masses):
-    p, w = rambo(2000, 1500.0, masses, seed=3)
+    p, w = rambo(20000, 1500.0, masses, seed=3)
     tot = p.sum(axis=1)
-    assert np.allclose(tot[:, 0], 1500.0, rtol=0, atol=1e-9)
-    assert np.abs(tot[:, 1:]).max() < 1e-9
+    # to rounding level (the repair step), including the nearly collinear events whose boost
+    # loses digits
+    assert np.abs(tot[:, 0] - 1500.0).max() < 1e-14 * 1500.0
+    assert np.abs(tot[:, 1:]).max() < 1e-14 * 1500.0
     m2 = p[..., 0] ** 2 - (p[..., 1:] ** 2).sum(-1)
-    for i, m in enumerate(masses):
-        assert np.allclose(np.sqrt(np.abs(m2[:, i])), m, atol=2e-4)
+    assert (np.abs(m2 - np.asarray(masses) ** 2) / p[..., 0] ** 2).max() < 1e-14
     assert np.all(w > 0)
 
 

@@ -238,3 +238,32 @@ def test_ew_qcd_process_colour_and_gauge():
     J = me.jamps(p, a)
     for leg in (0, 4, 5):
         assert np.abs(me.jamps(p, a, gauge_leg=leg)).max() / (np.abs(J).max() * p[:, leg, 0].max()) < 1e-13
+
+
+def test_condition_estimate():
+    """The parity tests' condition estimate: at least 1 (triangle inequality on the diagram sum),
+    modest for the two-diagram e+e- -> mu+mu-, and larger where a propagator nearly goes on shell
+    (a gluon pair made nearly collinear in g g > t t~ g g)."""
+    me = get("e+ e- > mu+ mu-")
+    p, a, _, _ = make_inputs(WORKLOADS["eemumu"], 64)
+    k = me.condition(p, a)
+    assert np.all(k >= 1.0) and k.max() < 1e3
+    me4 = get("g g > t t~ g g")
+    p, a, _, _ = make_inputs(WORKLOADS["ggttgg"], 8)
+    k0 = me4.condition(p, a)
+    q = p.copy()
+    # rotate gluon 5 onto gluon 4's direction up to 1e-6 rad, keeping its energy; the top pair
+    # absorbs the three-momentum change (energy conservation is irrelevant to the estimate)
+    d = q[:, 4, 1:] / np.linalg.norm(q[:, 4, 1:], axis=1, keepdims=True)
+    perp = np.cross(d, [0.0, 0.0, 1.0])
+    perp /= np.linalg.norm(perp, axis=1, keepdims=True)
+    n5 = d + 1e-6 * perp
+    n5 /= np.linalg.norm(n5, axis=1, keepdims=True)
+    new5 = q[:, 5, :1] * n5
+    shift = (new5 - q[:, 5, 1:]) / 2
+    q[:, 5, 1:] = new5
+    for t in (2, 3):
+        q[:, t, 1:] -= shift
+        q[:, t, 0] = np.sqrt(173.0 ** 2 + (q[:, t, 1:] ** 2).sum(-1))
+    k1 = me4.condition(q, a)
+    assert np.all(k0 >= 1.0) and np.median(k1) > 100 * np.median(k0)
