@@ -153,7 +153,7 @@ def _source_sha():
 
 def _traffic_per_event(kernel, workload):
     """DRAM bytes per event of `kernel` from the committed ncu summary, if taken on this source."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         d = json.load(open(path))
         e = d[f"{kernel}:{workload}"]

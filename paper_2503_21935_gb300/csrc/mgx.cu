@@ -298,7 +298,9 @@ struct BatchDesc {
   int64_t item_start[kMaxBatch + 1];
 };
 
-__global__ void __launch_bounds__(kThreads)
+// (register budget of 4 resident blocks per SM, as the thread-per-event kernel gets by default:
+// occupancy hides the workspace latency better than the few registers more would)
+__global__ void __launch_bounds__(kThreads, 4)
     batch_kernel(const KParams* __restrict__ params, const BatchIOArray io, const BatchDesc D,
                  unsigned long long* __restrict__ counter, double* __restrict__ ws, int64_t nthreads, int mode) {
   extern __shared__ double smem[];
