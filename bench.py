@@ -386,7 +386,8 @@ def run_gpu(args):
         achieved = flops / launch_s / 1e12
         peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
         peak_inst = FP32_PEAK_GINST if f32 else FP64_PEAK_GINST
-        per_evt = _traffic_per_event("me_kernel", WORKLOAD)
+        per_evt = _traffic_per_event("me_kernel_float" if f32 else "me_kernel", WORKLOAD) \
+            if args.mode in ("fp64", "float") else None
         line = {"metric": METRIC.replace("FP64", {"fp64": "FP64", "mixed_fp32": "mixed FP32 colour sum",
                                                    "mixed_tf32": "tcgen05 TF32 colour sum",
                                                    "mixed_bf16x3": "tcgen05 BF16x3 colour sum",
