@@ -11,27 +11,9 @@ import pytest
 
 from phasespace import WORKLOADS, make_inputs, rambo, incoming_beams
 from oracle.matrix_element import get as oracle_get, near_tie
-
-TOL = 1e-12
+from _parity import TOL, bounds as _bounds
 
 pytestmark = pytest.mark.gpu
-
-
-def _bounds(process, mom, a, rel):
-    """Per-event bound on a relative deviation: TOL, except for events the oracle marks
-    cancellation-limited (condition estimate kappa with kappa * 1e-16 > TOL, reading P11), which
-    are reported and held to 100 x 1e-16 x kappa instead.  Such events must stay rare."""
-    bound = np.full(rel.shape[0], TOL)
-    bad = np.flatnonzero(rel.reshape(rel.shape[0], -1).max(axis=1) > TOL)
-    if bad.size:
-        kappa = oracle_get(process).condition(mom[bad], a[bad])
-        limited = kappa * 1e-16 > TOL
-        for e, k in zip(bad, kappa):
-            print(f"{process}: event {e} deviates {rel[e].max():.2e}, condition estimate {k:.3g}"
-                  + (" (cancellation-limited)" if k * 1e-16 > TOL else ""))
-        bound[bad[limited]] = 1e-14 * kappa[limited]
-        assert limited.sum() <= max(1, rel.shape[0] // 50), "too many cancellation-limited events"
-    return bound if rel.ndim == 1 else bound[:, None]
 
 _procs = {}
 
@@ -180,6 +162,43 @@ def test_ragged_sizes(nevt):
     ref = oracle_get(wl.process).evaluate(mom, a)
     rel = np.abs(got["me"] / ref["me"] - 1.0)
     assert np.all(rel <= _bounds(wl.process, mom, a, rel))
+
+
+def _degenerate_events():
+    """Hand-built events on the special branches of the spinor and polarisation code: particles
+    exactly along +z and -z (massless and massive), massive particles at rest."""
+    out = {}
+    e = 250.0
+    beams = [[e, 0, 0, e], [e, 0, 0, -e]]
+    out["e+ e- > mu+ mu-"] = np.array([beams + [[e, 0, 0, e], [e, 0, 0, -e]],
+                                       beams + [[e, 0, 0, -e], [e, 0, 0, e]],
+                                       beams + [[e, e, 0, 0], [e, -e, 0, 0]]], dtype=float)
+    mt = 173.0
+    out["g g > t t~"] = np.array([[[mt, 0, 0, mt], [mt, 0, 0, -mt], [mt, 0, 0, 0], [mt, 0, 0, 0]],
+                                  [[750, 0, 0, 750], [750, 0, 0, -750], [750, 0, 0, np.sqrt(750 ** 2 - mt ** 2)],
+                                   [750, 0, 0, -np.sqrt(750 ** 2 - mt ** 2)]]], dtype=float)
+    # a final gluon along the beam axis would make a t-channel propagator vanish (collinear
+    # singularity), so the 2 -> 3 event puts the gluon along +x and the tops back to back in z
+    pz = np.sqrt(600.0 ** 2 - mt ** 2 - 150.0 ** 2)
+    out["g g > t t~ g"] = np.array([[[750, 0, 0, 750], [750, 0, 0, -750], [600, -150, 0, pz], [600, -150, 0, -pz],
+                                     [300, 300, 0, 0]]], dtype=float)
+    return out
+
+
+def test_degenerate_kinematics():
+    for proc_name, mom in _degenerate_events().items():
+        n = mom.shape[0]
+        a = np.full(n, 0.118)
+        rh = np.linspace(0.1, 0.9, n)
+        rc = np.linspace(0.2, 0.8, n)
+        proc = _proc(proc_name)
+        got = _run(proc, mom, a, rh, rc)
+        ref = oracle_get(proc_name).evaluate(mom, a, rh, rc)
+        assert np.all(np.isfinite(got["me"]))
+        rel = np.abs(got["me"] / ref["me"] - 1.0)
+        assert np.all(rel <= _bounds(proc_name, mom, a, rel)), f"{proc_name}: max rel {rel.max():.3e}"
+        tot = ref["mh"].sum(axis=1, keepdims=True)
+        assert (np.abs(got["mh"] - ref["mh"][:, proc.good_helicities]) / tot).max() <= TOL
 
 
 def test_empty_batch_and_errors():
