@@ -164,6 +164,14 @@ def _traffic_per_event(kernel, workload):
     return None
 
 
+def _workload_config(nevt, mode):
+    from phasespace import WORKLOADS
+    wl = WORKLOADS[WORKLOAD]
+    return {"workload": f"g g > t t~ g g, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, alpha_s=0.118",
+            "process": wl.process, "nevt_per_gpu": nevt, "mode": mode,
+            "l2": "inputs larger than L2 (192 MiB momenta, 4.3 GB workspace)"}
+
+
 # ------------------------------------------------------------------ reference arm (oracle)
 def run_reference(args):
     rank, world, _ = _dist()
@@ -181,8 +189,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(b for _, _, b in rates),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "g g > t t~ g g, flat RAMBO, sqrt(s)=1500 GeV, bounded sample per step",
-                       "nevt_per_step": n},
+            "config": dict(_workload_config(args.nevt, args.mode),
+                           sample=f"each step evaluates {n} events of this workload on the host cores"),
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_core} events per core x {cores} spawn processes per step"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -266,7 +274,8 @@ def extra_batched(pkg, dev, stream):
         b.capture(inputs, outs, side)
         ms_b = _timed(lambda: b.replay(side), 3, 1, side)
     return {"events": total, "batched_graph": {"value": total / (ms_b * 1e-3), "unit": "events/s", "ms": ms_b,
-                                               "blocks_per_sm": bps, "events_per_item": epi},
+                                               "blocks_per_sm": bps, "events_per_item": dict(zip(
+                                                   [name for name, _ in sets], epi))},
             "sequential": {"value": total / (ms_seq * 1e-3), "unit": "events/s", "ms": ms_seq}}
 
 
@@ -283,17 +292,26 @@ def extra_surrogate(pkg, dev):
     U.calibrate(1 << 20)
     res = {"training": {"events": 1 << 22, "steps": 4000, "batch": 8192, "seconds": train_s,
                         "loss_first": hist[0][1], "loss_last": hist[-1][1]}}
-    for name, fn in (("plain", U.plain), ("surrogate", U.two_stage)):
+    # the two-stage leg runs until 10^6 unweighted events; the plain leg (about 8x slower per
+    # unweighted event) is timed over a fixed 4 batches, its rate being what is compared
+    for name, fn, target, nbatch in (("plain", U.plain, None, 4), ("surrogate", U.two_stage, 1000000, None)):
         fn(1 << 20, seed=900)                      # warm-up
         torch.cuda.synchronize()
+        n_unw = gen = calls = over = 0
+        b = 0
         t0 = time.perf_counter()
-        r = fn(1 << 22, seed=901)
+        while (target is not None and n_unw < target) or (nbatch is not None and b < nbatch):
+            r = fn(1 << 22, seed=901 + b)
+            n_unw += int(r["weight"].shape[0])
+            gen += r["generated"]
+            calls += r["exact_calls"]
+            over += int((r["weight"] > 1).sum().item())
+            b += 1
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        n_unw = int(r["weight"].shape[0])
-        res[name] = {"value": n_unw / dt, "unit": "unweighted events/s", "generated": r["generated"],
-                     "unweighted": n_unw, "exact_me_calls": r["exact_calls"], "seconds": dt,
-                     "overweight_fraction": float((r["weight"] > 1).float().mean().item()) if n_unw else None}
+        res[name] = {"value": n_unw / dt, "unit": "unweighted events/s", "generated": gen,
+                     "unweighted": n_unw, "exact_me_calls": calls, "seconds": dt, "batches": b,
+                     "overweight_fraction": over / n_unw if n_unw else None}
     res["gain"] = res["surrogate"]["value"] / res["plain"]["value"] if res["plain"]["value"] else None
     return res
 
@@ -396,10 +414,8 @@ def run_gpu(args):
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed_fp32": "f64+f32", "mixed_tf32": "f64+tf32", "mixed_bf16x3": "f64+bf16",
                           "float": "f32"}[args.mode], "data": "synthetic",
-                "config": {"workload": f"g g > t t~ g g, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, "
-                                       "alpha_s=0.118", "process": wl.process, "nevt_per_gpu": nevt,
-                           "mode": args.mode, "ngood": proc.ngood, "ndiagrams": proc.ndiagrams,
-                           "ncol": proc.ncol, "l2": "inputs larger than L2 (192 MiB momenta, ~1 GiB workspace)"},
+                "config": dict(_workload_config(nevt, args.mode), ngood=proc.ngood, ndiagrams=proc.ndiagrams,
+                               ncol=proc.ncol),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak,
                              "traffic": None if per_evt is None else per_evt * nevt,

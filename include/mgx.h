@@ -189,8 +189,10 @@ int mgx_batch_compute(mgx_batch* batch, const mgx_batch_io* io, int mode, void* 
 int mgx_batch_capture(mgx_batch* batch, const mgx_batch_io* io, int mode, void* workspace, size_t workspace_bytes,
                       void* stream);
 int mgx_batch_replay(mgx_batch* batch, void* stream);
-/* Autotuner: times the batched launch on these buffers for blocks per SM in {2, 4} and
- * events per work item in {128, 512, 2048}, keeps the fastest.  Synchronous. */
+/* Autotuner: times the batched launch on these buffers, first for blocks per SM in {2, 3, 4} x
+ * one common work-item size in {128, 512, 2048}, then each process's own work-item size in
+ * {64, ..., 4096} in turn with the others fixed; keeps the fastest schedule for later launches
+ * and captures.  events_per_item: NULL or [nproc] (the chosen size per process).  Synchronous. */
 int mgx_batch_autotune(mgx_batch* batch, const mgx_batch_io* io, int mode, void* workspace,
                        size_t workspace_bytes, void* stream, int* blocks_per_sm, int* events_per_item);
 /* Autotuner of a single process: times mgx_compute on these inputs for the thread-per-event

@@ -105,8 +105,8 @@ class MatrixElement:
         return out
 
     def condition(self, p, alpha_s, trials=4, seed=0):
-        """Relative condition estimate of me per event (reading P11 of the hot-path scope table):
-        the larger of
+        """Relative condition estimate of me per event, used to tell cancellation-limited events
+        from real deviations in the float64 parity comparison: the larger of
           kappa_terms = sum_h sum_ij |C_ij| a_i(h) a_j(h) / sum_h |M_h|^2, a_i(h) = sum_t |k_ti A_t(h)|
             (relative perturbations eps of every diagram term move me by at most ~2 eps kappa_terms),
           kappa_in = max over `trials` random one-ulp sign perturbations of every momentum component

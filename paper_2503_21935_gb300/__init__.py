@@ -217,11 +217,13 @@ class Batch:
         _check(lib().mgx_batch_replay(self._h, ctypes.c_void_p(stream.cuda_stream)), "mgx_batch_replay")
 
     def autotune(self, inputs, outputs, mode=MGX_FP64):
+        """Returns (blocks per SM, [events per work item of each process])."""
         io = self._make_io(inputs, outputs)
-        b, e = ctypes.c_int(), ctypes.c_int()
+        b = ctypes.c_int()
+        e = (ctypes.c_int * len(self.procs))()
         _check(lib().mgx_batch_autotune(self._h, io, mode, _ptr(self.ws), self.ws.numel(), _stream(self.ws.device),
-                                        ctypes.byref(b), ctypes.byref(e)), "mgx_batch_autotune")
-        return b.value, e.value
+                                        ctypes.byref(b), e), "mgx_batch_autotune")
+        return b.value, list(e)
 
 
 class Mlp:

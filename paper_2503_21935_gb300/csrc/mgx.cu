@@ -294,7 +294,8 @@ struct BatchIOArray {
 };
 
 struct BatchDesc {
-  int nproc, events_per_item, max_npar4;
+  int nproc, max_npar4;
+  int epi[kMaxBatch];    // events per work item, per process
   int64_t item_start[kMaxBatch + 1];
 };
 
@@ -319,8 +320,8 @@ __global__ void __launch_bounds__(kThreads, 4)
     const KParams& P = params[p];
     const BatchIO b = io.io[p];
     const int npar4 = 4 * P.npar;
-    const int64_t first = (item - D.item_start[p]) * D.events_per_item;
-    const int64_t last = min(first + (int64_t)D.events_per_item, b.nevt);
+    const int64_t first = (item - D.item_start[p]) * D.epi[p];
+    const int64_t last = min(first + (int64_t)D.epi[p], b.nevt);
     for (int64_t base = first; base < last; base += blockDim.x) {
       stage_momenta(b.mom, base, min((int64_t)blockDim.x, last - base), npar4, smem);
       const int64_t e = base + threadIdx.x;
@@ -1163,7 +1164,7 @@ struct mgx_batch {
   std::vector<mgx_process*> procs;
   KParams* d_params = nullptr;
   int blocks_per_sm = 4;
-  int events_per_item = 512;
+  std::vector<int> epi;       // events per work item, per process
   int max_ws = 0, max_npar4 = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1174,14 +1175,17 @@ namespace {
 constexpr int kBatchMaxBlocksPerSm = 4;
 
 int batch_launch(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_t wsb, cudaStream_t st,
-                 int blocks_per_sm, int epi) {
+                 int blocks_per_sm, const int* epi) {
   const int n = (int)b->procs.size();
   BatchDesc D{};
   D.nproc = n;
-  D.events_per_item = epi;
   D.max_npar4 = b->max_npar4;
   D.item_start[0] = 0;
-  for (int p = 0; p < n; ++p) D.item_start[p + 1] = D.item_start[p] + (io[p].nevt + epi - 1) / epi;
+  for (int p = 0; p < n; ++p) {
+    if (epi[p] < 1) return MGX_ERR_INVALID_ARGUMENT;
+    D.epi[p] = epi[p];
+    D.item_start[p + 1] = D.item_start[p] + (io[p].nevt + epi[p] - 1) / epi[p];
+  }
   BatchIO ios[kMaxBatch];
   for (int p = 0; p < n; ++p) {
     if (io[p].nevt < 0 || (io[p].nevt > 0 && (!io[p].momenta || !io[p].alpha_s || !io[p].me))) return MGX_ERR_INVALID_ARGUMENT;
@@ -1214,6 +1218,7 @@ extern "C" int mgx_batch_create(mgx_process* const* procs, int nproc, mgx_batch*
   mgx_batch* b = new mgx_batch();
   b->device = procs[0]->device;
   std::vector<KParams> kp;
+  b->epi.assign(nproc, 512);
   for (int p = 0; p < nproc; ++p) {
     b->procs.push_back(procs[p]);
     kp.push_back(procs[p]->kp);
@@ -1254,7 +1259,7 @@ extern "C" int mgx_batch_compute(mgx_batch* b, const mgx_batch_io* io, int mode,
   int cur = 0;
   if (cudaGetDevice(&cur) != cudaSuccess) return MGX_ERR_CUDA;
   if (cur != b->device) return MGX_ERR_DEVICE_MISMATCH;
-  return batch_launch(b, io, mode, ws, wsb, (cudaStream_t)stream, b->blocks_per_sm, b->events_per_item);
+  return batch_launch(b, io, mode, ws, wsb, (cudaStream_t)stream, b->blocks_per_sm, b->epi.data());
 }
 
 extern "C" int mgx_batch_capture(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_t wsb, void* stream) {
@@ -1264,7 +1269,7 @@ extern "C" int mgx_batch_capture(mgx_batch* b, const mgx_batch_io* io, int mode,
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MGX_ERR_CUDA;
-  const int rc = batch_launch(b, io, mode, ws, wsb, st, b->blocks_per_sm, b->events_per_item);
+  const int rc = batch_launch(b, io, mode, ws, wsb, st, b->blocks_per_sm, b->epi.data());
   cudaGraph_t g = nullptr;
   const bool ended = cudaStreamEndCapture(st, &g) == cudaSuccess;
   if (rc != MGX_OK) {
@@ -1285,32 +1290,53 @@ extern "C" int mgx_batch_replay(mgx_batch* b, void* stream) {
 extern "C" int mgx_batch_autotune(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_t wsb, void* stream,
                                   int* blocks_per_sm, int* events_per_item) {
   if (!b || !io) return MGX_ERR_INVALID_ARGUMENT;
+  if (mode != MGX_FP64 && mode != MGX_MIXED_FP32) return MGX_ERR_UNSUPPORTED_MODE;
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  const int n = (int)b->procs.size();
+  // time one schedule: a warm-up launch, then two timed launches
+  auto timed = [&](int bps, const std::vector<int>& epi, float* ms) -> int {
+    int rc = batch_launch(b, io, mode, ws, wsb, st, bps, epi.data());
+    if (rc != MGX_OK) return rc;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2; ++r) batch_launch(b, io, mode, ws, wsb, st, bps, epi.data());
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return MGX_ERR_CUDA;
+    cudaEventElapsedTime(ms, e0, e1);
+    return MGX_OK;
+  };
   float best = 1e30f;
-  int bb = b->blocks_per_sm, be = b->events_per_item;
-  const int bps_c[] = {2, 4};
-  const int epi_c[] = {128, 512, 2048};
-  for (int bps : bps_c)
-    for (int epi : epi_c) {
-      int rc = batch_launch(b, io, mode, ws, wsb, st, bps, epi);   // warm-up
-      if (rc != MGX_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < 2; ++r) batch_launch(b, io, mode, ws, wsb, st, bps, epi);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return MGX_ERR_CUDA; }
+  int bb = b->blocks_per_sm;
+  std::vector<int> be = b->epi;
+  int rc = MGX_OK;
+  // stage 1: blocks per SM x one common work-item size
+  for (int bps : {2, 3, 4})
+    for (int e : {128, 512, 2048}) {
+      std::vector<int> cand(n, e);
       float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; bb = bps; be = epi; }
+      if ((rc = timed(bps, cand, &ms)) != MGX_OK) break;
+      if (ms < best) { best = ms; bb = bps; be = cand; }
+    }
+  // stage 2: each process's work-item size in turn, the others fixed
+  for (int p = 0; p < n && rc == MGX_OK; ++p)
+    for (int e : {64, 128, 256, 512, 1024, 2048, 4096}) {
+      if (e == be[p]) continue;
+      std::vector<int> cand = be;
+      cand[p] = e;
+      float ms = 0.0f;
+      if ((rc = timed(bb, cand, &ms)) != MGX_OK) break;
+      if (ms < best) { best = ms; be = cand; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (rc != MGX_OK) return rc;
   b->blocks_per_sm = bb;
-  b->events_per_item = be;
+  b->epi = be;
   if (blocks_per_sm) *blocks_per_sm = bb;
-  if (events_per_item) *events_per_item = be;
+  if (events_per_item)
+    for (int p = 0; p < n; ++p) events_per_item[p] = be[p];
   return MGX_OK;
 }
 
