@@ -243,6 +243,39 @@ def extra_ggttggg(pkg, dev, stream):
     return out
 
 
+def extra_eemumu(pkg, dev, stream):
+    """e+ e- > mu+ mu-, 8192 events: a launch- and latency-bound case.  Microseconds per launch,
+    launched directly and replayed from a CUDA graph of 20 launches, and the HBM bandwidth that the
+    algorithmic bytes (momenta, alpha_s, two random numbers in; me and two selections out) imply."""
+    import numpy as np
+    import torch
+    from phasespace import WORKLOADS, make_inputs
+    wl = WORKLOADS["eemumu"]
+    mom, a, rh, rc = make_inputs(wl, wl.nevt)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
+    proc = pkg.Process(wl.process, device=dev.index)
+    n = wl.nevt
+    out = {"me": torch.empty(n, dtype=torch.float64, device=dev),
+           "selhel": torch.empty(n, dtype=torch.int32, device=dev),
+           "selcol": torch.empty(n, dtype=torch.int32, device=dev)}
+    side = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        step = lambda: proc.compute(M, A, RH, RC, stream=side, out=out)
+        direct_ms = _timed(step, 200, 10, side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            for _ in range(20):
+                step()
+        graph_ms = _timed(g.replay, 20, 2, side) / 20
+    algo = n * (4 * 4 * 8 + 3 * 8 + 8 + 4 + 4)
+    return {"nevt": n, "ngood": proc.ngood,
+            "direct_us_per_launch": direct_ms * 1e3, "graph_us_per_launch": graph_ms * 1e3,
+            "events_per_s_direct": n / (direct_ms * 1e-3), "events_per_s_graph": n / (graph_ms * 1e-3),
+            "algorithmic_bytes_per_launch": algo, "hbm_gbs_graph": algo / (graph_ms * 1e-3) / 1e9}
+
+
 def extra_batched(pkg, dev, stream):
     """g g > t t~ (2^22), t t~ g (2^20), t t~ g g (2^18), g u~ > ta+ ta- g g u~ (2^16): one
     autotuned persistent launch captured in a CUDA graph vs one launch per process."""
@@ -435,6 +468,7 @@ def run_gpu(args):
             extras = {}
             for key, fn in (("ggttgg_modes", lambda: extra_modes(pkg, proc, M, A, RH, RC, nevt, stream)),
                             ("ggttggg", lambda: extra_ggttggg(pkg, dev, stream)),
+                            ("eemumu", lambda: extra_eemumu(pkg, dev, stream)),
                             ("batched", lambda: extra_batched(pkg, dev, stream)),
                             ("surrogate_unweighting", lambda: extra_surrogate(pkg, dev))):
                 t0 = time.perf_counter()

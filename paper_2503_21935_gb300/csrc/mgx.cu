@@ -192,9 +192,13 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
       for (int ih = 0; ih < P.ngood; ++ih) {
         const cxT<R> amp = group_amp<R>(P.terms, o, P.good[ih], W);
         const int jb = P.jamp_off + 2 * P.ncol * ih;
+        // phase rotation by sign-bit and swap selects (no branch per flow), then one add each
         for (int f = 0; f < o.mass; ++f) {
           const int2 q = __ldg(fl + f);
-          add_phase(W[jb + 2 * q.x], W[jb + 2 * q.x + 1], q.y, amp);
+          const int off = jb + 2 * q.x;
+          const cxT<R> j = cxT<R>{W[off], W[off + 1]} + rot_phase(q.y, amp);
+          W[off] = j.r;
+          W[off + 1] = j.i;
         }
       }
       continue;
@@ -253,7 +257,7 @@ __device__ __forceinline__ void stage_momenta(const double* __restrict__ mom, in
 }
 
 template <class R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
               int32_t* __restrict__ selhel, int32_t* __restrict__ selcol, double* __restrict__ mh_out,
@@ -414,7 +418,9 @@ __global__ void __launch_bounds__(kCtaThreads)
           const int2* fl = C.flows + o.cpl;
           for (int f = 0; f < o.mass; ++f) {
             const int2 q = __ldg(fl + f);
-            add_phase(J[2 * q.x], J[2 * q.x + 1], q.y, amp);
+            const cx r = rot_phase(q.y, amp);
+            J[2 * q.x] += r.r;
+            J[2 * q.x + 1] += r.i;
           }
         }
       }

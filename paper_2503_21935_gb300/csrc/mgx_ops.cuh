@@ -363,17 +363,6 @@ __device__ inline void op_variant(const KParams& P, const Op& o, int v, double g
   }
 }
 
-// add phase(code) * a to (re, im)
-template <class R>
-__device__ __forceinline__ void add_phase(R& jr, R& ji, int code, cxT<R> a) {
-  switch (code) {
-    case 0: jr = jr + a.r; ji = ji + a.i; break;   // +1
-    case 1: jr = jr - a.i; ji = ji + a.r; break;   // +i
-    case 2: jr = jr - a.r; ji = ji - a.i; break;   // -1
-    default: jr = jr + a.i; ji = ji - a.r; break;  // -i
-  }
-}
-
 // ================================================================ diagram amplitudes
 // phase(code) * a, code 0..3 for 1, i, -1, -i: a swap of the parts and sign flips done on the
 // sign bits (integer operations, no floating-point arithmetic)
