@@ -36,6 +36,7 @@ struct mgx_program_desc {
   int ws_doubles, ndiag, nterm, avg_den;
   int gs_power;          // power of g_s of every amplitude (vertices are evaluated with g_s = 1)
   int col_den;           // common denominator of the colour matrix
+  int jamp_zero;         // some flow is never updated: zero the jamps first
   int counts[12];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows,
                          // groups, runs (terms sharing one bilinear within a group)
   struct {
@@ -184,7 +185,8 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
   using T = Real<R>;
   const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
   const double scale = coupling_scale(P, alphas[e]);
-  for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = T::from(0.0);
+  if (P.jamp_zero)
+    for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = T::from(0.0);
   for (int iop = 0; iop < P.nops; ++iop) {
     const Op o = load_op(P.ops, iop);
     if (o.code == OP_AMP) {
@@ -192,11 +194,13 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
       for (int ih = 0; ih < P.ngood; ++ih) {
         const cxT<R> amp = group_amp<R>(P.terms, o, P.good[ih], W);
         const int jb = P.jamp_off + 2 * P.ncol * ih;
-        // phase rotation by sign-bit and swap selects (no branch per flow), then one add each
+        // phase rotation by sign-bit and swap selects (no branch per flow), then one add each;
+        // the first update of a flow in program order (code bit 2) writes
         for (int f = 0; f < o.mass; ++f) {
           const int2 q = __ldg(fl + f);
           const int off = jb + 2 * q.x;
-          const cxT<R> j = cxT<R>{W[off], W[off + 1]} + rot_phase(q.y, amp);
+          cxT<R> j = rot_phase(q.y & 3, amp);
+          if (!(q.y & 4)) j = cxT<R>{W[off], W[off + 1]} + j;
           W[off] = j.r;
           W[off + 1] = j.i;
         }
@@ -418,7 +422,7 @@ __global__ void __launch_bounds__(kCtaThreads)
           const int2* fl = C.flows + o.cpl;
           for (int f = 0; f < o.mass; ++f) {
             const int2 q = __ldg(fl + f);
-            const cx r = rot_phase(q.y, amp);
+            const cx r = rot_phase(q.y & 3, amp);
             J[2 * q.x] += r.r;
             J[2 * q.x + 1] += r.i;
           }
@@ -854,6 +858,7 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
   kp.nin = prog->nin;
   kp.avg = 1.0 / prog->avg_den;
   kp.gs_power = prog->gs_power;
+  kp.jamp_zero = prog->jamp_zero;
   // couplings
   const double e = std::sqrt(4.0 * M_PI * prm.alpha_em);
   const double mz2 = prm.mz * prm.mz;
@@ -1142,8 +1147,9 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   double t = w(ffv_f) * (c[0] + c[1]) + w(ffv_v) * c[2] + w(vvv) * c[3] + w(vvvv) * c[4] + w(bil) * c[5] +
              w(rbil) * c[6];
   // per good helicity: one product per run, a 4-vector add per further term of a run, an add per
-  // further run of a group, and an add per (group, flow)
-  t += ngood * (w(run) * c[11] + w(term_add) * (c[8] - c[11]) + w(run_add) * (c[11] - c[10]) + w(flow) * c[9]);
+  // further run of a group, and an add per (group, flow) except each flow's first (a write)
+  const double flow_adds = c[9] - (pr->prog->jamp_zero ? 0.0 : n);
+  t += ngood * (w(run) * c[11] + w(term_add) * (c[8] - c[11]) + w(run_add) * (c[11] - c[10]) + w(flow) * flow_adds);
   if (mode == MGX_FP64) t += ngood * (flops ? 2 * n * n + 4 * n : n * n + 3 * n);  // quadratic form
   else if (!flops) t += ngood * 2 * n;                                              // f64 -> f32 conversions
   t += ngood * (flops ? 4 * n : 2 * n);                                             // colour weights

@@ -34,7 +34,7 @@ constexpr int MAXNPAR = 8;
 
 struct KParams {
   const int4* ops;       // 4 int4 (16 int32 fields) per op
-  const int2* flows;     // (colour flow, phase code 0..3 for 1, i, -1, -i)
+  const int2* flows;     // (colour flow, phase code 0..3 for 1, i, -1, -i; | 4 on a flow's first update)
   const int4* terms;     // 2 int4 per diagram term: (bilinear base, mask, other base, mask), (phase, kind, -, -)
   const double* colsym;  // ncol*ncol: C_ii on the diagonal, 2 C_ij above it
   const float* colsym_f;
@@ -42,6 +42,7 @@ struct KParams {
   int cur_doubles, jamp_off, mh_off, colw_off, ws_doubles;
   double avg;            // 1 / (4 Ncol_in S)
   int gs_power;          // |M|^2 carries (4 pi alpha_s)^gs_power; vertices use g_s = 1
+  int jamp_zero;         // jamps need zeroing (a flow no group updates); else first updates write
   double cpl[MAXCPL][4]; // cL.re cL.im cR.re cR.im
   int cplflags[MAXCPL];
   double mass[MAXMASS], width[MAXMASS];

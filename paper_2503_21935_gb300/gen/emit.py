@@ -65,7 +65,7 @@ def emit(path):
             f'  {{"{P.process}", {P.npar}, {P.nin}, {P.root}, {len(P.ops)}, {pre}_ops, '
             f'{len(P.flows) // 2}, {pre}_flows, {len(P.terms) // 8}, {pre}_terms, {P.ncol}, {pre}_colour, {len(P.couplings)}, {pre}_coupl, '
             f'{len(P.masses)}, {pre}_mass, {pre}_extmass, {P.ws_current_doubles}, {P.ndiagrams}, '
-            f'{P.nterms}, {P.average_den}, {P.gs_power}, {P.col_den}, '
+            f'{P.nterms}, {P.average_den}, {P.gs_power}, {P.col_den}, {P.jamp_zero}, '
             f'{{{c["var_ffv_f"]}, {c["var_ffv_fb"]}, {c["var_ffv_v"]}, {c["var_vvv"]}, {c["var_vvvv"]}, {c["var_bil"]}, {c["var_rbil"]}, '
             f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"] + c["bil"] + c["rbil"]}, {c["amp_terms"]}, {c["amp_flows"]}, {c["amp"]}, {c["amp_runs"]}}}, '
             f'{cta_init}}},')

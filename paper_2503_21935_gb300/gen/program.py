@@ -24,6 +24,7 @@ from .diagrams import Diagrams, Current
 OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP, OP_BIL, OP_RBIL = 1, 2, 3, 4, 5, 6, 7, 8, 9
 EXT_U, EXT_V, EXT_UBAR, EXT_VBAR, EXT_EPS_IN, EXT_EPS_OUT = 0, 1, 2, 3, 4, 5
 NFIELD = 16
+FLOW_FIRST = 4                  # flow entry phase-code bit: first update of that flow (write, not add)
 
 # coupling flags
 C_GS = 1        # multiply by the per-event strong coupling g_s
@@ -388,6 +389,18 @@ def _dfs_schedule(B):
         for u in set(uses(item)):
             if last[u] == pos:
                 A.release(offset[u], B.blocksize(u))
+    # the first update of each flow in program order writes instead of adding (phase code bit 2),
+    # so the jamps need no zeroing beforehand; a flow that no group updates stays unwritten, in
+    # which case every jamp is zeroed first (flag returned with the tables)
+    seen = set()
+    for op in ops:
+        if op[0] != OP_AMP:
+            continue
+        for k in range(op[9], op[9] + op[10]):
+            if flows[2 * k] not in seen:
+                seen.add(flows[2 * k])
+                flows[2 * k + 1] |= FLOW_FIRST
+    B.all_flows_written = len(seen) == len(B.D_perms)
     return ops, flows, terms, A.top
 
 
@@ -494,6 +507,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     gsp = gs_power(D)
     npar = D.npar
     B = _Builder(D)
+    B.D_perms = _perms(D)
     ops, flows, terms, top = _dfs_schedule(B)
     counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, bil=0, rbil=0, amp=0, amp_flows=0,
                   var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0, var_rbil=0)
@@ -530,6 +544,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
                    average_den=4 * ncol_in * ident, flop_counts=counts)
     prog.cta = cta
     prog.gs_power = gsp
+    prog.jamp_zero = 0 if B.all_flows_written else 1
     # integer scaling of the colour matrix for the tensor-core colour sum (exact in tf32)
     den = 1
     for row in C:
