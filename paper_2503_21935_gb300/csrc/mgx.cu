@@ -37,8 +37,9 @@ struct mgx_program_desc {
   int gs_power;          // power of g_s of every amplitude (vertices are evaluated with g_s = 1)
   int col_den;           // common denominator of the colour matrix
   int jamp_zero;         // some flow is never updated: zero the jamps first
-  int counts[12];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows,
-                         // groups, runs (terms sharing one bilinear within a group)
+  int counts[13];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows,
+                         // groups, runs (terms sharing one bilinear within a group); sum-current
+                         // 4-vector adds (variants x (summands - 1))
   struct {
     int nops;
     const int32_t* ops;
@@ -1150,6 +1151,7 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   // further run of a group, and an add per (group, flow) except each flow's first (a write)
   const double flow_adds = c[9] - (pr->prog->jamp_zero ? 0.0 : n);
   t += ngood * (w(run) * c[11] + w(term_add) * (c[8] - c[11]) + w(run_add) * (c[11] - c[10]) + w(flow) * flow_adds);
+  t += w(term_add) * c[12];                        // sum currents, per variant of their legs
   if (mode == MGX_FP64) t += ngood * (flops ? 2 * n * n + 4 * n : n * n + 3 * n);  // quadratic form
   else if (!flops) t += ngood * 2 * n;                                              // f64 -> f32 conversions
   t += ngood * (flops ? 4 * n : 2 * n);                                             // colour weights

@@ -23,7 +23,8 @@
 
 namespace mgx {
 
-enum { OP_EXT = 1, OP_FFV_F = 2, OP_FFV_FB = 3, OP_FFV_V = 4, OP_VVV = 5, OP_VVVV = 6, OP_AMP = 7, OP_BIL = 8, OP_RBIL = 9 };
+enum { OP_EXT = 1, OP_FFV_F = 2, OP_FFV_FB = 3, OP_FFV_V = 4, OP_VVV = 5, OP_VVVV = 6, OP_AMP = 7, OP_BIL = 8, OP_RBIL = 9,
+       OP_SUM = 10 };
 enum { EXT_U = 0, EXT_V = 1, EXT_UBAR = 2, EXT_VBAR = 3, EXT_EPS_IN = 4, EXT_EPS_OUT = 5 };
 enum { CPL_GS = 1, CPL_CHIRAL = 2 };
 

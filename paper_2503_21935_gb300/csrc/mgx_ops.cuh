@@ -77,10 +77,26 @@ __device__ __forceinline__ void apply_pref(cxT<R> pref, const cxT<R>* x, cxT<R>*
   }
 }
 
+// phase(code) * a, code 0..3 for 1, i, -1, -i: a swap of the parts and sign flips done on the
+// sign bits (integer operations, no floating-point arithmetic)
+__device__ __forceinline__ double neg_if(double x, bool c) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
+}
+__device__ __forceinline__ float neg_if(float x, bool c) {
+  return __int_as_float(__float_as_int(x) ^ ((int)c << 31));
+}
+template <class R>
+__device__ __forceinline__ cxT<R> rot_phase(int code, cxT<R> a) {
+  const bool swap = code & 1;
+  const R r = swap ? a.i : a.r, i = swap ? a.r : a.i;
+  return {neg_if(r, code == 1 || code == 2), neg_if(i, code >= 2)};
+}
+
 // ================================================================ headers
 template <class R, class S>
 __device__ inline void op_header(const KParams& P, const Op& o, double gs, const double* pe, const S& W) {
   using T = Real<R>;
+  if (o.code == OP_SUM) return;   // no header
   if (o.code == OP_EXT) {
     const double* p = pe + 4 * o.aux;
     const double sgn = o.aux < P.nin ? 1.0 : -1.0;  // incoming momentum
@@ -349,6 +365,26 @@ __device__ inline void var_vvvv(const KParams& P, const Op& o, int v, const S& W
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
+// sum current: variant v = sum_t phase_t Y_t[v] over currents Y_t on the same legs; list entries
+// (Y variant base, -, -, -), (phase, -, -, -) in the term table from aux, aux2 of them
+template <class R, class S>
+__device__ inline void var_sum(const KParams& P, const Op& o, int v, const S& W) {
+  cxT<R> s[4], y[4];
+  for (int t = 0; t < o.aux2; ++t) {
+    const int4 a = __ldg(P.terms + 2 * (o.aux + t));
+    const int4 b = __ldg(P.terms + 2 * (o.aux + t) + 1);
+    W.load4(a.x + 8 * v, y);
+    if (t == 0) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[j] = rot_phase(b.x, y[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[j] = s[j] + rot_phase(b.x, y[j]);
+    }
+  }
+  W.store4(o.dst + 8 * v, s);
+}
+
 template <class R, class S>
 __device__ inline void op_variant(const KParams& P, const Op& o, int v, double gs, const double* pe, const S& W) {
   switch (o.code) {
@@ -359,26 +395,12 @@ __device__ inline void op_variant(const KParams& P, const Op& o, int v, double g
     case OP_BIL: var_ffv_v<R>(P, o, v, gs, W); break;   // the column bilinear is the vertex current without propagator
     case OP_RBIL: var_rbil<R>(P, o, v, gs, W); break;
     case OP_VVV: var_vvv<R>(P, o, v, W); break;
+    case OP_SUM: var_sum<R>(P, o, v, W); break;
     default: var_vvvv<R>(P, o, v, W); break;
   }
 }
 
 // ================================================================ diagram amplitudes
-// phase(code) * a, code 0..3 for 1, i, -1, -i: a swap of the parts and sign flips done on the
-// sign bits (integer operations, no floating-point arithmetic)
-__device__ __forceinline__ double neg_if(double x, bool c) {
-  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)c << 63));
-}
-__device__ __forceinline__ float neg_if(float x, bool c) {
-  return __int_as_float(__float_as_int(x) ^ ((int)c << 31));
-}
-template <class R>
-__device__ __forceinline__ cxT<R> rot_phase(int code, cxT<R> a) {
-  const bool swap = code & 1;
-  const R r = swap ? a.i : a.r, i = swap ? a.r : a.i;
-  return {neg_if(r, code == 1 || code == 2), neg_if(i, code >= 2)};
-}
-
 // A group of diagram terms sharing one colour vector (up to a phase): sum over the group of
 // phase_t * amp_t(h), where amp_t = X_t . Y_t with X_t a root bilinear and Y_t the term's other
 // current: kind 0, Q . V (column bilinear Q^mu = psibar gamma^mu (..) psi_C, Minkowski dot with

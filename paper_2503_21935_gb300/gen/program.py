@@ -21,7 +21,7 @@ from . import sm
 from .colour import colour_matrix
 from .diagrams import Diagrams, Current
 
-OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP, OP_BIL, OP_RBIL = 1, 2, 3, 4, 5, 6, 7, 8, 9
+OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP, OP_BIL, OP_RBIL, OP_SUM = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10
 EXT_U, EXT_V, EXT_UBAR, EXT_VBAR, EXT_EPS_IN, EXT_EPS_OUT = 0, 1, 2, 3, 4, 5
 NFIELD = 16
 FLOW_FIRST = 4                  # flow entry phase-code bit: first update of that flow (write, not add)
@@ -62,7 +62,7 @@ def _bit(npar, leg):
     return 1 << (npar - 1 - leg)
 
 
-HEADER = {"EXT": 4, "FFV_F": 6, "FFV_FB": 6, "FFV_V": 6, "VVV": 18, "VVVV": 6, "BIL": 6, "RBIL": 6}
+HEADER = {"EXT": 4, "FFV_F": 6, "FFV_FB": 6, "FFV_V": 6, "VVV": 18, "VVVV": 6, "BIL": 6, "RBIL": 6, "SUM": 0}
 # float64 instructions per variant of the two root bilinears (column: Q = psibar gamma psi_col;
 # row: R = psibar Vslash), used to choose between them
 BIL_COST = {"BIL": 56, "RBIL": 40}
@@ -178,12 +178,19 @@ class _Builder:
     def varbase(self, i, offset):
         return offset[i] + HEADER[self.cur(i).op]
 
-    def current_row(self, i, offset):
+    def current_row(self, i, offset, terms=None):
         D = self.D
         c = self.cur(i)
         op = [0] * NFIELD
         op[1] = offset[i]
         op[5] = self.hmask(c.mask)
+        if c.op == "SUM":
+            # sum of phased currents over the same legs: list entries (base, mask, -, -, phase, ...)
+            # in the term table; variant v of every summand is its variant v
+            op[0], op[11], op[12] = OP_SUM, len(terms) // 8, len(c.children)
+            for k, ph in zip(c.children, c.phases):
+                terms += [self.varbase(k, offset), self.hmask(D.currents[k].mask), 0, 0, ph, 0, 0, 0]
+            return op
         if c.op == "EXT":
             leg = c.leg
             f = c.flav
@@ -222,31 +229,34 @@ class _Builder:
             raise ValueError(c.op)
         return op
 
-    def amp_row(self, group, offset, flows, terms):
+    def amp_row(self, runs, fl, offset, flows, terms):
         """One AMP row per term group: term table entries (bil base, bil mask, other base, other mask,
-        phase, kind, run start, run end) and the group's (flow, phase) list.  Terms closing on the same
-        bilinear are adjacent and form a run: the kernel sums the run's phased other operands first
-        and takes one product with the bilinear per run (distributivity)."""
-        D = self.D
-        tis, phases, fl = group
+        phase, kind, run start, run end) and the group's (flow, phase) list.  `runs` lists
+        (bilinear, kind, [(other current, phase), ...]): terms closing on the same bilinear, whose
+        phased other operands the kernel sums first and closes with one product (distributivity)."""
         op = [0] * NFIELD
         op[0] = OP_AMP
         op[11] = len(terms) // 8
-        op[12] = len(tis)
-        key = lambda ti: (D.terms[ti].bil, D.terms[ti].kind)
-        items = sorted(zip(tis, phases), key=lambda x: key(x[0]))
-        for k, (ti, ph) in enumerate(items):
-            t = D.terms[ti]
-            bil, oth = D.currents[t.bil], D.currents[t.other]
-            start = k == 0 or key(items[k - 1][0]) != key(ti)
-            end = k == len(items) - 1 or key(items[k + 1][0]) != key(ti)
-            terms += [self.varbase(t.bil, offset), self.hmask(bil.mask), self.varbase(t.other, offset),
-                      self.hmask(oth.mask), ph, t.kind, int(start), int(end)]
+        op[12] = sum(len(items) for _, _, items in runs)
+        for x, kind, items in runs:
+            for k, (y, ph) in enumerate(items):
+                terms += [self.varbase(x, offset), self.hmask(self.cur(x).mask), self.varbase(y, offset),
+                          self.hmask(self.cur(y).mask), ph, kind, int(k == 0), int(k == len(items) - 1)]
         op[9] = len(flows) // 2
         op[10] = len(fl)
         for f, ph in fl:
             flows += [f, ph]
         return op
+
+
+def _runs(D, group):
+    """The group's terms as runs: (bilinear, kind, [(other current, phase), ...]) per bilinear."""
+    tis, phases, _ = group
+    out = {}
+    for ti, ph in zip(tis, phases):
+        t = D.terms[ti]
+        out.setdefault((t.bil, t.kind), []).append((t.other, ph))
+    return [(x, kind, items) for (x, kind), items in sorted(out.items())]
 
 
 def _bipartite_min_cover(left, right, edges, wl, wr):
@@ -358,10 +368,27 @@ def _dfs_schedule(B):
         done.add(i)
         order.append(("C", i))
     groups = _term_groups(D)
-    for gi, (tis, _, _) in enumerate(groups):
-        for ti in tis:
-            emit(D.terms[ti].bil)
-            emit(D.terms[ti].other)
+    # a run of several terms closing on one bilinear gets a sum current: the phased sum of its
+    # other operands (all over the same legs), computed once per helicity state of those legs
+    # instead of once per full helicity inside the amplitude row
+    gruns = []
+    for gi, g in enumerate(groups):
+        eff = []
+        for x, kind, items in _runs(D, g):
+            if len(items) > 1:
+                mask = cur[items[0][0]].mask
+                if any(cur[y].mask != mask for y, _ in items):
+                    raise ValueError("terms of one bilinear cover different legs")
+                node = Current(len(cur), mask, cur[items[0][0]].flav, "SUM", children=tuple(y for y, _ in items))
+                node.phases = [ph for _, ph in items]
+                cur.append(node)
+                items = [(node.id, 0)]
+            eff.append((x, kind, items))
+        gruns.append(eff)
+        for x, _, items in eff:
+            emit(x)
+            for y, _ in items:
+                emit(y)
         order.append(("A", gi))
 
     def uses(item):
@@ -369,8 +396,8 @@ def _dfs_schedule(B):
         if kind == "C":
             return list(cur[x].children)
         out = []
-        for ti in groups[x][0]:
-            out += [D.terms[ti].bil, D.terms[ti].other]
+        for b, _, items in gruns[x]:
+            out += [b] + [y for y, _ in items]
         return out
     last = {}
     for pos, item in enumerate(order):
@@ -383,9 +410,9 @@ def _dfs_schedule(B):
         kind, x = item
         if kind == "C":
             offset[x] = A.alloc(B.blocksize(x))
-            ops.append(B.current_row(x, offset))
+            ops.append(B.current_row(x, offset, terms))
         else:
-            ops.append(B.amp_row(groups[x], offset, flows, terms))
+            ops.append(B.amp_row(gruns[x], groups[x][2], offset, flows, terms))
         for u in set(uses(item)):
             if last[u] == pos:
                 A.release(offset[u], B.blocksize(u))
@@ -471,7 +498,7 @@ def _wave_schedule(B, chunk):
         done |= want
         first = len(ops)
         for gi in ch:
-            ops.append(B.amp_row(groups[gi], offset, flows, terms))
+            ops.append(B.amp_row(_runs(D, groups[gi]), groups[gi][2], offset, flows, terms))
         steps.append((1, first, len(ch)))
         for x in list(live):
             if last_chunk[x] == ci:
@@ -512,7 +539,8 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, bil=0, rbil=0, amp=0, amp_flows=0,
                   var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0, var_rbil=0)
     name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
-            OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil", OP_RBIL: "rbil"}
+            OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil", OP_RBIL: "rbil", OP_SUM: "sum"}
+    counts["sum"] = counts["sum_adds"] = 0
     for op in ops:
         k = name[op[0]]
         counts[k] += 1
@@ -520,6 +548,8 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
             counts["amp_flows"] += op[10]
             counts["amp_terms"] = counts.get("amp_terms", 0) + op[12]
             counts["amp_runs"] = counts.get("amp_runs", 0) + sum(terms[8 * (op[11] + k) + 6] for k in range(op[12]))
+        elif op[0] == OP_SUM:
+            counts["sum_adds"] += (op[12] - 1) << bin(op[5]).count("1")     # 4-vector adds
         elif op[0] != OP_EXT:
             counts["var_" + k] += 1 << bin(op[5]).count("1")
     # CTA schedule: largest chunk whose store fits the shared-memory budget
