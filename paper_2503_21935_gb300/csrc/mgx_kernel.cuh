@@ -6,9 +6,12 @@
 // process compiler) and computes every off-shell current once per helicity state
 // of its own external legs ("variants"), keeping the variants in a per-event
 // workspace laid out [offset][thread] so that a warp's accesses are coalesced.
-// Diagram amplitudes (one per diagram term) are closed at the root vertex for every
-// good helicity and added to the colour-flow amplitudes (jamps); the colour sum
-// J^dagger C J, the helicity sum and the selections follow in the same thread.
+// Every diagram term is closed at the root vertex through a root bilinear; terms with
+// the same colour vector up to a phase form a group, terms of a group sharing a
+// bilinear are summed first (a "sum current" over the same legs, once per helicity
+// state of those legs) and closed with one product per good helicity, and each group
+// amplitude is added to its colour flows (jamps).  The colour sum J^dagger C J, the
+// helicity sum and the selections follow in the same thread.
 // The arithmetic is templated on its real type R: double or float.
 //
 // Feynman rules (all momenta incoming at a vertex; metric +---; chiral gamma basis):

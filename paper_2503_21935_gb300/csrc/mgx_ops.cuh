@@ -7,6 +7,7 @@
 //   [header (H(kind) slots) | variant 0 (4 complex) | variant 1 | ...]
 // The op table carries the child block offsets (momenta at +0) and the child
 // variant bases (fields 13-15), so no op needs to know its children's kinds.
+// Sum currents (OP_SUM) have no header; their summand list lives in the term table.
 #pragma once
 #include "mgx_kernel.cuh"
 

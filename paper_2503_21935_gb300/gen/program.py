@@ -9,8 +9,12 @@ where k is the current's incoming momentum and variant v holds the current for
 the helicities pdep(v, mask) of the legs in `mask` (leg p <-> bit npar-1-p, the
 bit of the canonical helicity index).  A current is computed once per helicity
 state of its own legs (helicity recycling) and its block is freed after its last
-use.  AMP ops close a diagram term at the root vertex for every good helicity
-and add it, times a phase in {1, i, -1, -i}, to the term's colour flows.
+use.  Every diagram term is closed at the root vertex through a root bilinear (column
+Q.V or row R.psi, chosen by an exact minimum vertex cover); terms with one colour
+vector up to a phase form a group; terms of a group sharing a bilinear form a run
+whose other operands are summed by a SUM op (once per helicity state of their legs).
+AMP ops take one product per run and good helicity and add the group amplitude,
+times a phase in {1, i, -1, -i}, to the group's colour flows.
 """
 import itertools
 import math
