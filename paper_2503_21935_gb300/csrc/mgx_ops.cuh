@@ -93,6 +93,19 @@ __device__ __forceinline__ cxT<R> rot_phase(int code, cxT<R> a) {
   return {neg_if(r, code == 1 || code == 2), neg_if(i, code >= 2)};
 }
 
+// VVVV colour structure j needs the dot products of two child pairs (children 0, 1, 2 = e1, e2, e3):
+// j = 0: (e1.e3, e2.e3), j = 1: (e1.e2, e2.e3), j = 2: (e1.e2, e1.e3)
+__device__ __forceinline__ void vvvv_pairs(int j, int& x0, int& y0, int& x1, int& y1) {
+  x0 = 0;
+  y0 = j == 0 ? 2 : 1;
+  x1 = j == 2 ? 0 : 1;
+  y1 = 2;
+}
+// child k of an op: variant base and helicity mask
+__device__ __forceinline__ int child_base(const Op& o, int k) { return k == 0 ? o.va : (k == 1 ? o.vb : o.vc); }
+__device__ __forceinline__ int child_mask(const Op& o, int k) { return k == 0 ? o.ma : (k == 1 ? o.mb : o.mc); }
+__device__ __forceinline__ int nvar_of(int mask) { return 1 << __popc(mask); }
+
 // ================================================================ headers
 template <class R, class S>
 __device__ inline void op_header(const KParams& P, const Op& o, double gs, const double* pe, const S& W) {
@@ -125,7 +138,30 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
 #pragma unroll
     for (int j = 0; j < 4; ++j) k[j] = k[j] + kc[j];
     W.storek(o.dst, k);
-    W[o.dst + 4] = -(T::from(gs * gs) * T::rcp(msq(k)));  // (-i)(-i g_s^2)/P^2
+    const R sv = -(T::from(gs * gs) * T::rcp(msq(k)));   // (-i)(-i g_s^2)/P^2
+    W[o.dst + 4] = sv;
+    // the structure's two pair tables: s (e_x0 . e_y0) and -s (e_x1 . e_y1) for every pair of variants
+    int x0, y0, x1, y1;
+    vvvv_pairs(o.aux, x0, y0, x1, y1);
+    int base = o.dst + 6;
+#pragma unroll 1
+    for (int tab = 0; tab < 2; ++tab) {
+      const int x = tab ? x1 : x0, y = tab ? y1 : y0;
+      const int nx = nvar_of(child_mask(o, x)), ny = nvar_of(child_mask(o, y));
+      const R f = tab ? -sv : sv;
+      for (int iy = 0; iy < ny; ++iy) {
+        cxT<R> ey[4];
+        W.load4(child_base(o, y) + 8 * iy, ey);
+        for (int ix = 0; ix < nx; ++ix) {
+          cxT<R> ex[4];
+          W.load4(child_base(o, x) + 8 * ix, ex);
+          const cxT<R> d = rmul(f, mdot(ex, ey));
+          W[base + 2 * (ix + nx * iy)] = d.r;
+          W[base + 2 * (ix + nx * iy) + 1] = d.i;
+        }
+      }
+      base += 2 * nx * ny;
+    }
     return;
   }
   W.storek(o.dst, k);
@@ -133,11 +169,30 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
     // prefactor -i g_s/P^2 = i s, s folded into the momentum combinations of the vertex
     const R s = -(T::from(gs) * T::rcp(msq(k)));
     const R two = T::from(2.0);
+    R q1[4], q2[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       W[o.dst + 6 + j] = s * (ka[j] - kb[j]);            // s (k1 - k2)
-      W[o.dst + 10 + j] = s * fma(two, kb[j], ka[j]);    // s (k2 - k3) = s (k1 + 2 k2)
-      W[o.dst + 14 + j] = -(s * fma(two, ka[j], kb[j])); // s (k3 - k1) = -s (2 k1 + k2)
+      q1[j] = s * fma(two, kb[j], ka[j]);                // s (k2 - k3) = s (k1 + 2 k2)
+      q2[j] = -(s * fma(two, ka[j], kb[j]));             // s (k3 - k1) = -s (2 k1 + k2)
+    }
+    W.storek(o.dst + 10, q1);
+    W.storek(o.dst + 14, q2);
+    // per child variant: a1 = q1 . e1 and a2 = q2 . e2 (each depends on one child only)
+    const int n1 = nvar_of(o.ma), n2 = nvar_of(o.mb);
+    for (int v1 = 0; v1 < n1; ++v1) {
+      cxT<R> e[4];
+      W.load4(o.va + 8 * v1, e);
+      const cxT<R> a = rdot(q1, e);
+      W[o.dst + 18 + 2 * v1] = a.r;
+      W[o.dst + 18 + 2 * v1 + 1] = a.i;
+    }
+    for (int v2 = 0; v2 < n2; ++v2) {
+      cxT<R> e[4];
+      W.load4(o.vb + 8 * v2, e);
+      const cxT<R> a = rdot(q2, e);
+      W[o.dst + 18 + 2 * (n1 + v2)] = a.r;
+      W[o.dst + 18 + 2 * (n1 + v2) + 1] = a.i;
     }
     return;
   }
@@ -317,53 +372,53 @@ __device__ inline void var_rbil(const KParams& P, const Op& o, int v, double gs,
   W.store4(o.dst + 6 + 8 * v, out);
 }
 
-// J^r = i [ (e1.e2) s(k1-k2)^r + e2^r (s(k2-k3).e1) + e1^r (s(k3-k1).e2) ],  s = -g_s/P^2
+// J^r = i [ (e1.e2) s(k1-k2)^r + e2^r (s(k2-k3).e1) + e1^r (s(k3-k1).e2) ],  s = -g_s/P^2;
+// the two single-child dot products come from the header's per-variant tables
 template <class R, class S>
 __device__ inline void var_vvv(const KParams& P, const Op& o, int v, const S& W) {
   const int hb = pdep(v, o.mdst);
+  const int i1 = pext(hb, o.ma), i2 = pext(hb, o.mb);
+  const int n1 = nvar_of(o.ma), n2 = nvar_of(o.mb);
   cxT<R> e1[4], e2[4];
-  W.load4(o.va + 8 * pext(hb, o.ma), e1);
-  W.load4(o.vb + 8 * pext(hb, o.mb), e2);
-  R d[4], q1[4], q2[4];
+  W.load4(o.va + 8 * i1, e1);
+  W.load4(o.vb + 8 * i2, e2);
+  R d[4];
   W.loadk(o.dst + 6, d);
-  W.loadk(o.dst + 10, q1);
-  W.loadk(o.dst + 14, q2);
   const cxT<R> s12 = mdot(e1, e2);
-  const cxT<R> a1 = rdot(q1, e1);
-  const cxT<R> a2 = rdot(q2, e2);
+  const cxT<R> a1 = {W[o.dst + 18 + 2 * i1], W[o.dst + 18 + 2 * i1 + 1]};
+  const cxT<R> a2 = {W[o.dst + 18 + 2 * (n1 + i2)], W[o.dst + 18 + 2 * (n1 + i2) + 1]};
   cxT<R> out[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const cxT<R> t = cfma(e1[j], a2, cfma(e2[j], a1, rmul(d[j], s12)));
     out[j] = {Real<R>::neg(t.i), t.r};
   }
-  W.store4(o.dst + 18 + 8 * v, out);
+  W.store4(o.dst + 18 + 2 * (n1 + n2) + 8 * v, out);
 }
 
-// J = s { j=0: (e1.e3) e2 - (e2.e3) e1 ; j=1: (e1.e2) e3 - (e2.e3) e1 ; j=2: (e1.e2) e3 - (e1.e3) e2 }
+// J = s { j=0: (e1.e3) e2 - (e2.e3) e1 ; j=1: (e1.e2) e3 - (e2.e3) e1 ; j=2: (e1.e2) e3 - (e1.e3) e2 },
+// i.e. J = X e_m0 + Y e_m1 with X = s (pair 0 dot), Y = -s (pair 1 dot) from the header's pair
+// tables and m0, m1 the children outside pair 0, pair 1
 template <class R, class S>
 __device__ inline void var_vvvv(const KParams& P, const Op& o, int v, const S& W) {
   const int hb = pdep(v, o.mdst);
-  cxT<R> e1[4], e2[4], e3[4];
-  W.load4(o.va + 8 * pext(hb, o.ma), e1);
-  W.load4(o.vb + 8 * pext(hb, o.mb), e2);
-  W.load4(o.vc + 8 * pext(hb, o.mc), e3);
-  const R s = W[o.dst + 4];
+  int x0, y0, x1, y1;
+  vvvv_pairs(o.aux, x0, y0, x1, y1);
+  const int ix0 = pext(hb, child_mask(o, x0)), iy0 = pext(hb, child_mask(o, y0));
+  const int ix1 = pext(hb, child_mask(o, x1)), iy1 = pext(hb, child_mask(o, y1));
+  const int nx0 = nvar_of(child_mask(o, x0)), ny0 = nvar_of(child_mask(o, y0));
+  const int nx1 = nvar_of(child_mask(o, x1)), ny1 = nvar_of(child_mask(o, y1));
+  const int t0 = o.dst + 6, t1 = t0 + 2 * nx0 * ny0;
+  const cxT<R> X = {W[t0 + 2 * (ix0 + nx0 * iy0)], W[t0 + 2 * (ix0 + nx0 * iy0) + 1]};
+  const cxT<R> Y = {W[t1 + 2 * (ix1 + nx1 * iy1)], W[t1 + 2 * (ix1 + nx1 * iy1) + 1]};
+  const int m0 = 3 - x0 - y0, m1 = 3 - x1 - y1;
+  cxT<R> a[4], b[4];
+  W.load4(child_base(o, m0) + 8 * pext(hb, child_mask(o, m0)), a);
+  W.load4(child_base(o, m1) + 8 * pext(hb, child_mask(o, m1)), b);
   cxT<R> out[4];
-  if (o.aux == 0) {
-    const cxT<R> x = rmul(s, mdot(e1, e3)), y = rmul(-s, mdot(e2, e3));
 #pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cfma(x, e2[j], cmul(y, e1[j]));
-  } else if (o.aux == 1) {
-    const cxT<R> x = rmul(s, mdot(e1, e2)), y = rmul(-s, mdot(e2, e3));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cfma(x, e3[j], cmul(y, e1[j]));
-  } else {
-    const cxT<R> x = rmul(s, mdot(e1, e2)), y = rmul(-s, mdot(e1, e3));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = cfma(x, e3[j], cmul(y, e2[j]));
-  }
-  W.store4(o.dst + 6 + 8 * v, out);
+  for (int j = 0; j < 4; ++j) out[j] = cfma(X, a[j], cmul(Y, b[j]));
+  W.store4(t1 + 2 * nx1 * ny1 + 8 * v, out);
 }
 
 // sum current: variant v = sum_t phase_t Y_t[v] over currents Y_t on the same legs; list entries

@@ -176,11 +176,28 @@ class _Builder:
     def nvar(self, i):
         return 1 << bin(self.cur(i).mask).count("1")
 
+    # VVVV colour structures: the two child pairs whose dot products each one needs
+    VVVV_PAIRS = {0: ((0, 2), (1, 2)), 1: ((0, 1), (1, 2)), 2: ((0, 1), (0, 2))}
+
+    def header(self, i):
+        """Header slots of current i.  VVV and VVVV headers also hold, per event, the dot
+        products that depend on only one child (VVV: (k-combination . e) per child variant) or one
+        pair of children (VVVV: e_x . e_y per pair of variants), so that the variants, which
+        range over all children's helicities, do not recompute them."""
+        c = self.cur(i)
+        h = HEADER[c.op]
+        if c.op == "VVV":
+            h += 2 * (self.nvar(c.children[0]) + self.nvar(c.children[1]))
+        elif c.op == "VVVV":
+            for x, y in self.VVVV_PAIRS[c.struct]:
+                h += 2 * self.nvar(c.children[x]) * self.nvar(c.children[y])
+        return h
+
     def blocksize(self, i):
-        return HEADER[self.cur(i).op] + 8 * self.nvar(i)
+        return self.header(i) + 8 * self.nvar(i)
 
     def varbase(self, i, offset):
-        return offset[i] + HEADER[self.cur(i).op]
+        return offset[i] + self.header(i)
 
     def current_row(self, i, offset, terms=None):
         D = self.D
@@ -493,8 +510,12 @@ def _wave_schedule(B, chunk):
                 w = []
                 for x in sorted(bylev.get(l, []), key=lambda i: (cur[i].op, i)):
                     w += [(row_of[x], v) for v in range(B.nvar(x))]
-                w += [(row_of[x], 255) for x in sorted(bylev.get(l + 1, []))]
+                # headers of the next level; VVV / VVVV headers read their children's variants
+                # (child dot products), so they wait for a wave of their own
+                nxt = sorted(bylev.get(l + 1, []))
+                w += [(row_of[x], 255) for x in nxt if cur[x].op not in ("VVV", "VVVV")]
                 waves.append(w)
+                waves.append([(row_of[x], 255) for x in nxt if cur[x].op in ("VVV", "VVVV")])
             for w in waves:
                 if w:
                     steps.append((0, len(items), len(w)))
@@ -544,7 +565,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
                   var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0, var_rbil=0)
     name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
             OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil", OP_RBIL: "rbil", OP_SUM: "sum"}
-    counts["sum"] = counts["sum_adds"] = 0
+    counts["sum"] = counts["sum_adds"] = counts["vvv_hdr"] = counts["vvvv_hdr"] = 0
     for op in ops:
         k = name[op[0]]
         counts[k] += 1
@@ -556,6 +577,11 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
             counts["sum_adds"] += (op[12] - 1) << bin(op[5]).count("1")     # 4-vector adds
         elif op[0] != OP_EXT:
             counts["var_" + k] += 1 << bin(op[5]).count("1")
+        if op[0] == OP_VVV:
+            counts["vvv_hdr"] += (1 << bin(op[6]).count("1")) + (1 << bin(op[7]).count("1"))
+        elif op[0] == OP_VVVV:
+            nv = [1 << bin(op[6 + j]).count("1") for j in range(3)]
+            counts["vvvv_hdr"] += sum(nv[x] * nv[y] for x, y in _Builder.VVVV_PAIRS[op[11]])
     # CTA schedule: largest chunk whose store fits the shared-memory budget
     cta = None
     nterm = len(D.terms)
