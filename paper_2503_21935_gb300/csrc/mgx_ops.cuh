@@ -93,6 +93,35 @@ __device__ __forceinline__ cxT<R> rot_phase(int code, cxT<R> a) {
   return {neg_if(r, code == 1 || code == 2), neg_if(i, code >= 2)};
 }
 
+// The slash blocks of a vector current variant V (A = V^0 - V.sigma, B = V^0 + V.sigma) are four
+// complex numbers: a00 = V0 - V3, a11 = V0 + V3, m = V1 - i V2, p = V1 + i V2 (A = [[a00, -m], [-p, a11]],
+// B = [[a11, m], [p, a00]]).  Fermion-vector vertices keep them per V variant in their header.
+template <class R, class S>
+__device__ __forceinline__ void store_slash(const S& W, int off, const cxT<R>* V) {
+  const cxT<R> sl[4] = {V[0] - V[3], V[0] + V[3], cxT<R>{V[1].r + V[2].i, V[1].i - V[2].r},
+                        cxT<R>{V[1].r - V[2].i, V[1].i + V[2].r}};
+  W.store4(off, sl);
+}
+template <class R, class S>
+__device__ __forceinline__ SlashT<R> load_slash(const S& W, int off) {
+  cxT<R> sl[4];
+  W.load4(off, sl);
+  SlashT<R> s;
+  s.a00 = sl[0]; s.a11 = sl[1]; s.b00 = sl[1]; s.b11 = sl[0];
+  s.a01 = cneg(sl[2]); s.a10 = cneg(sl[3]); s.b01 = sl[2]; s.b10 = sl[3];
+  return s;
+}
+// slash blocks of every variant of child b (the vector) into the header from offset 6
+template <class R, class S>
+__device__ __forceinline__ void header_slashes(const Op& o, const S& W) {
+  const int nv = 1 << __popc(o.mb);
+  for (int i = 0; i < nv; ++i) {
+    cxT<R> V[4];
+    W.load4(o.vb + 8 * i, V);
+    store_slash<R>(W, o.dst + 6 + 8 * i, V);
+  }
+}
+
 // VVVV colour structure j needs the dot products of two child pairs (children 0, 1, 2 = e1, e2, e3):
 // j = 0: (e1.e3, e2.e3), j = 1: (e1.e2, e2.e3), j = 2: (e1.e2, e1.e3)
 __device__ __forceinline__ void vvvv_pairs(int j, int& x0, int& y0, int& x1, int& y1) {
@@ -125,6 +154,7 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
     coupling<R>(P, o.cpl, gs, cl, cr, chiral);
     W[o.dst + 4] = chiral ? T::from(1.0) : cl.r;
     W[o.dst + 5] = chiral ? T::from(0.0) : cl.i;
+    if (o.code == OP_RBIL) header_slashes<R>(o, W);
     return;
   }
   R ka[4], kb[4], k[4];
@@ -207,6 +237,7 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
   if (!chiral) pref = cmul(pref, cl);
   W[o.dst + 4] = pref.r;
   W[o.dst + 5] = pref.i;
+  if (o.code != OP_FFV_V) header_slashes<R>(o, W);
 }
 
 // ================================================================ variants
@@ -234,15 +265,14 @@ template <class R, class S>
 __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs, const S& W) {
   using T = Real<R>;
   const int hb = pdep(v, o.mdst);
-  cxT<R> psi[4], V[4];
+  cxT<R> psi[4];
   W.load4(o.va + 8 * pext(hb, o.ma), psi);
-  W.load4(o.vb + 8 * pext(hb, o.mb), V);
+  const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
   R k[4];
   W.loadk(o.dst, k);
   const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
   const double md = P.mass[o.mass];
   const R a00 = k[0] - k[3], a11 = k[0] + k[3];
-  const SlashT<R> Sl = slash(V);
   cxT<R> u0 = cfma(Sl.a01, psi[3], cmul(Sl.a00, psi[2]));
   cxT<R> u1 = cfma(Sl.a11, psi[3], cmul(Sl.a10, psi[2]));
   cxT<R> l0 = cfma(Sl.b01, psi[1], cmul(Sl.b00, psi[0]));
@@ -266,7 +296,7 @@ __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs
     o2 = rfma(m, l0, o2); o3 = rfma(m, l1, o3);
   }
   cxT<R> out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
-  W.store4(o.dst + 6 + 8 * v, out);
+  W.store4(o.dst + 6 + 8 * (nvar_of(o.mb) + v), out);
 }
 
 // psibar' = pref psibar Vslash (cL PL + cR PR) (kslash' + m),  kslash' built from -k
@@ -274,9 +304,9 @@ template <class R, class S>
 __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double gs, const S& W) {
   using T = Real<R>;
   const int hb = pdep(v, o.mdst);
-  cxT<R> pb[4], V[4];
+  cxT<R> pb[4];
   W.load4(o.va + 8 * pext(hb, o.ma), pb);
-  W.load4(o.vb + 8 * pext(hb, o.mb), V);
+  const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
   R kin[4];
   W.loadk(o.dst, kin);
   const R k[4] = {-kin[0], -kin[1], -kin[2], -kin[3]};
@@ -284,7 +314,6 @@ __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double g
   const double md = P.mass[o.mass];
   const R a00 = k[0] - k[3], a11 = k[0] + k[3];
   const cxT<R> ka01 = {-k[1], k[2]}, ka10 = {-k[1], -k[2]};
-  const SlashT<R> Sl = slash(V);
   cxT<R> xu0 = cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00));
   cxT<R> xu1 = cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01));
   cxT<R> xl0 = cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00));
@@ -307,7 +336,7 @@ __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double g
     o2 = rfma(m, xl0, o2); o3 = rfma(m, xl1, o3);
   }
   cxT<R> out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
-  W.store4(o.dst + 6 + 8 * v, out);
+  W.store4(o.dst + 6 + 8 * (nvar_of(o.mb) + v), out);
 }
 
 // J = pref (C - k (k.C)/M^2),  C^mu = cL rbar_l sigmabar^mu c_L + cR rbar_u sigma^mu c_R
@@ -352,11 +381,10 @@ __device__ inline void var_ffv_v(const KParams& P, const Op& o, int v, double gs
 template <class R, class S>
 __device__ inline void var_rbil(const KParams& P, const Op& o, int v, double gs, const S& W) {
   const int hb = pdep(v, o.mdst);
-  cxT<R> pb[4], V[4];
+  cxT<R> pb[4];
   W.load4(o.va + 8 * pext(hb, o.ma), pb);
-  W.load4(o.vb + 8 * pext(hb, o.mb), V);
+  const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
   const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
-  const SlashT<R> Sl = slash(V);
   // psibar Vslash = (psibar_l B, psibar_u A)
   cxT<R> x[4] = {cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00)), cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01)),
                  cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00)), cfma(pb[1], Sl.a11, cmul(pb[0], Sl.a01))};
@@ -369,7 +397,7 @@ __device__ inline void var_rbil(const KParams& P, const Op& o, int v, double gs,
   }
   cxT<R> out[4];
   apply_pref(pref, x, out);
-  W.store4(o.dst + 6 + 8 * v, out);
+  W.store4(o.dst + 6 + 8 * (nvar_of(o.mb) + v), out);
 }
 
 // J^r = i [ (e1.e2) s(k1-k2)^r + e2^r (s(k2-k3).e1) + e1^r (s(k3-k1).e2) ],  s = -g_s/P^2;

@@ -29,6 +29,7 @@ OP_EXT, OP_FFV_F, OP_FFV_FB, OP_FFV_V, OP_VVV, OP_VVVV, OP_AMP, OP_BIL, OP_RBIL,
 EXT_U, EXT_V, EXT_UBAR, EXT_VBAR, EXT_EPS_IN, EXT_EPS_OUT = 0, 1, 2, 3, 4, 5
 NFIELD = 16
 FLOW_FIRST = 4                  # flow entry phase-code bit: first update of that flow (write, not add)
+CHILD_HEADER = ("VVV", "VVVV", "FFV_F", "FFV_FB", "RBIL")   # headers that read child variants
 
 # coupling flags
 C_GS = 1        # multiply by the per-event strong coupling g_s
@@ -182,11 +183,14 @@ class _Builder:
     def header(self, i):
         """Header slots of current i.  VVV and VVVV headers also hold, per event, the dot
         products that depend on only one child (VVV: (k-combination . e) per child variant) or one
-        pair of children (VVVV: e_x . e_y per pair of variants), so that the variants, which
+        pair of children (VVVV: e_x . e_y per pair of variants), and fermion-vector vertices hold
+        the slash blocks of each variant of their vector child, so that the variants, which
         range over all children's helicities, do not recompute them."""
         c = self.cur(i)
         h = HEADER[c.op]
-        if c.op == "VVV":
+        if c.op in ("FFV_F", "FFV_FB", "RBIL"):
+            h += 8 * self.nvar(c.children[1])          # slash blocks per vector variant
+        elif c.op == "VVV":
             h += 2 * (self.nvar(c.children[0]) + self.nvar(c.children[1]))
         elif c.op == "VVVV":
             for x, y in self.VVVV_PAIRS[c.struct]:
@@ -510,12 +514,12 @@ def _wave_schedule(B, chunk):
                 w = []
                 for x in sorted(bylev.get(l, []), key=lambda i: (cur[i].op, i)):
                     w += [(row_of[x], v) for v in range(B.nvar(x))]
-                # headers of the next level; VVV / VVVV headers read their children's variants
-                # (child dot products), so they wait for a wave of their own
+                # headers of the next level; headers that read their children's variants (dot
+                # products, slash blocks) wait for a wave of their own
                 nxt = sorted(bylev.get(l + 1, []))
-                w += [(row_of[x], 255) for x in nxt if cur[x].op not in ("VVV", "VVVV")]
+                w += [(row_of[x], 255) for x in nxt if cur[x].op not in CHILD_HEADER]
                 waves.append(w)
-                waves.append([(row_of[x], 255) for x in nxt if cur[x].op in ("VVV", "VVVV")])
+                waves.append([(row_of[x], 255) for x in nxt if cur[x].op in CHILD_HEADER])
             for w in waves:
                 if w:
                     steps.append((0, len(items), len(w)))
@@ -565,7 +569,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
                   var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0, var_rbil=0)
     name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
             OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil", OP_RBIL: "rbil", OP_SUM: "sum"}
-    counts["sum"] = counts["sum_adds"] = counts["vvv_hdr"] = counts["vvvv_hdr"] = 0
+    counts["sum"] = counts["sum_adds"] = counts["vvv_hdr"] = counts["vvvv_hdr"] = counts["slash_hdr"] = 0
     for op in ops:
         k = name[op[0]]
         counts[k] += 1
@@ -577,6 +581,8 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
             counts["sum_adds"] += (op[12] - 1) << bin(op[5]).count("1")     # 4-vector adds
         elif op[0] != OP_EXT:
             counts["var_" + k] += 1 << bin(op[5]).count("1")
+        if op[0] in (OP_FFV_F, OP_FFV_FB, OP_RBIL):
+            counts["slash_hdr"] += 1 << bin(op[7]).count("1")
         if op[0] == OP_VVV:
             counts["vvv_hdr"] += (1 << bin(op[6]).count("1")) + (1 << bin(op[7]).count("1"))
         elif op[0] == OP_VVVV:
