@@ -210,8 +210,7 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
       continue;
     }
     op_header<R>(P, o, gs, pe, W);
-    const int nv = 1 << __popc(o.mdst);
-    for (int v = 0; v < nv; ++v) op_variant<R>(P, o, v, gs, pe, W);
+    op_variants<R>(P, o, 1 << __popc(o.mdst), gs, pe, W);
   }
   if constexpr (std::is_same<R, double>::value) {
     if (mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3) {
@@ -1143,7 +1142,7 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   const double ngood = (double)pr->good.size();
   const double n = pr->prog->ncol;
   struct K { double fma, mul, add; };
-  const K ffv_f{56, 24, 2}, ffv_v{24, 24, 24}, bil{16, 16, 24}, rbil{24, 8, 0}, vvv{46, 10, 0},
+  const K ffv_f{56, 24, 0}, ffv_v{24, 24, 24}, bil{16, 16, 24}, rbil{24, 8, 0}, vvv{46, 10, 0},
       vvvv{24, 8, 0}, run{14, 2, 0}, term_add{0, 0, 8}, run_add{0, 0, 2}, flow{0, 0, 2},
       vvv_dot{6, 2, 0}, vvvv_dot{14, 4, 0}, slash{0, 0, 8};
   auto w = [&](const K& k) { return flops ? 2 * k.fma + k.mul + k.add : k.fma + k.mul + k.add; };

@@ -260,24 +260,45 @@ __device__ inline void var_ext(const KParams& P, const Op& o, int v, const doubl
   W.store4(o.dst + 4 + 8 * v, w);
 }
 
+// Per-op values of the f f V fermion currents, loaded once for all variants of the op
+template <class R>
+struct FfvCtx {
+  R k[4];         // the current's momentum as the propagator numerator sees it (-k for a row current)
+  R a00, a11;     // k0 - k3, k0 + k3
+  cxT<R> pref;    // propagator prefactor (non-chiral coupling folded in)
+  R m;
+  bool massive, chiral;
+  int out;        // workspace offset of variant 0
+};
+template <class R, class S>
+__device__ __forceinline__ FfvCtx<R> ffv_ctx(const KParams& P, const Op& o, const S& W, bool row) {
+  FfvCtx<R> c;
+  R kin[4];
+  W.loadk(o.dst, kin);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) c.k[j] = row ? -kin[j] : kin[j];
+  c.a00 = c.k[0] - c.k[3];
+  c.a11 = c.k[0] + c.k[3];
+  c.pref = {W[o.dst + 4], W[o.dst + 5]};
+  c.massive = P.massive[o.mass] != 0;
+  c.m = Real<R>::from(P.mass[o.mass]);
+  c.chiral = (P.cplflags[o.cpl] & CPL_CHIRAL) != 0;
+  c.out = o.dst + 6 + 8 * nvar_of(o.mb);
+  return c;
+}
+
 // psi' = pref (kslash + m) Vslash (cL PL + cR PR) psi
 template <class R, class S>
-__device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs, const S& W) {
-  using T = Real<R>;
+__device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs, const FfvCtx<R>& c, const S& W) {
   const int hb = pdep(v, o.mdst);
   cxT<R> psi[4];
   W.load4(o.va + 8 * pext(hb, o.ma), psi);
   const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
-  R k[4];
-  W.loadk(o.dst, k);
-  const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
-  const double md = P.mass[o.mass];
-  const R a00 = k[0] - k[3], a11 = k[0] + k[3];
   cxT<R> u0 = cfma(Sl.a01, psi[3], cmul(Sl.a00, psi[2]));
   cxT<R> u1 = cfma(Sl.a11, psi[3], cmul(Sl.a10, psi[2]));
   cxT<R> l0 = cfma(Sl.b01, psi[1], cmul(Sl.b00, psi[0]));
   cxT<R> l1 = cfma(Sl.b11, psi[1], cmul(Sl.b10, psi[0]));
-  if (P.cplflags[o.cpl] & CPL_CHIRAL) {
+  if (c.chiral) {
     cxT<R> cl, cr;
     bool ch;
     coupling<R>(P, o.cpl, gs, cl, cr, ch);
@@ -285,40 +306,34 @@ __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs
     l0 = cmul(cl, l0); l1 = cmul(cl, l1);
   }
   // upper = m phi_u + KA phi_l, lower = KB phi_u + m phi_l; KA = [[a00, -(k1-ik2)], [-(k1+ik2), a11]]
+  const R* k = c.k;
   const cxT<R> ka01 = {-k[1], k[2]}, ka10 = {-k[1], -k[2]};
-  cxT<R> o0 = cfma(ka01, l1, rmul(a00, l0));
-  cxT<R> o1 = cfma(ka10, l0, rmul(a11, l1));
-  cxT<R> o2 = cfma(cxT<R>{k[1], -k[2]}, u1, rmul(a11, u0));
-  cxT<R> o3 = cfma(cxT<R>{k[1], k[2]}, u0, rmul(a00, u1));
-  if (P.massive[o.mass]) {
-    const R m = T::from(md);
-    o0 = rfma(m, u0, o0); o1 = rfma(m, u1, o1);
-    o2 = rfma(m, l0, o2); o3 = rfma(m, l1, o3);
+  cxT<R> o0 = cfma(ka01, l1, rmul(c.a00, l0));
+  cxT<R> o1 = cfma(ka10, l0, rmul(c.a11, l1));
+  cxT<R> o2 = cfma(cxT<R>{k[1], -k[2]}, u1, rmul(c.a11, u0));
+  cxT<R> o3 = cfma(cxT<R>{k[1], k[2]}, u0, rmul(c.a00, u1));
+  if (c.massive) {
+    o0 = rfma(c.m, u0, o0); o1 = rfma(c.m, u1, o1);
+    o2 = rfma(c.m, l0, o2); o3 = rfma(c.m, l1, o3);
   }
-  cxT<R> out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
-  W.store4(o.dst + 6 + 8 * (nvar_of(o.mb) + v), out);
+  cxT<R> out[4] = {cmul(c.pref, o0), cmul(c.pref, o1), cmul(c.pref, o2), cmul(c.pref, o3)};
+  W.store4(c.out + 8 * v, out);
 }
 
 // psibar' = pref psibar Vslash (cL PL + cR PR) (kslash' + m),  kslash' built from -k
 template <class R, class S>
-__device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double gs, const S& W) {
-  using T = Real<R>;
+__device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double gs, const FfvCtx<R>& c, const S& W) {
   const int hb = pdep(v, o.mdst);
   cxT<R> pb[4];
   W.load4(o.va + 8 * pext(hb, o.ma), pb);
   const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
-  R kin[4];
-  W.loadk(o.dst, kin);
-  const R k[4] = {-kin[0], -kin[1], -kin[2], -kin[3]};
-  const cxT<R> pref = {W[o.dst + 4], W[o.dst + 5]};
-  const double md = P.mass[o.mass];
-  const R a00 = k[0] - k[3], a11 = k[0] + k[3];
+  const R* k = c.k;
   const cxT<R> ka01 = {-k[1], k[2]}, ka10 = {-k[1], -k[2]};
   cxT<R> xu0 = cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00));
   cxT<R> xu1 = cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01));
   cxT<R> xl0 = cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00));
   cxT<R> xl1 = cfma(pb[1], Sl.a11, cmul(pb[0], Sl.a01));
-  if (P.cplflags[o.cpl] & CPL_CHIRAL) {
+  if (c.chiral) {
     cxT<R> cl, cr;
     bool ch;
     coupling<R>(P, o.cpl, gs, cl, cr, ch);
@@ -326,17 +341,16 @@ __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double g
     xl0 = cmul(cr, xl0); xl1 = cmul(cr, xl1);
   }
   // x (kslash + m) = (m x_u + x_l KB, x_u KA + m x_l)
-  cxT<R> o0 = cfma(xl1, cneg(ka10), rmul(a11, xl0));
-  cxT<R> o1 = cfma(xl0, cneg(ka01), rmul(a00, xl1));
-  cxT<R> o2 = cfma(xu1, ka10, rmul(a00, xu0));
-  cxT<R> o3 = cfma(xu0, ka01, rmul(a11, xu1));
-  if (P.massive[o.mass]) {
-    const R m = T::from(md);
-    o0 = rfma(m, xu0, o0); o1 = rfma(m, xu1, o1);
-    o2 = rfma(m, xl0, o2); o3 = rfma(m, xl1, o3);
+  cxT<R> o0 = cfma(xl1, cneg(ka10), rmul(c.a11, xl0));
+  cxT<R> o1 = cfma(xl0, cneg(ka01), rmul(c.a00, xl1));
+  cxT<R> o2 = cfma(xu1, ka10, rmul(c.a00, xu0));
+  cxT<R> o3 = cfma(xu0, ka01, rmul(c.a11, xu1));
+  if (c.massive) {
+    o0 = rfma(c.m, xu0, o0); o1 = rfma(c.m, xu1, o1);
+    o2 = rfma(c.m, xl0, o2); o3 = rfma(c.m, xl1, o3);
   }
-  cxT<R> out[4] = {cmul(pref, o0), cmul(pref, o1), cmul(pref, o2), cmul(pref, o3)};
-  W.store4(o.dst + 6 + 8 * (nvar_of(o.mb) + v), out);
+  cxT<R> out[4] = {cmul(c.pref, o0), cmul(c.pref, o1), cmul(c.pref, o2), cmul(c.pref, o3)};
+  W.store4(c.out + 8 * v, out);
 }
 
 // J = pref (C - k (k.C)/M^2),  C^mu = cL rbar_l sigmabar^mu c_L + cR rbar_u sigma^mu c_R
@@ -473,8 +487,8 @@ template <class R, class S>
 __device__ inline void op_variant(const KParams& P, const Op& o, int v, double gs, const double* pe, const S& W) {
   switch (o.code) {
     case OP_EXT: var_ext<R>(P, o, v, pe, W); break;
-    case OP_FFV_F: var_ffv_f<R>(P, o, v, gs, W); break;
-    case OP_FFV_FB: var_ffv_fb<R>(P, o, v, gs, W); break;
+    case OP_FFV_F: var_ffv_f<R>(P, o, v, gs, ffv_ctx<R>(P, o, W, false), W); break;
+    case OP_FFV_FB: var_ffv_fb<R>(P, o, v, gs, ffv_ctx<R>(P, o, W, true), W); break;
     case OP_FFV_V:
     case OP_BIL: var_ffv_v<R>(P, o, v, gs, W); break;   // the column bilinear is the vertex current without propagator
     case OP_RBIL: var_rbil<R>(P, o, v, gs, W); break;
@@ -482,6 +496,21 @@ __device__ inline void op_variant(const KParams& P, const Op& o, int v, double g
     case OP_SUM: var_sum<R>(P, o, v, W); break;
     default: var_vvvv<R>(P, o, v, W); break;
   }
+}
+
+// all nv variants of one op (the thread-per-event kernel): per-op values loaded once
+template <class R, class S>
+__device__ inline void op_variants(const KParams& P, const Op& o, int nv, double gs, const double* pe, const S& W) {
+  if (o.code == OP_FFV_F || o.code == OP_FFV_FB) {
+    const bool row = o.code == OP_FFV_FB;
+    const FfvCtx<R> c = ffv_ctx<R>(P, o, W, row);
+    if (row)
+      for (int v = 0; v < nv; ++v) var_ffv_fb<R>(P, o, v, gs, c, W);
+    else
+      for (int v = 0; v < nv; ++v) var_ffv_f<R>(P, o, v, gs, c, W);
+    return;
+  }
+  for (int v = 0; v < nv; ++v) op_variant<R>(P, o, v, gs, pe, W);
 }
 
 // ================================================================ diagram amplitudes
