@@ -263,7 +263,7 @@ __device__ inline void var_ext(const KParams& P, const Op& o, int v, const doubl
 // Per-op values of the f f V fermion currents, loaded once for all variants of the op
 template <class R>
 struct FfvCtx {
-  R k[4];         // the current's momentum as the propagator numerator sees it (-k for a row current)
+  R k1, k2;       // the current's momentum as the propagator numerator sees it (-k for a row current)
   R a00, a11;     // k0 - k3, k0 + k3
   cxT<R> pref;    // propagator prefactor (non-chiral coupling folded in)
   R m;
@@ -273,12 +273,16 @@ struct FfvCtx {
 template <class R, class S>
 __device__ __forceinline__ FfvCtx<R> ffv_ctx(const KParams& P, const Op& o, const S& W, bool row) {
   FfvCtx<R> c;
-  R kin[4];
-  W.loadk(o.dst, kin);
+  R k[4];
+  W.loadk(o.dst, k);
+  if (row) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) c.k[j] = row ? -kin[j] : kin[j];
-  c.a00 = c.k[0] - c.k[3];
-  c.a11 = c.k[0] + c.k[3];
+    for (int j = 0; j < 4; ++j) k[j] = -k[j];
+  }
+  c.k1 = k[1];
+  c.k2 = k[2];
+  c.a00 = k[0] - k[3];
+  c.a11 = k[0] + k[3];
   c.pref = {W[o.dst + 4], W[o.dst + 5]};
   c.massive = P.massive[o.mass] != 0;
   c.m = Real<R>::from(P.mass[o.mass]);
@@ -306,12 +310,11 @@ __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs
     l0 = cmul(cl, l0); l1 = cmul(cl, l1);
   }
   // upper = m phi_u + KA phi_l, lower = KB phi_u + m phi_l; KA = [[a00, -(k1-ik2)], [-(k1+ik2), a11]]
-  const R* k = c.k;
-  const cxT<R> ka01 = {-k[1], k[2]}, ka10 = {-k[1], -k[2]};
+  const cxT<R> ka01 = {-c.k1, c.k2}, ka10 = {-c.k1, -c.k2};
   cxT<R> o0 = cfma(ka01, l1, rmul(c.a00, l0));
   cxT<R> o1 = cfma(ka10, l0, rmul(c.a11, l1));
-  cxT<R> o2 = cfma(cxT<R>{k[1], -k[2]}, u1, rmul(c.a11, u0));
-  cxT<R> o3 = cfma(cxT<R>{k[1], k[2]}, u0, rmul(c.a00, u1));
+  cxT<R> o2 = cfma(cxT<R>{c.k1, -c.k2}, u1, rmul(c.a11, u0));
+  cxT<R> o3 = cfma(cxT<R>{c.k1, c.k2}, u0, rmul(c.a00, u1));
   if (c.massive) {
     o0 = rfma(c.m, u0, o0); o1 = rfma(c.m, u1, o1);
     o2 = rfma(c.m, l0, o2); o3 = rfma(c.m, l1, o3);
@@ -327,8 +330,7 @@ __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double g
   cxT<R> pb[4];
   W.load4(o.va + 8 * pext(hb, o.ma), pb);
   const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
-  const R* k = c.k;
-  const cxT<R> ka01 = {-k[1], k[2]}, ka10 = {-k[1], -k[2]};
+  const cxT<R> ka01 = {-c.k1, c.k2}, ka10 = {-c.k1, -c.k2};
   cxT<R> xu0 = cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00));
   cxT<R> xu1 = cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01));
   cxT<R> xl0 = cfma(pb[1], Sl.a10, cmul(pb[0], Sl.a00));
