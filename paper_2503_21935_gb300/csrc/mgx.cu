@@ -298,7 +298,11 @@ struct BatchIO {
 
 constexpr int kMaxBatch = 16;
 
-struct BatchIOArray {
+// Everything the batch kernel reads per process, passed by value (about 17 KB of kernel
+// parameters): the process parameters then sit in the constant bank like the single-process
+// kernel's, instead of being loaded from global memory on every use.
+struct BatchParams {
+  KParams kp[kMaxBatch];
   BatchIO io[kMaxBatch];
 };
 
@@ -311,7 +315,7 @@ struct BatchDesc {
 // (register budget of 4 resident blocks per SM, as the thread-per-event kernel gets by default:
 // occupancy hides the workspace latency better than the few registers more would)
 __global__ void __launch_bounds__(kThreads, 4)
-    batch_kernel(const KParams* __restrict__ params, const BatchIOArray io, const BatchDesc D,
+    batch_kernel(const __grid_constant__ BatchParams BP, const BatchDesc D,
                  unsigned long long* __restrict__ counter, double* __restrict__ ws, int64_t nthreads, int mode) {
   extern __shared__ double smem[];
   __shared__ long long s_item;
@@ -326,8 +330,8 @@ __global__ void __launch_bounds__(kThreads, 4)
     if (item >= nitems) break;
     int p = 0;
     while (item >= D.item_start[p + 1]) ++p;
-    const KParams& P = params[p];
-    const BatchIO b = io.io[p];
+    const KParams& P = BP.kp[p];
+    const BatchIO& b = BP.io[p];
     const int npar4 = 4 * P.npar;
     const int64_t first = (item - D.item_start[p]) * D.epi[p];
     const int64_t last = min(first + (int64_t)D.epi[p], b.nevt);
@@ -1179,7 +1183,6 @@ double mgx_fp64_flops_per_event(const mgx_process* pr, int mode) { return pr ? f
 struct mgx_batch {
   int device = 0;
   std::vector<mgx_process*> procs;
-  KParams* d_params = nullptr;
   int blocks_per_sm = 4;
   std::vector<int> epi;       // events per work item, per process
   int max_ws = 0, max_npar4 = 0;
@@ -1218,10 +1221,14 @@ int batch_launch(mgx_batch* b, const mgx_batch_io* io, int mode, void* ws, size_
   unsigned long long* counter = (unsigned long long*)ws;
   double* w = (double*)((char*)ws + 256);
   if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st) != cudaSuccess) return MGX_ERR_CUDA;
-  BatchIOArray arr;
-  for (int p = 0; p < n; ++p) arr.io[p] = ios[p];
+  static_assert(sizeof(BatchParams) + sizeof(BatchDesc) + 64 < 32000, "batch kernel parameters too large");
+  BatchParams bp;
+  for (int p = 0; p < n; ++p) {
+    bp.kp[p] = b->procs[p]->kp;
+    bp.io[p] = ios[p];
+  }
   const size_t shm = (size_t)kThreads * b->max_npar4 * sizeof(double);
-  batch_kernel<<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(b->d_params, arr, D, counter, w, nt, mode);
+  batch_kernel<<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(bp, D, counter, w, nt, mode);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
@@ -1234,23 +1241,11 @@ extern "C" int mgx_batch_create(mgx_process* const* procs, int nproc, mgx_batch*
     if (!procs[p] || procs[p]->device != procs[0]->device) return MGX_ERR_DEVICE_MISMATCH;
   mgx_batch* b = new mgx_batch();
   b->device = procs[0]->device;
-  std::vector<KParams> kp;
   b->epi.assign(nproc, 512);
   for (int p = 0; p < nproc; ++p) {
     b->procs.push_back(procs[p]);
-    kp.push_back(procs[p]->kp);
     b->max_ws = std::max(b->max_ws, procs[p]->kp.ws_doubles);
     b->max_npar4 = std::max(b->max_npar4, 4 * procs[p]->kp.npar);
-  }
-  int cur = 0;
-  cudaGetDevice(&cur);
-  cudaSetDevice(b->device);
-  const bool ok = cudaMalloc(&b->d_params, sizeof(KParams) * nproc) == cudaSuccess &&
-                  cudaMemcpy(b->d_params, kp.data(), sizeof(KParams) * nproc, cudaMemcpyHostToDevice) == cudaSuccess;
-  cudaSetDevice(cur);
-  if (!ok) {
-    mgx_batch_destroy(b);
-    return MGX_ERR_CUDA;
   }
   *out = b;
   return MGX_OK;
@@ -1260,7 +1255,6 @@ extern "C" void mgx_batch_destroy(mgx_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFree(b->d_params);
   delete b;
 }
 
