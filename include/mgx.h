@@ -156,8 +156,9 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
 enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2 };
 int mgx_process_set_kernel(mgx_process* proc, int kernel);  /* INVALID_ARGUMENT if unusable */
 int mgx_process_get_kernel(const mgx_process* proc);        /* the kernel AUTO resolves to */
-/* Thread blocks of 128 threads per SM for the thread-per-event kernel (1..16, default 4);
- * the workspace size grows with it. */
+/* Thread blocks of 128 threads per SM for the thread-per-event kernel (1..16, default 4; the
+ * float mode launches twice as many, its kernel having half the registers); the workspace
+ * size grows with it.  The CTA-per-event kernel serves MGX_FP64 and MGX_MIXED_FP32 only. */
 int mgx_process_set_blocks_per_sm(mgx_process* proc, int blocks_per_sm);
 
 /* ---- batched multi-process launch (one persistent kernel over several processes) ----

@@ -261,8 +261,10 @@ __device__ __forceinline__ void stage_momenta(const double* __restrict__ mom, in
   __syncthreads();
 }
 
+// 4 resident blocks per SM for float64 (128 registers), 8 for float (64 registers): the float
+// path is latency-bound on its workspace and gains from the extra warps
 template <class R>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 4)
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
               int32_t* __restrict__ selhel, int32_t* __restrict__ selcol, double* __restrict__ mh_out,
@@ -618,13 +620,18 @@ struct mgx_process {
 
 namespace {
 
-int64_t grid_threads(const mgx_process* pr, int64_t nevt) {
-  const int64_t cap = (int64_t)sm_count(pr->device) * pr->blocks_per_sm * kThreads;
+// the float kernel has half the registers of the float64 one (64 vs 128), so twice the blocks fit
+int64_t grid_threads(const mgx_process* pr, int64_t nevt, int mode = MGX_FP64) {
+  const int bps = mode == MGX_FLOAT ? 2 * pr->blocks_per_sm : pr->blocks_per_sm;
+  const int64_t cap = (int64_t)sm_count(pr->device) * bps * kThreads;
   const int64_t need = ((nevt + kThreads - 1) / kThreads) * kThreads;
   return std::max<int64_t>(kThreads, std::min(cap, need));
 }
 
-int64_t ws_doubles_per_thread(const KParams& kp) { return kp.ws_doubles; }
+// per-thread workspace bytes: one 8-byte slot per element, 4-byte in the float mode
+size_t thread_ws_bytes(const KParams& kp, int mode) {
+  return (size_t)kp.ws_doubles * (mode == MGX_FLOAT ? sizeof(float) : sizeof(double));
+}
 
 void set_layout(KParams& kp, int cur_doubles, int ngood, int ncol) {
   kp.cur_doubles = cur_doubles;
@@ -765,8 +772,8 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
   if (mode == MGX_MIXED_BF16X3)
     return launch_tc<TcBf16x3>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
   if (mode_f64(mode) && use_cta(pr, kp)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
-  const int64_t nt = grid_threads(pr, nevt);
-  const size_t need = (size_t)nt * ws_doubles_per_thread(kp) * sizeof(double);
+  const int64_t nt = grid_threads(pr, nevt, mode);
+  const size_t need = (size_t)nt * thread_ws_bytes(kp, mode);
   if (wsb < need || ws == nullptr) return MGX_ERR_WORKSPACE_TOO_SMALL;
   const int blocks = (int)(nt / kThreads);
   const size_t shm = (size_t)kThreads * 4 * kp.npar * sizeof(double);
@@ -1044,7 +1051,9 @@ int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* b
     *bytes = nevt == 0 ? 0 : tc_plan(pr, pr->kp, nevt).total;
     return MGX_OK;
   }
-  *bytes = (nevt == 0 || use_cta(pr, pr->kp)) ? 0 : (size_t)grid_threads(pr, nevt) * pr->kp.ws_doubles * sizeof(double);
+  *bytes = (nevt == 0 || (mode_f64(mode) && use_cta(pr, pr->kp)))
+               ? 0
+               : (size_t)grid_threads(pr, nevt, mode) * thread_ws_bytes(pr->kp, mode);
   return MGX_OK;
 }
 
