@@ -169,7 +169,7 @@ def _workload_config(nevt, mode):
     wl = WORKLOADS[WORKLOAD]
     return {"workload": f"g g > t t~ g g, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, alpha_s=0.118",
             "process": wl.process, "nevt_per_gpu": nevt, "mode": mode,
-            "l2": "inputs larger than L2 (192 MiB momenta, 4.3 GB workspace)"}
+            "l2": "inputs larger than L2 (192 MiB momenta, 5.0 GB workspace)"}
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
