@@ -244,9 +244,10 @@ def extra_ggttggg(pkg, dev, stream):
 
 
 def extra_eemumu(pkg, dev, stream):
-    """e+ e- > mu+ mu-, 8192 events: a launch- and latency-bound case.  Microseconds per launch,
-    launched directly and replayed from a CUDA graph of 20 launches, and the HBM bandwidth that the
-    algorithmic bytes (momenta, alpha_s, two random numbers in; me and two selections out) imply."""
+    """e+ e- > mu+ mu-, 8192 events: a small batch.  Microseconds per launch, launched directly and
+    replayed from a CUDA graph of 20 launches; the HBM bandwidth that the algorithmic bytes
+    (momenta, alpha_s, two random numbers in; me and two selections out) imply, and the FP64 pipe
+    fraction that the batch's float64 instructions imply."""
     import numpy as np
     import torch
     from phasespace import WORKLOADS, make_inputs
@@ -270,7 +271,9 @@ def extra_eemumu(pkg, dev, stream):
                 step()
         graph_ms = _timed(g.replay, 20, 2, side) / 20
     algo = n * (4 * 4 * 8 + 3 * 8 + 8 + 4 + 4)
-    return {"nevt": n, "ngood": proc.ngood,
+    inst = proc.fp64_ops_per_event(0) * n
+    return {"nevt": n, "ngood": proc.ngood, "kernel": proc.kernel,
+            "fp64_inst_per_event": inst / n, "fp64_pipe_frac_graph": inst / (graph_ms * 1e-3) / (FP64_PEAK_GINST * 1e9),
             "direct_us_per_launch": direct_ms * 1e3, "graph_us_per_launch": graph_ms * 1e3,
             "events_per_s_direct": n / (direct_ms * 1e-3), "events_per_s_graph": n / (graph_ms * 1e-3),
             "algorithmic_bytes_per_launch": algo, "hbm_gbs_graph": algo / (graph_ms * 1e-3) / 1e9}

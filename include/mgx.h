@@ -149,11 +149,14 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
                      void* stream);
 
 /* Kernel variant (for tuning and testing).  THREAD: one thread per event, current variants
- * and jamps in the global workspace (the default that AUTO resolves to).  CTA: one thread
- * block per event with the event's currents in shared memory; available when the
- * process's current store fits in shared memory and ncol <= 32.  Both give identical
- * results up to float64 rounding. */
-enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2 };
+ * and jamps in the global workspace (what AUTO resolves to for throughput batches).  CTA: one
+ * thread block per event with the event's currents in shared memory; available when the
+ * process's current store fits in shared memory and ncol <= 32 (MGX_FP64, MGX_MIXED_FP32).
+ * THREAD_SMEM: the thread-per-event kernel with each thread's workspace in shared memory
+ * (64 threads per block, no caller workspace needed); available for small processes (e+ e- >
+ * mu+ mu-, g g > t t~), and what AUTO picks when the whole batch fits one block per SM (a
+ * latency-bound batch).  All give identical results up to float64 rounding. */
+enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2, MGX_KERNEL_THREAD_SMEM = 3 };
 int mgx_process_set_kernel(mgx_process* proc, int kernel);  /* INVALID_ARGUMENT if unusable */
 int mgx_process_get_kernel(const mgx_process* proc);        /* the kernel AUTO resolves to */
 /* Thread blocks of 128 threads per SM for the thread-per-event kernel (1..16, default 4; the

@@ -22,7 +22,7 @@ MGX_MIXED_BF16X3 = 3
 MGX_FLOAT = 4
 MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32, "mixed_tf32": MGX_MIXED_TF32,
          "mixed_bf16x3": MGX_MIXED_BF16X3, "float": MGX_FLOAT}
-MGX_KERNEL_AUTO, MGX_KERNEL_THREAD, MGX_KERNEL_CTA = 0, 1, 2
+MGX_KERNEL_AUTO, MGX_KERNEL_THREAD, MGX_KERNEL_CTA, MGX_KERNEL_THREAD_SMEM = 0, 1, 2, 3
 
 
 class MgxError(RuntimeError):
@@ -366,7 +366,7 @@ class Process:
         return ws
 
     def set_kernel(self, kernel):
-        """MGX_KERNEL_AUTO / MGX_KERNEL_THREAD / MGX_KERNEL_CTA."""
+        """MGX_KERNEL_AUTO / MGX_KERNEL_THREAD / MGX_KERNEL_CTA / MGX_KERNEL_THREAD_SMEM."""
         _check(lib().mgx_process_set_kernel(self._h, kernel), "mgx_process_set_kernel")
 
     @property

@@ -262,9 +262,11 @@ __device__ __forceinline__ void stage_momenta(const double* __restrict__ mom, in
 }
 
 // 4 resident blocks per SM for float64 (128 registers), 8 for float (64 registers): the float
-// path is latency-bound on its workspace and gains from the extra warps
-template <class R>
-__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 4)
+// path is latency-bound on its workspace and gains from the extra warps.  With kSmemWs the
+// per-event workspace lives in shared memory after the staged momenta (small processes in
+// latency-bound batches, kSmemThreads threads per block, one block per SM).
+template <class R, bool kSmemWs>
+__global__ void __launch_bounds__(kThreads, kSmemWs ? 1 : (std::is_same<R, float>::value ? 8 : 4))
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
               int32_t* __restrict__ selhel, int32_t* __restrict__ selcol, double* __restrict__ mh_out,
@@ -273,7 +275,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 
   extern __shared__ double smem[];
   const int npar4 = 4 * P.npar;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const WST<R> W{reinterpret_cast<R*>(ws) + tid, nthreads};
+  const WST<R> W = kSmemWs ? WST<R>{reinterpret_cast<R*>(smem + blockDim.x * npar4) + threadIdx.x, blockDim.x}
+                           : WST<R>{reinterpret_cast<R*>(ws) + tid, nthreads};
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nevt; base += nthreads) {
     stage_momenta(mom, base, min((int64_t)blockDim.x, nevt - base), npar4, smem);
     const int64_t e = base + threadIdx.x;
@@ -649,6 +652,23 @@ bool use_cta(const mgx_process* pr, const KParams& kp) {
   return pr->kernel == MGX_KERNEL_CTA && cta_usable(pr, kp);
 }
 
+// shared-memory-workspace variant of the thread-per-event kernel
+constexpr int kSmemThreads = 64;
+constexpr size_t kSmemMax = 227u << 10;   // dynamic shared memory per block
+size_t smem_ws_block_bytes(const KParams& kp, int mode) {
+  return (size_t)kSmemThreads * (thread_ws_bytes(kp, mode) + 4 * kp.npar * sizeof(double));
+}
+bool smem_usable(const KParams& kp, int mode) {
+  return (mode == MGX_FP64 || mode == MGX_MIXED_FP32 || mode == MGX_FLOAT) && smem_ws_block_bytes(kp, mode) <= kSmemMax;
+}
+// the thread kernel with its workspace in shared memory: chosen explicitly, or by AUTO when the
+// whole batch fits one pass of a block per SM (a latency-bound batch of a small process)
+bool use_smem_ws(const mgx_process* pr, const KParams& kp, int64_t nevt, int mode) {
+  if (!smem_usable(kp, mode)) return false;
+  if (pr->kernel == MGX_KERNEL_THREAD_SMEM) return true;
+  return pr->kernel == MGX_KERNEL_AUTO && nevt <= (int64_t)kSmemThreads * sm_count(pr->device);
+}
+
 size_t cta_smem_bytes(const mgx_process* pr, const KParams& kp) {
   const int ngp = kp.ngood <= 32 ? 32 : (kp.ngood <= 64 ? 64 : 128);
   const int G = kCtaThreads / ngp;
@@ -746,7 +766,7 @@ int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mo
     const int64_t n = std::min(t.chunk, nevt - c0);
     const int64_t nt = grid_threads(pr, n);
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return MGX_ERR_CUDA;
-    me_kernel<double><<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(kp, n, mom + c0 * npar4, as + c0, nullptr, nullptr,
+    me_kernel<double, false><<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(kp, n, mom + c0 * npar4, as + c0, nullptr, nullptr,
                                                                 me + c0, nullptr, nullptr, nullptr, nullptr, w_thr, nt,
                                                                 MGX_MIXED_TF32, jexp, colw);
     const int64_t rows = 2 * n * kp.ngood;
@@ -772,16 +792,26 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
   if (mode == MGX_MIXED_BF16X3)
     return launch_tc<TcBf16x3>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
   if (mode_f64(mode) && use_cta(pr, kp)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
+  if (use_smem_ws(pr, kp, nevt, mode)) {
+    const size_t smem = smem_ws_block_bytes(kp, mode);
+    auto kern = mode == MGX_FLOAT ? me_kernel<float, true> : me_kernel<double, true>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return MGX_ERR_CUDA;
+    const int64_t blocks = std::min<int64_t>((nevt + kSmemThreads - 1) / kSmemThreads, sm_count(pr->device));
+    kern<<<(unsigned)blocks, kSmemThreads, smem, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, nullptr,
+                                                       blocks * kSmemThreads, mode, nullptr, nullptr);
+    return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+  }
   const int64_t nt = grid_threads(pr, nevt, mode);
   const size_t need = (size_t)nt * thread_ws_bytes(kp, mode);
   if (wsb < need || ws == nullptr) return MGX_ERR_WORKSPACE_TOO_SMALL;
   const int blocks = (int)(nt / kThreads);
   const size_t shm = (size_t)kThreads * 4 * kp.npar * sizeof(double);
   if (mode == MGX_FLOAT)
-    me_kernel<float><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
+    me_kernel<float, false><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
                                                     mode, nullptr, nullptr);
   else
-    me_kernel<double><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
+    me_kernel<double, false><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
                                                      mode, nullptr, nullptr);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
@@ -1051,7 +1081,7 @@ int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* b
     *bytes = nevt == 0 ? 0 : tc_plan(pr, pr->kp, nevt).total;
     return MGX_OK;
   }
-  *bytes = (nevt == 0 || (mode_f64(mode) && use_cta(pr, pr->kp)))
+  *bytes = (nevt == 0 || (mode_f64(mode) && use_cta(pr, pr->kp)) || use_smem_ws(pr, pr->kp, nevt, mode))
                ? 0
                : (size_t)grid_threads(pr, nevt, mode) * thread_ws_bytes(pr->kp, mode);
   return MGX_OK;
@@ -1130,15 +1160,17 @@ int mgx_compute_host(mgx_process* pr, int64_t nevt, const double* momenta, const
 }
 
 int mgx_process_set_kernel(mgx_process* pr, int kernel) {
-  if (!pr || kernel < MGX_KERNEL_AUTO || kernel > MGX_KERNEL_CTA) return MGX_ERR_INVALID_ARGUMENT;
+  if (!pr || kernel < MGX_KERNEL_AUTO || kernel > MGX_KERNEL_THREAD_SMEM) return MGX_ERR_INVALID_ARGUMENT;
   if (kernel == MGX_KERNEL_CTA && !cta_usable(pr, pr->kp)) return MGX_ERR_INVALID_ARGUMENT;
+  if (kernel == MGX_KERNEL_THREAD_SMEM && !smem_usable(pr->kp, MGX_FP64)) return MGX_ERR_INVALID_ARGUMENT;
   pr->kernel = kernel;
   return MGX_OK;
 }
 
 int mgx_process_get_kernel(const mgx_process* pr) {
   if (!pr) return MGX_ERR_INVALID_ARGUMENT;
-  return use_cta(pr, pr->kp) ? MGX_KERNEL_CTA : MGX_KERNEL_THREAD;
+  if (use_cta(pr, pr->kp)) return MGX_KERNEL_CTA;
+  return pr->kernel == MGX_KERNEL_THREAD_SMEM ? MGX_KERNEL_THREAD_SMEM : MGX_KERNEL_THREAD;
 }
 
 int mgx_process_set_blocks_per_sm(mgx_process* pr, int blocks_per_sm) {
@@ -1371,6 +1403,7 @@ extern "C" int mgx_process_autotune(mgx_process* pr, int64_t nevt, const double*
   struct Cand { int kernel, bps; };
   std::vector<Cand> cands = {{MGX_KERNEL_THREAD, 2}, {MGX_KERNEL_THREAD, 4}};
   if (cta_usable(pr, pr->kp) && mode_f64(mode)) cands.push_back({MGX_KERNEL_CTA, 4});
+  if (smem_usable(pr->kp, mode)) cands.push_back({MGX_KERNEL_THREAD_SMEM, 4});
   const int save_k = pr->kernel, save_b = pr->blocks_per_sm;
   float best = 1e30f;
   Cand pick{save_k, save_b};
@@ -1457,7 +1490,7 @@ extern "C" int mgx_compute_noalloc(mgx_process* pr, int64_t nevt, const double* 
   const int64_t blocks = std::max<int64_t>(1, std::min({fit, want, cap}));
   const int64_t nt = blocks * kThreads;
   const size_t shm = (size_t)kThreads * 4 * pr->kp.npar * sizeof(double);
-  me_kernel<double><<<(unsigned)blocks, kThreads, shm, (cudaStream_t)stream>>>(
+  me_kernel<double, false><<<(unsigned)blocks, kThreads, shm, (cudaStream_t)stream>>>(
       pr->kp, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, scratch, nt, mode,
       nullptr, nullptr);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;

@@ -38,10 +38,11 @@ def _run(proc, mom, a, rh, rc, mode=0):
 
 
 CASES = [("eemumu", 300), ("ggtt", 300), ("ggttg", 260), ("ggttgg", 160), ("ggttggg", 20), ("gu_tataggu", 140)]
-KERNELS = {"thread": 1, "cta": 2}
+KERNELS = {"auto": 0, "thread": 1, "cta": 2, "smem": 3}
+SMEM_PROCESSES = ("eemumu", "ggtt")        # per-thread workspace small enough for shared memory
 
 
-@pytest.mark.parametrize("kernel", ["thread", "cta"])
+@pytest.mark.parametrize("kernel", ["thread", "cta", "smem"])
 @pytest.mark.parametrize("name,nevt", CASES)
 def test_parity_fp64(name, nevt, kernel):
     wl = WORKLOADS[name]
@@ -49,6 +50,8 @@ def test_parity_fp64(name, nevt, kernel):
     proc = _proc(wl.process)
     if kernel == "cta" and name == "ggttggg":
         pytest.skip("g g > t t~ g g g: current store does not fit in shared memory (thread kernel only)")
+    if kernel == "smem" and name not in SMEM_PROCESSES:
+        pytest.skip("per-thread workspace too large for the shared-memory kernel")
     proc.set_kernel(KERNELS[kernel])
     try:
         got = _run(proc, mom, a, rh, rc)
@@ -119,7 +122,7 @@ FLOAT_CASES = [("eemumu", 300, 1e-4), ("ggtt", 300, 1e-4), ("ggttg", 260, 1e-4),
                ("ggttggg", 20, 1e-4), ("gu_tataggu", 140, 1e-2)]
 
 
-@pytest.mark.parametrize("kernel", ["thread", "cta"])
+@pytest.mark.parametrize("kernel", ["thread", "cta", "smem"])
 @pytest.mark.parametrize("name,nevt,bound", FLOAT_CASES)
 def test_parity_float_mode(name, nevt, bound, kernel):
     """Float32 path: me within the stated bound; |M_h|^2 and colour weights relative to the event total too."""
@@ -128,6 +131,8 @@ def test_parity_float_mode(name, nevt, bound, kernel):
     proc = _proc(wl.process)
     if kernel == "cta" and name == "ggttggg":
         pytest.skip("g g > t t~ g g g: no CTA kernel to select")
+    if kernel == "smem" and name not in SMEM_PROCESSES:
+        pytest.skip("per-thread workspace too large for the shared-memory kernel")
     proc.set_kernel(KERNELS[kernel])   # the float path always runs the thread-per-event kernel
     try:
         got = _run(proc, mom, a, rh, rc, mode=4)
@@ -162,6 +167,32 @@ def test_ragged_sizes(nevt):
     ref = oracle_get(wl.process).evaluate(mom, a)
     rel = np.abs(got["me"] / ref["me"] - 1.0)
     assert np.all(rel <= _bounds(wl.process, mom, a, rel))
+
+
+def test_shared_memory_workspace_kernel_multi_pass_and_auto():
+    """The shared-memory-workspace kernel over several passes of its grid equals the global-workspace
+    kernel; AUTO takes it for a latency-bound batch and needs no caller workspace then."""
+    import paper_2503_21935_gb300 as pkg
+    wl = WORKLOADS["ggtt"]
+    n = 64 * 152 * 3 + 17
+    mom, a, rh, rc = make_inputs(wl, n)
+    proc = _proc(wl.process)
+    proc.set_kernel(3)
+    try:
+        assert proc.kernel == 3
+        sm = _run(proc, mom, a, rh, rc)
+        assert proc.workspace_bytes(n) == 0
+    finally:
+        proc.set_kernel(1)
+    try:
+        gl = _run(proc, mom, a, rh, rc)
+    finally:
+        proc.set_kernel(0)
+    assert np.abs(sm["me"] / gl["me"] - 1.0).max() <= TOL
+    assert np.array_equal(sm["selhel"], gl["selhel"]) and np.array_equal(sm["selcol"], gl["selcol"])
+    assert proc.workspace_bytes(1000) == 0 and proc.workspace_bytes(1 << 20) > 0
+    with pytest.raises(pkg.MgxError):
+        _proc(WORKLOADS["ggttgg"].process).set_kernel(3)
 
 
 def _degenerate_events():
