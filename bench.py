@@ -272,7 +272,7 @@ def extra_eemumu(pkg, dev, stream):
         graph_ms = _timed(g.replay, 20, 2, side) / 20
     algo = n * (4 * 4 * 8 + 3 * 8 + 8 + 4 + 4)
     inst = proc.fp64_ops_per_event(0) * n
-    return {"nevt": n, "ngood": proc.ngood, "kernel": proc.kernel,
+    return {"nevt": n, "ngood": proc.ngood, "workspace_in_shared_memory": proc.workspace_bytes(n) == 0,
             "fp64_inst_per_event": inst / n, "fp64_pipe_frac_graph": inst / (graph_ms * 1e-3) / (FP64_PEAK_GINST * 1e9),
             "direct_us_per_launch": direct_ms * 1e3, "graph_us_per_launch": graph_ms * 1e3,
             "events_per_s_direct": n / (direct_ms * 1e-3), "events_per_s_graph": n / (graph_ms * 1e-3),
