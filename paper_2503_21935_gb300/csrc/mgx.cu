@@ -193,6 +193,44 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
     const Op o = load_op(P.ops, iop);
     if (o.code == OP_AMP) {
       const int2* fl = P.flows + o.cpl;
+      if (o.aux2 == 1) {
+        // one term X . Y: the helicities run as (bilinear variant, other variant) pairs so that
+        // each bilinear variant is loaded once; the term's phase rotates the product
+        const int4 a = __ldg(P.terms + 2 * o.aux);
+        const int4 b = __ldg(P.terms + 2 * o.aux + 1);
+        const int nx = 1 << __popc(a.y), ny = 1 << __popc(a.w);
+        for (int ix = 0; ix < nx; ++ix) {
+          cxT<R> X[4];
+          W.load4(a.x + 8 * ix, X);
+          const int hx = pdep(ix, a.y);
+          for (int iy = 0; iy < ny; ++iy) {
+            const int ih = P.hidx[hx | pdep(iy, a.w)];
+            if (ih < 0) continue;
+            cxT<R> Y[4];
+            W.load4(a.z + 8 * iy, Y);
+            cxT<R> amp;
+            if (b.y == 0) {
+              amp = mdot(X, Y);
+            } else {
+              amp = cmul(X[0], Y[0]);
+              amp = cfma(X[1], Y[1], amp);
+              amp = cfma(X[2], Y[2], amp);
+              amp = cfma(X[3], Y[3], amp);
+            }
+            amp = rot_phase(b.x, amp);
+            const int jb = P.jamp_off + 2 * P.ncol * ih;
+            for (int f = 0; f < o.mass; ++f) {
+              const int2 q = __ldg(fl + f);
+              const int off = jb + 2 * q.x;
+              cxT<R> j = rot_phase(q.y & 3, amp);
+              if (!(q.y & 4)) j = cxT<R>{W[off], W[off + 1]} + j;
+              W[off] = j.r;
+              W[off + 1] = j.i;
+            }
+          }
+        }
+        continue;
+      }
       for (int ih = 0; ih < P.ngood; ++ih) {
         const cxT<R> amp = group_amp<R>(P.terms, o, P.good[ih], W);
         const int jb = P.jamp_off + 2 * P.ncol * ih;
@@ -1012,7 +1050,10 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
   filter_events(nf, prog->npar, sqrts, masses, filter_seed, hmom);
   KParams fk = kp;
   fk.ngood = pr->nhel;
-  for (int h = 0; h < pr->nhel; ++h) fk.good[h] = h;
+  for (int h = 0; h < pr->nhel; ++h) {
+    fk.good[h] = h;
+    fk.hidx[h] = (signed char)h;
+  }
   set_layout(fk, prog->ws_doubles, fk.ngood, n);
   const int64_t nt = grid_threads(pr, nf);
   const size_t wsb = (size_t)nt * fk.ws_doubles * sizeof(double);
@@ -1043,7 +1084,11 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
     return MGX_ERR_NO_GOOD_HELICITY;
   }
   kp.ngood = (int)pr->good.size();
-  for (int i = 0; i < kp.ngood; ++i) kp.good[i] = pr->good[i];
+  for (int h = 0; h < MAXHEL; ++h) kp.hidx[h] = -1;
+  for (int i = 0; i < kp.ngood; ++i) {
+    kp.good[i] = pr->good[i];
+    kp.hidx[pr->good[i]] = (signed char)i;
+  }
   set_layout(kp, prog->ws_doubles, kp.ngood, n);
   cudaSetDevice(cur);
   *out = pr;

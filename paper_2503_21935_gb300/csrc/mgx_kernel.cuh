@@ -52,6 +52,7 @@ struct KParams {
   double mass[MAXMASS], width[MAXMASS];
   int massive[MAXMASS];  // mass[i] > 0, tested without a float64 compare
   int good[MAXHEL];      // canonical indices of the good helicities
+  signed char hidx[MAXHEL];  // rank of canonical helicity h among the good ones, -1 if not good
 };
 
 template <class R>
