@@ -9,6 +9,8 @@
 // variant bases (fields 13-15), so no op needs to know its children's kinds.
 // Sum currents (OP_SUM) have no header; their summand list lives in the term table.
 #pragma once
+#include <type_traits>
+
 #include "mgx_kernel.cuh"
 
 namespace mgx {
@@ -293,11 +295,9 @@ __device__ __forceinline__ FfvCtx<R> ffv_ctx(const KParams& P, const Op& o, cons
 
 // psi' = pref (kslash + m) Vslash (cL PL + cR PR) psi
 template <class R, class S>
-__device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs, const FfvCtx<R>& c, const S& W) {
-  const int hb = pdep(v, o.mdst);
-  cxT<R> psi[4];
-  W.load4(o.va + 8 * pext(hb, o.ma), psi);
-  const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
+__device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, int ib, const cxT<R>* psi, double gs,
+                                 const FfvCtx<R>& c, const S& W) {
+  const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * ib);
   cxT<R> u0 = cfma(Sl.a01, psi[3], cmul(Sl.a00, psi[2]));
   cxT<R> u1 = cfma(Sl.a11, psi[3], cmul(Sl.a10, psi[2]));
   cxT<R> l0 = cfma(Sl.b01, psi[1], cmul(Sl.b00, psi[0]));
@@ -325,11 +325,9 @@ __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, double gs
 
 // psibar' = pref psibar Vslash (cL PL + cR PR) (kslash' + m),  kslash' built from -k
 template <class R, class S>
-__device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, double gs, const FfvCtx<R>& c, const S& W) {
-  const int hb = pdep(v, o.mdst);
-  cxT<R> pb[4];
-  W.load4(o.va + 8 * pext(hb, o.ma), pb);
-  const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * pext(hb, o.mb));
+__device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, int ib, const cxT<R>* pb, double gs,
+                                  const FfvCtx<R>& c, const S& W) {
+  const SlashT<R> Sl = load_slash<R>(W, o.dst + 6 + 8 * ib);
   const cxT<R> ka01 = {-c.k1, c.k2}, ka10 = {-c.k1, -c.k2};
   cxT<R> xu0 = cfma(pb[3], Sl.b10, cmul(pb[2], Sl.b00));
   cxT<R> xu1 = cfma(pb[3], Sl.b11, cmul(pb[2], Sl.b01));
@@ -440,6 +438,24 @@ __device__ inline void var_vvv(const KParams& P, const Op& o, int v, const S& W)
   W.store4(o.dst + 18 + 2 * (n1 + n2) + 8 * v, out);
 }
 
+// the same for a pair loop that holds the first child, its dot and s (k1 - k2) already
+template <class R, class S>
+__device__ inline void var_vvv_pair(const Op& o, int v, const cxT<R>* e1, cxT<R> a1, int i2, const R* d, int n1,
+                               const S& W) {
+  cxT<R> e2[4];
+  W.load4(o.vb + 8 * i2, e2);
+  const cxT<R> s12 = mdot(e1, e2);
+  const cxT<R> a2 = {W[o.dst + 18 + 2 * (n1 + i2)], W[o.dst + 18 + 2 * (n1 + i2) + 1]};
+  const int n2 = nvar_of(o.mb);
+  cxT<R> out[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const cxT<R> t = cfma(e1[j], a2, cfma(e2[j], a1, rmul(d[j], s12)));
+    out[j] = {Real<R>::neg(t.i), t.r};
+  }
+  W.store4(o.dst + 18 + 2 * (n1 + n2) + 8 * v, out);
+}
+
 // J = s { j=0: (e1.e3) e2 - (e2.e3) e1 ; j=1: (e1.e2) e3 - (e2.e3) e1 ; j=2: (e1.e2) e3 - (e1.e3) e2 },
 // i.e. J = X e_m0 + Y e_m1 with X = s (pair 0 dot), Y = -s (pair 1 dot) from the header's pair
 // tables and m0, m1 the children outside pair 0, pair 1
@@ -489,8 +505,18 @@ template <class R, class S>
 __device__ inline void op_variant(const KParams& P, const Op& o, int v, double gs, const double* pe, const S& W) {
   switch (o.code) {
     case OP_EXT: var_ext<R>(P, o, v, pe, W); break;
-    case OP_FFV_F: var_ffv_f<R>(P, o, v, gs, ffv_ctx<R>(P, o, W, false), W); break;
-    case OP_FFV_FB: var_ffv_fb<R>(P, o, v, gs, ffv_ctx<R>(P, o, W, true), W); break;
+    case OP_FFV_F:
+    case OP_FFV_FB: {
+      // variant v = (spinor child variant ia, vector child variant ib)
+      const int hb = pdep(v, o.mdst);
+      cxT<R> psi[4];
+      W.load4(o.va + 8 * pext(hb, o.ma), psi);
+      if (o.code == OP_FFV_F)
+        var_ffv_f<R>(P, o, v, pext(hb, o.mb), psi, gs, ffv_ctx<R>(P, o, W, false), W);
+      else
+        var_ffv_fb<R>(P, o, v, pext(hb, o.mb), psi, gs, ffv_ctx<R>(P, o, W, true), W);
+      break;
+    }
     case OP_FFV_V:
     case OP_BIL: var_ffv_v<R>(P, o, v, gs, W); break;   // the column bilinear is the vertex current without propagator
     case OP_RBIL: var_rbil<R>(P, o, v, gs, W); break;
@@ -503,13 +529,41 @@ __device__ inline void op_variant(const KParams& P, const Op& o, int v, double g
 // all nv variants of one op (the thread-per-event kernel): per-op values loaded once
 template <class R, class S>
 __device__ inline void op_variants(const KParams& P, const Op& o, int nv, double gs, const double* pe, const S& W) {
+  if (std::is_same<R, float>::value && o.code == OP_VVV) {
+    // variants as (first child variant, second child variant) pairs, first child loaded once
+    // (float path only: in the float64 kernel the values kept live across the pairs cost spills
+    // that outweigh the saved loads)
+    R d[4];
+    W.loadk(o.dst + 6, d);
+    const int n1 = nvar_of(o.ma), n2 = nvar_of(o.mb);
+    for (int i1 = 0; i1 < n1; ++i1) {
+      cxT<R> e1[4];
+      W.load4(o.va + 8 * i1, e1);
+      const cxT<R> a1 = {W[o.dst + 18 + 2 * i1], W[o.dst + 18 + 2 * i1 + 1]};
+      const int h1 = pdep(i1, o.ma);
+      for (int i2 = 0; i2 < n2; ++i2)
+        var_vvv_pair<R>(o, pext(h1 | pdep(i2, o.mb), o.mdst), e1, a1, i2, d, n1, W);
+    }
+    return;
+  }
   if (o.code == OP_FFV_F || o.code == OP_FFV_FB) {
+    // variants as (spinor child variant, vector child variant) pairs: each spinor variant is
+    // loaded once (the op's legs are the disjoint union of its children's)
     const bool row = o.code == OP_FFV_FB;
     const FfvCtx<R> c = ffv_ctx<R>(P, o, W, row);
-    if (row)
-      for (int v = 0; v < nv; ++v) var_ffv_fb<R>(P, o, v, gs, c, W);
-    else
-      for (int v = 0; v < nv; ++v) var_ffv_f<R>(P, o, v, gs, c, W);
+    const int na = nvar_of(o.ma), nb = nvar_of(o.mb);
+    for (int ia = 0; ia < na; ++ia) {
+      cxT<R> psi[4];
+      W.load4(o.va + 8 * ia, psi);
+      const int ha = pdep(ia, o.ma);
+      for (int ib = 0; ib < nb; ++ib) {
+        const int v = pext(ha | pdep(ib, o.mb), o.mdst);
+        if (row)
+          var_ffv_fb<R>(P, o, v, ib, psi, gs, c, W);
+        else
+          var_ffv_f<R>(P, o, v, ib, psi, gs, c, W);
+      }
+    }
     return;
   }
   for (int v = 0; v < nv; ++v) op_variant<R>(P, o, v, gs, pe, W);
