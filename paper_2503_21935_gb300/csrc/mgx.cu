@@ -37,10 +37,11 @@ struct mgx_program_desc {
   int gs_power;          // power of g_s of every amplitude (vertices are evaluated with g_s = 1)
   int col_den;           // common denominator of the colour matrix
   int jamp_zero;         // some flow is never updated: zero the jamps first
-  int counts[16];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows,
+  int counts[17];        // variants: ffv_f, ffv_fb, ffv_v, vvv, vvvv, bil, rbil; current ops; amp terms, flows,
                          // groups, runs (terms sharing one bilinear within a group); sum-current
                          // 4-vector adds (variants x (summands - 1)); VVV header child dots; VVVV
-                         // header pair dots; header slash blocks (vector variants of f f V vertices)
+                         // header pair dots; header slash blocks (vector variants of f f V vertices);
+                         // those of them scaled by a fermion propagator prefactor
   struct {
     int nops;
     const int32_t* ops;
@@ -1232,9 +1233,9 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   const double ngood = (double)pr->good.size();
   const double n = pr->prog->ncol;
   struct K { double fma, mul, add; };
-  const K ffv_f{56, 24, 0}, ffv_v{24, 24, 24}, bil{16, 16, 24}, rbil{24, 8, 0}, vvv{46, 10, 0},
+  const K ffv_f{48, 16, 0}, ffv_v{24, 24, 24}, bil{16, 16, 24}, rbil{24, 8, 0}, vvv{46, 10, 0},
       vvvv{24, 8, 0}, run{14, 2, 0}, term_add{0, 0, 8}, run_add{0, 0, 2}, flow{0, 0, 2},
-      vvv_dot{6, 2, 0}, vvvv_dot{14, 4, 0}, slash{0, 0, 8};
+      vvv_dot{6, 2, 0}, vvvv_dot{14, 4, 0}, slash{0, 0, 8}, slash_pref{8, 8, 0};
   auto w = [&](const K& k) { return flops ? 2 * k.fma + k.mul + k.add : k.fma + k.mul + k.add; };
   double t = w(ffv_f) * (c[0] + c[1]) + w(ffv_v) * c[2] + w(vvv) * c[3] + w(vvvv) * c[4] + w(bil) * c[5] +
              w(rbil) * c[6];
@@ -1244,7 +1245,7 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   t += ngood * (w(run) * c[11] + w(term_add) * (c[8] - c[11]) + w(run_add) * (c[11] - c[10]) + w(flow) * flow_adds);
   t += w(term_add) * c[12];                        // sum currents, per variant of their legs
   t += w(vvv_dot) * c[13] + w(vvvv_dot) * c[14];   // per-event child dot tables of VVV / VVVV
-  t += w(slash) * c[15];                           // per-event slash blocks of f f V vertices
+  t += w(slash) * c[15] + w(slash_pref) * c[16];  // per-event slash blocks of f f V vertices
   if (mode == MGX_FP64) t += ngood * (flops ? 2 * n * n + 4 * n : n * n + 3 * n);  // quadratic form
   else if (!flops) t += ngood * 2 * n;                                              // f64 -> f32 conversions
   t += ngood * (flops ? 4 * n : 2 * n);                                             // colour weights

@@ -97,11 +97,20 @@ __device__ __forceinline__ cxT<R> rot_phase(int code, cxT<R> a) {
 
 // The slash blocks of a vector current variant V (A = V^0 - V.sigma, B = V^0 + V.sigma) are four
 // complex numbers: a00 = V0 - V3, a11 = V0 + V3, m = V1 - i V2, p = V1 + i V2 (A = [[a00, -m], [-p, a11]],
-// B = [[a11, m], [p, a00]]).  Fermion-vector vertices keep them per V variant in their header.
+// B = [[a11, m], [p, a00]]).  Fermion-vector vertices keep them per V variant in their header; a
+// fermion current stores them times its propagator prefactor (a scalar, so it commutes with every
+// factor of the current), which is then paid once per vector variant instead of once per variant.
 template <class R, class S>
 __device__ __forceinline__ void store_slash(const S& W, int off, const cxT<R>* V) {
   const cxT<R> sl[4] = {V[0] - V[3], V[0] + V[3], cxT<R>{V[1].r + V[2].i, V[1].i - V[2].r},
                         cxT<R>{V[1].r - V[2].i, V[1].i + V[2].r}};
+  W.store4(off, sl);
+}
+template <class R, class S>
+__device__ __forceinline__ void store_slash(const S& W, int off, const cxT<R>* V, cxT<R> pref) {
+  const cxT<R> sl[4] = {cmul(pref, V[0] - V[3]), cmul(pref, V[0] + V[3]),
+                        cmul(pref, cxT<R>{V[1].r + V[2].i, V[1].i - V[2].r}),
+                        cmul(pref, cxT<R>{V[1].r - V[2].i, V[1].i + V[2].r})};
   W.store4(off, sl);
 }
 template <class R, class S>
@@ -121,6 +130,15 @@ __device__ __forceinline__ void header_slashes(const Op& o, const S& W) {
     cxT<R> V[4];
     W.load4(o.vb + 8 * i, V);
     store_slash<R>(W, o.dst + 6 + 8 * i, V);
+  }
+}
+template <class R, class S>
+__device__ __forceinline__ void header_slashes(const Op& o, const S& W, cxT<R> pref) {
+  const int nv = 1 << __popc(o.mb);
+  for (int i = 0; i < nv; ++i) {
+    cxT<R> V[4];
+    W.load4(o.vb + 8 * i, V);
+    store_slash<R>(W, o.dst + 6 + 8 * i, V, pref);
   }
 }
 
@@ -237,9 +255,12 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
   bool chiral;
   coupling<R>(P, o.cpl, gs, cl, cr, chiral);
   if (!chiral) pref = cmul(pref, cl);
-  W[o.dst + 4] = pref.r;
-  W[o.dst + 5] = pref.i;
-  if (o.code != OP_FFV_V) header_slashes<R>(o, W);
+  if (o.code == OP_FFV_V) {
+    W[o.dst + 4] = pref.r;
+    W[o.dst + 5] = pref.i;
+  } else {
+    header_slashes<R>(o, W, pref);
+  }
 }
 
 // ================================================================ variants
@@ -267,7 +288,6 @@ template <class R>
 struct FfvCtx {
   R k1, k2;       // the current's momentum as the propagator numerator sees it (-k for a row current)
   R a00, a11;     // k0 - k3, k0 + k3
-  cxT<R> pref;    // propagator prefactor (non-chiral coupling folded in)
   R m;
   bool massive, chiral;
   int out;        // workspace offset of variant 0
@@ -285,7 +305,6 @@ __device__ __forceinline__ FfvCtx<R> ffv_ctx(const KParams& P, const Op& o, cons
   c.k2 = k[2];
   c.a00 = k[0] - k[3];
   c.a11 = k[0] + k[3];
-  c.pref = {W[o.dst + 4], W[o.dst + 5]};
   c.massive = P.massive[o.mass] != 0;
   c.m = Real<R>::from(P.mass[o.mass]);
   c.chiral = (P.cplflags[o.cpl] & CPL_CHIRAL) != 0;
@@ -293,7 +312,7 @@ __device__ __forceinline__ FfvCtx<R> ffv_ctx(const KParams& P, const Op& o, cons
   return c;
 }
 
-// psi' = pref (kslash + m) Vslash (cL PL + cR PR) psi
+// psi' = (kslash + m) (pref Vslash) (cL PL + cR PR) psi, pref Vslash from the header
 template <class R, class S>
 __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, int ib, const cxT<R>* psi, double gs,
                                  const FfvCtx<R>& c, const S& W) {
@@ -319,11 +338,11 @@ __device__ inline void var_ffv_f(const KParams& P, const Op& o, int v, int ib, c
     o0 = rfma(c.m, u0, o0); o1 = rfma(c.m, u1, o1);
     o2 = rfma(c.m, l0, o2); o3 = rfma(c.m, l1, o3);
   }
-  cxT<R> out[4] = {cmul(c.pref, o0), cmul(c.pref, o1), cmul(c.pref, o2), cmul(c.pref, o3)};
+  const cxT<R> out[4] = {o0, o1, o2, o3};
   W.store4(c.out + 8 * v, out);
 }
 
-// psibar' = pref psibar Vslash (cL PL + cR PR) (kslash' + m),  kslash' built from -k
+// psibar' = psibar (pref Vslash) (cL PL + cR PR) (kslash' + m),  kslash' built from -k
 template <class R, class S>
 __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, int ib, const cxT<R>* pb, double gs,
                                   const FfvCtx<R>& c, const S& W) {
@@ -349,7 +368,7 @@ __device__ inline void var_ffv_fb(const KParams& P, const Op& o, int v, int ib, 
     o0 = rfma(c.m, xu0, o0); o1 = rfma(c.m, xu1, o1);
     o2 = rfma(c.m, xl0, o2); o3 = rfma(c.m, xl1, o3);
   }
-  cxT<R> out[4] = {cmul(c.pref, o0), cmul(c.pref, o1), cmul(c.pref, o2), cmul(c.pref, o3)};
+  const cxT<R> out[4] = {o0, o1, o2, o3};
   W.store4(c.out + 8 * v, out);
 }
 

@@ -67,7 +67,7 @@ def emit(path):
             f'{len(P.masses)}, {pre}_mass, {pre}_extmass, {P.ws_current_doubles}, {P.ndiagrams}, '
             f'{P.nterms}, {P.average_den}, {P.gs_power}, {P.col_den}, {P.jamp_zero}, '
             f'{{{c["var_ffv_f"]}, {c["var_ffv_fb"]}, {c["var_ffv_v"]}, {c["var_vvv"]}, {c["var_vvvv"]}, {c["var_bil"]}, {c["var_rbil"]}, '
-            f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"] + c["bil"] + c["rbil"]}, {c["amp_terms"]}, {c["amp_flows"]}, {c["amp"]}, {c["amp_runs"]}, {c["sum_adds"]}, {c["vvv_hdr"]}, {c["vvvv_hdr"]}, {c["slash_hdr"]}}}, '
+            f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"] + c["bil"] + c["rbil"]}, {c["amp_terms"]}, {c["amp_flows"]}, {c["amp"]}, {c["amp_runs"]}, {c["sum_adds"]}, {c["vvv_hdr"]}, {c["vvvv_hdr"]}, {c["slash_hdr"]}, {c["slash_pref_hdr"]}}}, '
             f'{cta_init}}},')
     out.append("static const mgx_program_desc mgx_programs[] = {\n" + "\n".join(entries) + "\n};\n")
     out.append(f"static const int mgx_num_programs = {len(BUILTIN)};\n")

@@ -570,6 +570,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
             OP_VVVV: "vvvv", OP_AMP: "amp", OP_BIL: "bil", OP_RBIL: "rbil", OP_SUM: "sum"}
     counts["sum"] = counts["sum_adds"] = counts["vvv_hdr"] = counts["vvvv_hdr"] = counts["slash_hdr"] = 0
+    counts["slash_pref_hdr"] = 0
     for op in ops:
         k = name[op[0]]
         counts[k] += 1
@@ -583,6 +584,8 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
             counts["var_" + k] += 1 << bin(op[5]).count("1")
         if op[0] in (OP_FFV_F, OP_FFV_FB, OP_RBIL):
             counts["slash_hdr"] += 1 << bin(op[7]).count("1")
+        if op[0] in (OP_FFV_F, OP_FFV_FB):
+            counts["slash_pref_hdr"] += 1 << bin(op[7]).count("1")
         if op[0] == OP_VVV:
             counts["vvv_hdr"] += (1 << bin(op[6]).count("1")) + (1 << bin(op[7]).count("1"))
         elif op[0] == OP_VVVV:

@@ -3,7 +3,7 @@
 A small MLP learns log|M|^2 over phase space from events the exact path evaluates; it then
 drives stage 1 of a two-stage unweighting whose stage 2 corrects every surviving event with
 its exact |M|^2 (Danziger, Janssen, Schumann, Siegert, arXiv:2109.11964), so the unweighted
-sample stays unbiased and the exact path remains the judge.  Every arithmetic step runs in the
+sample stays unbiased and the exact |M|^2 has the last word.  Every arithmetic step runs in the
 library's kernels (phase space, cuts, matrix elements, network, weights, accept/reject,
 compaction); this module sequences the calls and holds device buffers (PyTorch tensors).
 """
