@@ -151,14 +151,18 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
 /* Kernel variant (for tuning and testing).  THREAD: one thread per event, current variants
  * and jamps in the global workspace (what AUTO resolves to for throughput batches).  CTA: one
  * thread block per event with the event's currents in shared memory; available when the
- * process's current store fits in shared memory and ncol <= 32 (MGX_FP64, MGX_MIXED_FP32).
+ * process's current store fits in shared memory and ncol <= 32 (MGX_FP64, MGX_MIXED_FP32), and
+ * what AUTO picks in those modes for a batch too small to fill the thread kernel's grid: at most
+ * 48 events per SM, or 8 per SM for a process that has THREAD_SMEM (no caller workspace needed).
  * THREAD_SMEM: the thread-per-event kernel with each thread's workspace in shared memory
  * (64 threads per block, no caller workspace needed); available for small processes (e+ e- >
- * mu+ mu-, g g > t t~), and what AUTO picks when the whole batch fits one block per SM (a
- * latency-bound batch).  All give identical results up to float64 rounding. */
+ * mu+ mu-, g g > t t~), and what AUTO picks otherwise when the whole batch fits one block per SM
+ * (a latency-bound batch).  All give identical results up to float64 rounding. */
 enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2, MGX_KERNEL_THREAD_SMEM = 3 };
 int mgx_process_set_kernel(mgx_process* proc, int kernel);  /* INVALID_ARGUMENT if unusable */
-int mgx_process_get_kernel(const mgx_process* proc);        /* the kernel AUTO resolves to */
+/* the kernel set; for AUTO, THREAD (the choice for throughput batches; AUTO picks CTA or
+ * THREAD_SMEM per call for small batches, as above) */
+int mgx_process_get_kernel(const mgx_process* proc);
 /* Thread blocks of 128 threads per SM for the thread-per-event kernel (1..16, default 4; the
  * float mode launches twice as many, its kernel having half the registers); the workspace
  * size grows with it.  The CTA-per-event kernel serves MGX_FP64 and MGX_MIXED_FP32 only. */

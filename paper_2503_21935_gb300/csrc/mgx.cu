@@ -683,6 +683,14 @@ void set_layout(KParams& kp, int cur_doubles, int ngood, int ncol) {
   kp.ws_doubles = kp.colw_off + ncol;
 }
 
+bool mode_ok(int mode) {
+  return mode == MGX_FP64 || mode == MGX_MIXED_FP32 || mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3 ||
+         mode == MGX_FLOAT;
+}
+bool mode_tc(int mode) { return mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3; }
+// modes whose whole path is the float64 amplitude code (CTA kernel, batch, fixed-scratch entry)
+bool mode_f64(int mode) { return mode == MGX_FP64 || mode == MGX_MIXED_FP32; }
+
 bool cta_usable(const mgx_process* pr, const KParams& kp) {
   return pr->prog->cta.nops > 0 && kp.ngood <= 128 && kp.ncol <= kMaxColCta;
 }
@@ -706,6 +714,18 @@ bool use_smem_ws(const mgx_process* pr, const KParams& kp, int64_t nevt, int mod
   if (!smem_usable(kp, mode)) return false;
   if (pr->kernel == MGX_KERNEL_THREAD_SMEM) return true;
   return pr->kernel == MGX_KERNEL_AUTO && nevt <= (int64_t)kSmemThreads * sm_count(pr->device);
+}
+
+// AUTO on a batch too small to fill the thread kernel's grid: the launch then lasts as long as
+// one thread takes for one event, and one block per event (the CTA kernel) takes a fraction of
+// that.  Measured crossovers on GB300 in FP64: about 9.5k events (g g > t t~ g), 12k (g u~ >
+// ta+ ta- g g u~) and 19k (g g > t t~ g g) against the thread kernel, about 2k against the
+// shared-memory thread kernel of the small processes; the limits below stay under them.
+bool use_cta_kernel(const mgx_process* pr, const KParams& kp, int64_t nevt, int mode) {
+  if (!mode_f64(mode) || !cta_usable(pr, kp)) return false;
+  if (pr->kernel == MGX_KERNEL_CTA) return true;
+  const int64_t per_sm = smem_usable(kp, mode) ? 8 : 48;
+  return pr->kernel == MGX_KERNEL_AUTO && nevt <= per_sm * sm_count(pr->device);
 }
 
 size_t cta_smem_bytes(const mgx_process* pr, const KParams& kp) {
@@ -732,14 +752,6 @@ int launch_cta(mgx_process* pr, const KParams& kp, int64_t nevt, const double* m
   me_cta_kernel<<<(unsigned)blocks, kCtaThreads, smem, st>>>(kp, C, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
-
-bool mode_ok(int mode) {
-  return mode == MGX_FP64 || mode == MGX_MIXED_FP32 || mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3 ||
-         mode == MGX_FLOAT;
-}
-bool mode_tc(int mode) { return mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3; }
-// modes whose whole path is the float64 amplitude code (CTA kernel, batch, fixed-scratch entry)
-bool mode_f64(int mode) { return mode == MGX_FP64 || mode == MGX_MIXED_FP32; }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -830,7 +842,7 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
   if (mode == MGX_MIXED_TF32) return launch_tc<TcTf32>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
   if (mode == MGX_MIXED_BF16X3)
     return launch_tc<TcBf16x3>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
-  if (mode_f64(mode) && use_cta(pr, kp)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
+  if (use_cta_kernel(pr, kp, nevt, mode)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
   if (use_smem_ws(pr, kp, nevt, mode)) {
     const size_t smem = smem_ws_block_bytes(kp, mode);
     auto kern = mode == MGX_FLOAT ? me_kernel<float, true> : me_kernel<double, true>;
@@ -1127,7 +1139,7 @@ int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* b
     *bytes = nevt == 0 ? 0 : tc_plan(pr, pr->kp, nevt).total;
     return MGX_OK;
   }
-  *bytes = (nevt == 0 || (mode_f64(mode) && use_cta(pr, pr->kp)) || use_smem_ws(pr, pr->kp, nevt, mode))
+  *bytes = (nevt == 0 || use_cta_kernel(pr, pr->kp, nevt, mode) || use_smem_ws(pr, pr->kp, nevt, mode))
                ? 0
                : (size_t)grid_threads(pr, nevt, mode) * thread_ws_bytes(pr->kp, mode);
   return MGX_OK;

@@ -21,7 +21,9 @@ def _setup():
         t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
         inp = (t(mom), t(a), t(rh), t(rc))
         p = pkg.Process(wl.process)
+        p.set_kernel(pkg.MGX_KERNEL_THREAD)   # the batch kernel runs the same per-thread code
         ref = p.compute(*inp)
+        p.set_kernel(pkg.MGX_KERNEL_AUTO)
         procs.append(p)
         inputs.append(inp)
         outs.append({"me": torch.zeros(n, dtype=torch.float64, device=dev),

@@ -39,6 +39,7 @@ def test_noalloc_matches_compute(name, nevt):
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
     proc = pkg.Process(wl.process, device=0)
+    proc.set_kernel(pkg.MGX_KERNEL_THREAD)     # the kernel the fixed-scratch entry point runs
     ref = proc.compute(M, A, RH, RC, mode=pkg.MGX_FP64)
     torch.cuda.synchronize()
     ptr = lambda x: ctypes.c_void_p(x.data_ptr())
