@@ -366,7 +366,9 @@ class Process:
         return ws
 
     def set_kernel(self, kernel):
-        """MGX_KERNEL_AUTO / MGX_KERNEL_THREAD / MGX_KERNEL_CTA / MGX_KERNEL_THREAD_SMEM."""
+        """MGX_KERNEL_AUTO / MGX_KERNEL_THREAD / MGX_KERNEL_CTA / MGX_KERNEL_THREAD_SMEM.  AUTO picks per
+        call by batch size: one block per event (CTA) or the shared-memory thread kernel for small
+        batches, the thread kernel otherwise."""
         _check(lib().mgx_process_set_kernel(self._h, kernel), "mgx_process_set_kernel")
 
     @property

@@ -2,7 +2,7 @@
 
 One program per process.  Each op is 16 int32 fields:
   0 code  1 dst  2 a  3 b  4 c  5 mask_dst  6 mask_a  7 mask_b  8 mask_c
-  9 coupling  10 mass/width entry  11 aux  12 aux2  13..15 reserved
+  9 coupling  10 mass/width entry  11 aux  12 aux2  13..15 variant bases of children a, b, c
 Offsets (fields 1-4) are in doubles inside a per-event workspace block:
   block = [k0 k1 k2 k3 | variant 0: 4 complex | variant 1 | ...]
 where k is the current's incoming momentum and variant v holds the current for
