@@ -143,32 +143,48 @@ def _ext_eps(k, lam, outgoing):
 
 # ---------------------------------------------------------------- workspace
 class Workspace:
-    """Flat float64 workspace [slot][event] with the compiler's offsets (complex = 2 slots)."""
+    """Flat float64 workspace [slot][event] with the compiler's offsets (complex = 2 slots).
+    With `log` set to a (reads, writes) pair of sets, every slot accessed is recorded."""
 
     def __init__(self, nslots, nevt):
         self.w = np.full((nslots, nevt), np.nan)
+        self.log = None
+
+    def _note(self, which, slots):
+        if self.log is not None:
+            self.log[which].update(np.ravel(slots).tolist())
 
     def k(self, off):
+        self._note(0, range(off, off + 4))
         return self.w[off:off + 4]
 
     def set_k(self, off, k):
+        self._note(1, range(off, off + 4))
         self.w[off:off + 4] = k
 
+    def set_r(self, off, x):
+        self._note(1, [off])
+        self.w[off] = x
+
     def cx(self, off):
+        self._note(0, [off, off + 1])
         return self.w[off] + 1j * self.w[off + 1]
 
     def set_cx(self, off, z):
+        self._note(1, [off, off + 1])
         self.w[off], self.w[off + 1] = z.real, z.imag
 
     def vec(self, base, idx):
         """Complex 4-vectors of variants idx (array) of the block whose variant 0 starts at base:
         [len(idx), 4, nevt]."""
         slots = base + 8 * np.asarray(idx)[:, None] + np.arange(8)[None, :]
+        self._note(0, slots)
         x = self.w[slots]
         return x[:, 0::2] + 1j * x[:, 1::2]
 
     def set_vec(self, base, idx, v):
         slots = base + 8 * np.asarray(idx)[:, None] + np.arange(8)[None, :]
+        self._note(1, slots)
         x = np.empty(slots.shape + v.shape[2:])
         x[:, 0::2], x[:, 1::2] = v.real, v.imag
         self.w[slots] = x
@@ -190,6 +206,19 @@ def _blocks(sl):
     return (s0, -s2, -s3, s1), (s1, s2, s3, s0)
 
 
+def _check_wave(logs):
+    """No item of a wave may touch a slot that another item of the wave writes."""
+    writer = {}
+    for it, (_, writes) in logs:
+        for s in writes:
+            if writer.setdefault(s, it) != it:
+                raise AssertionError(f"slot {s} written by items {writer[s]:#x} and {it:#x} of one wave")
+    for it, (reads, _) in logs:
+        for s in reads:
+            if writer.get(s, it) != it:
+                raise AssertionError(f"item {it:#x} reads slot {s} that item {writer[s]:#x} of its wave writes")
+
+
 def _select(w, r):
     """First index whose cumulative weight exceeds r x total (canonical order), else the last."""
     c = np.cumsum(w, axis=1)
@@ -208,11 +237,13 @@ class Emulator:
 
     def evaluate(self, mom, alpha_s, rnd_hel=None, rnd_col=None):
         """me [nevt], per-helicity |M_h|^2 [nevt, nhel] and colour weights [nevt, ncol] for momenta
-        [nevt, npar, 4] (every helicity, no filter), and the selections for the given uniforms."""
+        [nevt, npar, 4] (every helicity, no filter), and the selections for the given uniforms,
+        through the thread-per-event program (ops in order, one current's variants at a time)."""
         P = self.P
         nevt = mom.shape[0]
         pe = np.transpose(mom, (1, 2, 0))                     # [npar, 4, nevt]
         W = Workspace(P.ws_current_doubles, nevt)
+        self.terms, self.flows = P.terms, P.flows
         # jamps start as NaN unless a flow is never updated: every flow's first update must write
         jamps = np.zeros((self.nhel, P.ncol, nevt), complex) if P.jamp_zero else \
             np.full((self.nhel, P.ncol, nevt), np.nan + 0j)
@@ -222,6 +253,38 @@ class Emulator:
             else:
                 self._header(op, W, pe)
                 self._variants(op, W, pe)
+        return self._finish(jamps, alpha_s, rnd_hel, rnd_col)
+
+    def evaluate_cta(self, mom, alpha_s, rnd_hel=None, rnd_col=None):
+        """The same through the block-per-event schedule: waves of (op, header or variant) items
+        that a block's threads run in any order, amplitude steps into zeroed jamps.  Raises if an
+        item of a wave reads or writes a slot that another item of the same wave writes (a race)."""
+        T = self.P.cta
+        nevt = mom.shape[0]
+        pe = np.transpose(mom, (1, 2, 0))
+        W = Workspace(T["store"], nevt)
+        self.terms, self.flows = T["terms"], T["flows"]
+        jamps = np.zeros((self.nhel, self.P.ncol, nevt), complex)
+        for kind, start, count in T["steps"]:
+            if kind == 0:
+                logs = []
+                for it in T["items"][start:start + count]:
+                    op, v = T["ops"][it >> 8], it & 255
+                    W.log = (set(), set())
+                    if v == 255:
+                        self._header(op, W, pe)
+                    else:
+                        self._variants(op, W, pe, [v])
+                    logs.append((it, W.log))
+                W.log = None
+                _check_wave(logs)
+            else:
+                for a in range(start, start + count):
+                    self._amp(T["ops"][a], W, jamps, first_writes=False)
+        return self._finish(jamps, alpha_s, rnd_hel, rnd_col)
+
+    def _finish(self, jamps, alpha_s, rnd_hel, rnd_col):
+        P = self.P
         scale = (4 * math.pi * np.asarray(alpha_s)) ** P.gs_power
         mh = np.einsum("hie,ij,hje->eh", np.conj(jamps), self.C, jamps).real * scale[:, None]
         colw = (np.abs(jamps) ** 2).sum(axis=0).T * scale[:, None]
@@ -253,7 +316,7 @@ class Emulator:
             k = k + W.k(op[4])
             W.set_k(dst, k)
             sv = -1.0 / np.einsum("m,me->e", METRIC, k * k)    # (-i)(-i g_s^2)/P^2 with g_s = 1
-            W.w[dst + 4] = sv
+            W.set_r(dst + 4, sv)
             base = dst + 6
             for tab, (x, y) in enumerate(self._vvvv_pairs(op[11])):
                 nx, ny = nvar(op[6 + x]), nvar(op[6 + y])
@@ -270,11 +333,11 @@ class Emulator:
         if code == OP_VVV:
             ka, kb = W.k(op[2]), W.k(op[3])
             s = -1.0 / k2                                    # -i g_s/P^2 = i s with g_s = 1
-            W.w[dst + 6:dst + 10] = s * (ka - kb)
+            W.set_k(dst + 6, s * (ka - kb))
             q1 = s * (ka + 2 * kb)                           # s (k2 - k3)
             q2 = -s * (2 * ka + kb)                          # s (k3 - k1)
-            W.w[dst + 10:dst + 14] = q1
-            W.w[dst + 14:dst + 18] = q2
+            W.set_k(dst + 10, q1)
+            W.set_k(dst + 14, q2)
             n1, n2 = nvar(op[6]), nvar(op[7])
             e1, e2 = W.vec(op[13], np.arange(n1)), W.vec(op[14], np.arange(n2))
             a1 = np.einsum("m,me,vme->ve", METRIC, q1, e1)
@@ -302,11 +365,11 @@ class Emulator:
         return [((0, 2), (1, 2)), ((0, 1), (1, 2)), ((0, 1), (0, 2))][j]
 
     # -------------------------------------------------------------- variants
-    def _variants(self, op, W, pe):
+    def _variants(self, op, W, pe, vs=None):
+        """Variants vs (default: all) of one op."""
         code, dst, mdst = op[0], op[1], op[5]
-        nv = nvar(mdst)
-        v = np.arange(nv)
-        hb = [pdep(x, mdst) for x in range(nv)]
+        v = np.arange(nvar(mdst)) if vs is None else np.asarray(vs)
+        hb = [pdep(x, mdst) for x in v]
         child = lambda s: np.array([pext(h, op[6 + s]) for h in hb])
         if code == OP_EXT:
             p = pe[op[11]]
@@ -325,12 +388,12 @@ class Emulator:
                 else:
                     w = _ext_eps(p, lam, kind == EXT_EPS_OUT)
                 out.append(w)
-            W.set_vec(dst + 4, v, np.array(out))
+            W.set_vec(dst + 4, v, np.array(out)[v])
             return
         if code == OP_SUM:
             s = 0
             for t in range(op[12]):
-                e = self.P.terms[8 * (op[11] + t):8 * (op[11] + t + 1)]
+                e = self.terms[8 * (op[11] + t):8 * (op[11] + t + 1)]
                 s = s + PHASE[e[4]] * W.vec(e[0], v)
             W.set_vec(dst, v, s)
             return
@@ -396,7 +459,7 @@ class Emulator:
             i1, i2 = child(0), child(1)
             n1, n2 = nvar(op[6]), nvar(op[7])
             e1, e2 = W.vec(op[13], i1), W.vec(op[14], i2)
-            d = W.w[dst + 6:dst + 10]
+            d = W.k(dst + 6)
             a1 = np.array([W.cx(dst + 18 + 2 * i) for i in i1])
             a2 = np.array([W.cx(dst + 18 + 2 * (n1 + i)) for i in i2])
             s12 = _mdot(e1, e2)
@@ -418,20 +481,21 @@ class Emulator:
         raise ValueError(f"op code {code}")
 
     # -------------------------------------------------------------- amplitudes
-    def _amp(self, op, W, jamps):
+    def _amp(self, op, W, jamps, first_writes=True):
         """Group amplitude for every helicity: runs of terms sharing a bilinear X, the phased
-        other operands summed and closed with one product; then added to the group's flows."""
+        other operands summed and closed with one product; then added to the group's flows (a
+        flow's first update writes, in the thread-per-event program)."""
         h = np.arange(self.nhel)
         acc = 0
         s = None
         for t in range(op[12]):
-            e = self.P.terms[8 * (op[11] + t):8 * (op[11] + t + 1)]
+            e = self.terms[8 * (op[11] + t):8 * (op[11] + t + 1)]
             Y = W.vec(e[2], [pext(x, e[3]) for x in h])            # [nhel, 4, nevt]
             s = PHASE[e[4]] * Y if e[6] else s + PHASE[e[4]] * Y
             if e[7]:
                 X = W.vec(e[0], [pext(x, e[1]) for x in h])
                 acc = acc + (_mdot(X, s) if e[5] == 0 else (X * s).sum(axis=1))
         for f in range(op[10]):
-            flow, code = self.P.flows[2 * (op[9] + f):2 * (op[9] + f) + 2]
+            flow, code = self.flows[2 * (op[9] + f):2 * (op[9] + f) + 2]
             j = PHASE[code & 3] * acc
-            jamps[:, flow] = j if code & FLOW_FIRST else jamps[:, flow] + j
+            jamps[:, flow] = j if first_writes and code & FLOW_FIRST else jamps[:, flow] + j
