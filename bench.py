@@ -57,6 +57,9 @@ def _dist():
 
 
 # ------------------------------------------------------------------ CPU oracle timing
+ORACLE_CHUNK = 768      # events per oracle call (bounds its [terms, events, helicities] arrays)
+
+
 def _oracle_worker(args):
     wl_name, first, n = args
     sys.path.insert(0, ROOT)
@@ -67,7 +70,9 @@ def _oracle_worker(args):
     me = get(wl.process)
     me.evaluate(mom[:1], a[:1])          # warm caches / einsum paths outside the timing
     t0 = time.perf_counter()
-    me.evaluate(mom, a, rh, rc)
+    for c in range(0, n, ORACLE_CHUNK):
+        s = slice(c, c + ORACLE_CHUNK)
+        me.evaluate(mom[s], a[s], rh[s], rc[s])
     return time.perf_counter() - t0, n
 
 
@@ -372,7 +377,7 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cores = _host_cores()
-        per_core = 768
+        per_core = 8 * ORACLE_CHUNK        # about 10 s of oracle work per host process
         rate, n, busy, wall = cpu_oracle_rate(WORKLOAD, per_core, cores)
         cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} events of the same workload ({per_core} per spawn process), {busy:.1f} s busy"}
