@@ -123,7 +123,9 @@ int mgx_workspace_bytes(const mgx_process* proc, int64_t nevt, int mode, size_t*
  *           selcol [nevt] i32 (colour-flow index).
  * rnd_hel/rnd_col/selhel/selcol may all be NULL to skip selection.
  * workspace: device buffer of at least mgx_workspace_bytes(nevt, mode) bytes
- * (256-byte aligned); stream: a cudaStream_t (NULL = legacy default stream).
+ * (256-byte aligned; may be NULL when that is 0, as for the small batches that AUTO runs
+ * one block per event or with the workspace in shared memory); stream: a cudaStream_t
+ * (NULL = legacy default stream).
  * Asynchronous; errors: INVALID_ARGUMENT, DEVICE_MISMATCH, WORKSPACE_TOO_SMALL,
  * UNSUPPORTED_MODE, CUDA (launch failure). */
 int mgx_compute(mgx_process* proc, int64_t nevt, const double* momenta, const double* alpha_s,
@@ -204,9 +206,9 @@ int mgx_batch_replay(mgx_batch* batch, void* stream);
 int mgx_batch_autotune(mgx_batch* batch, const mgx_batch_io* io, int mode, void* workspace,
                        size_t workspace_bytes, void* stream, int* blocks_per_sm, int* events_per_item);
 /* Autotuner of a single process: times mgx_compute on these inputs for the thread-per-event
- * kernel at 2 and 4 blocks per SM and the CTA-per-event kernel (when usable), keeps the fastest
- * (me_scratch: DEVICE [nevt] output buffer).  Query mgx_workspace_bytes again afterwards.
- * Synchronous. */
+ * kernel at 2 and 4 blocks per SM, the CTA-per-event kernel and the shared-memory thread kernel
+ * (each when usable), keeps the fastest (me_scratch: DEVICE [nevt] output buffer).  Query
+ * mgx_workspace_bytes again afterwards.  Synchronous. */
 int mgx_process_autotune(mgx_process* proc, int64_t nevt, const double* momenta, const double* alpha_s, int mode,
                          void* workspace, size_t workspace_bytes, void* stream, int* kernel, int* blocks_per_sm,
                          double* me_scratch);
