@@ -284,6 +284,48 @@ def extra_eemumu(pkg, dev, stream):
             "algorithmic_bytes_per_launch": algo, "hbm_gbs_graph": algo / (graph_ms * 1e-3) / 1e9}
 
 
+def extra_phase_space(pkg, dev):
+    """Device random numbers and flat phase space for the g g > t t~ g g final state at
+    sqrt(s) = 1500 GeV: 2^26 Philox-4x32-10 uniforms (512 MiB, more than L2) and 2^22 RAMBO events
+    (massive Newton rescaling), in units/s and the HBM bandwidth their algorithmic bytes imply
+    (8 B per uniform out; 192 B of momenta and an 8 B weight per event out), beside the host
+    generator (numpy, one process) that makes the bench's inputs."""
+    import torch
+    from phasespace import WORKLOADS
+    from phasespace.rambo import rambo as host_rambo
+    wl = WORKLOADS["ggttgg"]
+    n = 1 << 22
+    masses = wl.final_masses()
+    L = pkg.lib()
+    m = torch.tensor(masses, dtype=torch.float64, device=dev)
+    mom = torch.empty((n, len(masses) + 2, 4), dtype=torch.float64, device=dev)
+    wt = torch.empty(n, dtype=torch.float64, device=dev)
+    nu = 1 << 26
+    u = torch.empty(nu, dtype=torch.float64, device=dev)
+    side = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        st = pkg._stream(dev)
+
+        def uni():
+            pkg._check(L.mgx_uniforms(nu, 0, 7, 1, pkg._ptr(u), st), "mgx_uniforms")
+
+        def ram():
+            pkg._check(L.mgx_rambo(n, 0, wl.sqrts, len(masses), pkg._ptr(m), 7, pkg._ptr(mom), pkg._ptr(wt), st),
+                       "mgx_rambo")
+        uni_ms = _timed(uni, 20, 3, side)
+        ram_ms = _timed(ram, 10, 3, side)
+    nh = 1 << 16
+    t0 = time.perf_counter()
+    host_rambo(nh, wl.sqrts, masses, 7)
+    host_s = time.perf_counter() - t0
+    rbytes = n * ((len(masses) + 2) * 32 + 8)
+    return {"nevt": n, "final_masses": masses,
+            "uniforms_per_s": nu / (uni_ms * 1e-3), "uniforms_hbm_gbs": 8 * nu / (uni_ms * 1e-3) / 1e9,
+            "rambo_events_per_s": n / (ram_ms * 1e-3), "rambo_hbm_gbs": rbytes / (ram_ms * 1e-3) / 1e9,
+            "rambo_ms": ram_ms, "host_rambo_events_per_s": nh / host_s, "host_sample": f"{nh} events, one process"}
+
+
 def extra_batched(pkg, dev, stream):
     """g g > t t~ (2^22), t t~ g (2^20), t t~ g g (2^18), g u~ > ta+ ta- g g u~ (2^16): one
     autotuned persistent launch captured in a CUDA graph vs one launch per process."""
@@ -478,7 +520,8 @@ def run_gpu(args):
                             ("ggttggg", lambda: extra_ggttggg(pkg, dev, stream)),
                             ("eemumu", lambda: extra_eemumu(pkg, dev, stream)),
                             ("batched", lambda: extra_batched(pkg, dev, stream)),
-                            ("surrogate_unweighting", lambda: extra_surrogate(pkg, dev))):
+                            ("surrogate_unweighting", lambda: extra_surrogate(pkg, dev)),
+                            ("phase_space", lambda: extra_phase_space(pkg, dev))):
                 t0 = time.perf_counter()
                 try:
                     extras[key] = fn()
