@@ -15,6 +15,7 @@ a read before the write also shows).  It shares no code with the oracle; physics
 restated here from their definitions.
 """
 import math
+from collections import Counter
 
 import numpy as np
 
@@ -28,6 +29,8 @@ PARAMS = {"": 0.0, "mt": 173.0, "wt": 1.4915, "mz": 91.1876, "wz": 2.4414, "mta"
 ALPHA_EM, G_F = 1.0 / 132.507, 1.16639e-5
 METRIC = np.array([1.0, -1.0, -1.0, -1.0])
 PHASE = np.array([1.0, 1j, -1.0, -1j])
+NAME = {OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv", OP_VVVV: "vvvv", OP_BIL: "bil",
+        OP_RBIL: "rbil"}
 
 
 def pext(x, mask):
@@ -244,6 +247,7 @@ class Emulator:
         pe = np.transpose(mom, (1, 2, 0))                     # [npar, 4, nevt]
         W = Workspace(P.ws_current_doubles, nevt)
         self.terms, self.flows = P.terms, P.flows
+        self.count = Counter()      # work executed per event, in the compiler's count names
         # jamps start as NaN unless a flow is never updated: every flow's first update must write
         jamps = np.zeros((self.nhel, P.ncol, nevt), complex) if P.jamp_zero else \
             np.full((self.nhel, P.ncol, nevt), np.nan + 0j)
@@ -264,6 +268,7 @@ class Emulator:
         pe = np.transpose(mom, (1, 2, 0))
         W = Workspace(T["store"], nevt)
         self.terms, self.flows = T["terms"], T["flows"]
+        self.count = Counter()
         jamps = np.zeros((self.nhel, self.P.ncol, nevt), complex)
         for kind, start, count in T["steps"]:
             if kind == 0:
@@ -310,6 +315,7 @@ class Emulator:
             if code == OP_RBIL:
                 nv = nvar(op[7])
                 W.set_vec(dst + 6, np.arange(nv), _slash(W.vec(op[14], np.arange(nv))))
+                self.count["slash_hdr"] += nv
             return
         k = W.k(op[2]) + W.k(op[3])
         if code == OP_VVVV:
@@ -327,6 +333,7 @@ class Emulator:
                     for ix in range(nx):
                         W.set_cx(base + 2 * (ix + nx * iy), d[ix, iy])
                 base += 2 * nx * ny
+                self.count["vvvv_hdr"] += nx * ny
             return
         W.set_k(dst, k)
         k2 = np.einsum("m,me->e", METRIC, k * k)
@@ -346,6 +353,7 @@ class Emulator:
                 W.set_cx(dst + 18 + 2 * v, a1[v])
             for v in range(n2):
                 W.set_cx(dst + 18 + 2 * (n1 + v), a2[v])
+            self.count["vvv_hdr"] += n1 + n2
             return
         m, w = self.mass[op[10]]
         inv = 1.0 / (k2 - m * m + 1j * m * w)
@@ -358,6 +366,8 @@ class Emulator:
         else:
             nv = nvar(op[7])
             W.set_vec(dst + 6, np.arange(nv), pref * _slash(W.vec(op[14], np.arange(nv))))
+            self.count["slash_hdr"] += nv
+            self.count["slash_pref_hdr"] += nv
 
     @staticmethod
     def _vvvv_pairs(j):
@@ -370,6 +380,10 @@ class Emulator:
         code, dst, mdst = op[0], op[1], op[5]
         v = np.arange(nvar(mdst)) if vs is None else np.asarray(vs)
         hb = [pdep(x, mdst) for x in v]
+        if code in NAME:
+            self.count["var_" + NAME[code]] += len(v)
+        elif code == OP_SUM:
+            self.count["sum_adds"] += (op[12] - 1) * len(v)
         child = lambda s: np.array([pext(h, op[6 + s]) for h in hb])
         if code == OP_EXT:
             p = pe[op[11]]
@@ -488,8 +502,10 @@ class Emulator:
         h = np.arange(self.nhel)
         acc = 0
         s = None
+        self.count.update(amp=1, amp_terms=op[12], amp_flows=op[10])
         for t in range(op[12]):
             e = self.terms[8 * (op[11] + t):8 * (op[11] + t + 1)]
+            self.count["amp_runs"] += e[7]
             Y = W.vec(e[2], [pext(x, e[3]) for x in h])            # [nhel, 4, nevt]
             s = PHASE[e[4]] * Y if e[6] else s + PHASE[e[4]] * Y
             if e[7]:

@@ -44,3 +44,19 @@ def test_block_schedule_matches_oracle_without_races(name, nevt):
     wl = WORKLOADS[name]
     mom, a, rh, rc = make_inputs(wl, nevt)
     _check(wl, mom, a, rh, rc, Emulator(wl.process).evaluate_cta(mom, a, rh, rc))
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_work_counts_match_execution(name):
+    """The compiler's work counts per event (variants per vertex kind, sum-current additions,
+    header tables, amplitude groups, terms, runs and flow updates), which the library's float64
+    work model multiplies by per-op instruction counts for the roofline, equal what one run of
+    the tables executes."""
+    wl = WORKLOADS[name]
+    mom, a, _, _ = make_inputs(wl, 1)
+    E = Emulator(wl.process)
+    E.evaluate(mom, a)
+    c = E.P.flop_counts
+    for k in ("var_ffv_f", "var_ffv_fb", "var_ffv_v", "var_vvv", "var_vvvv", "var_bil", "var_rbil", "sum_adds",
+              "vvv_hdr", "vvvv_hdr", "slash_hdr", "slash_pref_hdr", "amp", "amp_terms", "amp_runs", "amp_flows"):
+        assert E.count[k] == c[k], (k, E.count[k], c[k])
