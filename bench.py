@@ -76,15 +76,27 @@ def _oracle_worker(args):
     return time.perf_counter() - t0, n
 
 
+_ONE_THREAD = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
 def cpu_oracle_rate(wl_name, per_core, cores):
-    """Events/s of the float64 oracle on `cores` host processes, per_core events each."""
+    """Events/s of the float64 oracle on `cores` single-threaded host processes, per_core events each."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     jobs = [(wl_name, 1000 + i * per_core, per_core) for i in range(cores)]
-    t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, jobs)
-    wall = time.perf_counter() - t0
+    saved = {k: os.environ.get(k) for k in _ONE_THREAD}
+    os.environ.update({k: "1" for k in _ONE_THREAD})     # spawned workers inherit it before numpy loads
+    try:
+        t0 = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     busy = max(t for t, _ in res)
     n = sum(k for _, k in res)
     return n / busy, n, busy, wall
@@ -363,7 +375,10 @@ def extra_batched(pkg, dev, stream):
 
 
 def extra_surrogate(pkg, dev):
-    """g g > t t~ g g with cuts: surrogate training, then unweighted events/s plain vs two-stage."""
+    """g g > t t~ g g with cuts: surrogate training, then unweighted events/s plain vs two-stage.
+    The two-stage leg takes stage-1 batches of 2^25 events so that the exact |M|^2 of the survivors
+    (about 2^18 per batch) runs at a size that fills the GPU; its time is split by phase (CUDA
+    events on the stream) and summed over the batches."""
     import torch
     from paper_2503_21935_gb300.surrogate import Unweighter
     U = Unweighter("g g > t t~ g g", 1500.0, [173.0, 173.0, 0.0, 0.0], cut_particles=[4, 5], device=dev.index,
@@ -376,25 +391,34 @@ def extra_surrogate(pkg, dev):
     res = {"training": {"events": 1 << 22, "steps": 4000, "batch": 8192, "seconds": train_s,
                         "loss_first": hist[0][1], "loss_last": hist[-1][1]}}
     # the two-stage leg runs until 10^6 unweighted events; the plain leg (about 8x slower per
-    # unweighted event) is timed over a fixed 4 batches, its rate being what is compared
-    for name, fn, target, nbatch in (("plain", U.plain, None, 4), ("surrogate", U.two_stage, 1000000, None)):
-        fn(1 << 20, seed=900)                      # warm-up
+    # unweighted event) is timed over a fixed 4 batches of 2^22, its rate being what is compared
+    legs = (("plain", lambda b, prof: U.plain(1 << 22, seed=901, first=b << 22), None, 4),
+            ("surrogate", lambda b, prof: U.two_stage(1 << 25, seed=901, first=b << 25, profile=prof), 1000000, None))
+    for name, fn, target, nbatch in legs:
+        fn(1 << 10, False)                         # warm-up (batch index far from the timed ones)
         torch.cuda.synchronize()
         n_unw = gen = calls = over = 0
         b = 0
+        phases = {}
         t0 = time.perf_counter()
         while (target is not None and n_unw < target) or (nbatch is not None and b < nbatch):
-            r = fn(1 << 22, seed=901 + b)
+            r = fn(b, name == "surrogate")
             n_unw += int(r["weight"].shape[0])
             gen += r["generated"]
             calls += r["exact_calls"]
             over += int((r["weight"] > 1).sum().item())
+            if name == "surrogate" and U.timing:
+                for k, v in U.timing.items():
+                    phases[k] = phases.get(k, 0.0) + v
             b += 1
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         res[name] = {"value": n_unw / dt, "unit": "unweighted events/s", "generated": gen,
                      "unweighted": n_unw, "exact_me_calls": calls, "seconds": dt, "batches": b,
                      "overweight_fraction": over / n_unw if n_unw else None}
+        if phases:
+            res[name]["phase_ms"] = phases
+            res[name]["phase_ms_sum"] = sum(phases.values())
     res["gain"] = res["surrogate"]["value"] / res["plain"]["value"] if res["plain"]["value"] else None
     return res
 
@@ -421,8 +445,12 @@ def run_gpu(args):
         cores = _host_cores()
         per_core = 8 * ORACLE_CHUNK        # about 10 s of oracle work per host process
         rate, n, busy, wall = cpu_oracle_rate(WORKLOAD, per_core, cores)
+        r1, n1, busy1, _ = cpu_oracle_rate(WORKLOAD, per_core, 1)
         cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
-               "sample": f"{n} events of the same workload ({per_core} per spawn process), {busy:.1f} s busy"}
+               "sample": f"{n} events of the same workload ({per_core} per single-threaded spawn process), "
+                         f"{busy:.1f} s busy",
+               "single_thread": {"value": r1, "unit": "events/s", "cores": 1,
+                                 "sample": f"{n1} events in one single-threaded process, {busy1:.1f} s"}}
 
     from paper_2503_21935_gb300.dist import event_range, max_over_ranks
     wl = WORKLOADS[WORKLOAD]

@@ -89,7 +89,10 @@ void mgx_params_default(mgx_params* p);
 int mgx_num_processes(void);
 const char* mgx_process_name(int i);
 
-/* Create a process on CUDA device `device`: resolves the couplings and masses,
+/* Create a process on CUDA device `device`: the set-up half of the multi-event ME interface of
+ * Sec. 2 (a process with its couplings and masses is prepared once, then evaluated for many event
+ * batches; the paper does not describe the helicity filter, which drops the helicities whose
+ * |M_h|^2 vanishes identically so that no batch evaluates them).  Resolves the couplings and masses,
  * uploads the process's op table and colour matrix, and runs the helicity
  * filter: all 2^npar helicities are evaluated on 16 flat phase-space events
  * (Philox-4x32-10 keyed by filter_seed, RAMBO at params->filter_sqrt_s) and
@@ -117,7 +120,10 @@ int mgx_colour_matrix(const mgx_process* proc, double* out);
 /* Device workspace (bytes) that mgx_compute needs for nevt events in `mode`. */
 int mgx_workspace_bytes(const mgx_process* proc, int64_t nevt, int mode, size_t* bytes);
 
-/* Compute a batch.  All arrays are DEVICE pointers on the process's device:
+/* Compute a batch: the reentrant, stateless multi-event ME call of Sec. 2 (well-defined input and
+ * output buffers for a whole batch of events), evaluating per event the Feynman diagrams, the
+ * colour-matrix quadratic form J^dagger C J and the helicity sum of Sec. 3, plus the helicity and
+ * colour selection that the event record needs.  All arrays are DEVICE pointers on the process's device:
  *   momenta [nevt][npar][4] f64, alpha_s [nevt] f64, rnd_hel/rnd_col [nevt] f64 in [0,1)
  *   outputs me [nevt] f64, selhel [nevt] i32 (canonical helicity index),
  *           selcol [nevt] i32 (colour-flow index).
@@ -232,7 +238,11 @@ int mgx_kernel_launches(const mgx_process* proc, int64_t nevt, int mode);
  * Arguments are those of mgx_compute without the workspace (DEVICE pointers; the caller still
  * passes every input and output).  The thread-per-event kernel's workspace lives in one fixed
  * module-scope device array of mgx_noalloc_scratch_bytes() = 128 MiB, which every GPU that
- * loads the library holds until the process exits; the grid is sized so the workspace fits.
+ * loads the library holds until the process exits; the grid is sized so the workspace fits, i.e.
+ * floor(128 MiB / (128 x per-event workspace)) blocks of 128 threads, at most the usual persistent
+ * grid: g g > t t~ g g gets 16 blocks (2048 events in flight instead of 77824), g g > t t~ g g g
+ * a single block (128 events in flight), so their throughput through this entry point is
+ * about 1/38 and 1/600 of mgx_compute's on a full batch; the small processes get the full grid.
  * The call itself allocates nothing (no cudaMalloc/cudaFree, no allocating library call); the
  * process handle must have been created beforehand.  Set-up: the first call on a device looks
  * up the array's device address with that device current, so make that first call before any
@@ -291,6 +301,11 @@ int mgx_mlp_gradients(mgx_mlp* net, int n, const float* x, const float* t, float
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on one batch. */
 int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, float lr, float* loss, void* ws,
                        size_t wsb, void* stream);
+/* One Adam step on a gradient the caller supplies (DEVICE, num_params floats): the update half of a
+ * data-parallel training step, after the per-replica gradients of mgx_mlp_gradients have been
+ * averaged across replicas (weighted by their batch sizes).  Replicas that start from the same
+ * parameters and apply the same averaged gradient stay identical.  Asynchronous on stream. */
+int mgx_mlp_adam_step(mgx_mlp* net, const float* grad, float lr, void* stream);
 
 /* ---- unweighting (plain hit-or-miss and two-stage with the surrogate) ----
  * Plain: keep with probability min(1, w/w_max), weight max(1, w/w_max).  Two-stage

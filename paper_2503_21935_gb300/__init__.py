@@ -93,6 +93,9 @@ def lib():
             "mgx_mlp_forward": (I, [P, I64, P, P, P, SZ, P]),
             "mgx_mlp_gradients": (I, [P, I, P, P, P, P, P, SZ, P]),
             "mgx_mlp_train_step": (I, [P, I, P, P, ctypes.c_float, P, P, SZ, P]),
+            "mgx_mlp_adam_step": (I, [P, P, ctypes.c_float, P]),
+            "mgx_noalloc_scratch_bytes": (SZ, []),
+            "mgx_compute_noalloc": (I, [P, I64, P, P, P, P, P, P, P, I, P]),
             "mgx_status_string": (ctypes.c_char_p, [I]),
             "mgx_version": (I, []),
         }
@@ -104,9 +107,14 @@ def lib():
     return _lib
 
 
+def status_string(rc):
+    """The library's message for a status code."""
+    return lib().mgx_status_string(rc).decode()
+
+
 def _check(rc, what):
     if rc != MGX_OK:
-        raise MgxError(f"{what}: {lib().mgx_status_string(rc).decode()} ({rc})")
+        raise MgxError(f"{what}: {status_string(rc)} ({rc})")
 
 
 def default_params():
@@ -294,6 +302,22 @@ class Mlp:
         _check(lib().mgx_mlp_gradients(self._h, n, _ptr(xd), _ptr(td), _ptr(g), _ptr(loss), _ptr(ws), ws.numel(),
                                        _stream(xd.device)), "mgx_mlp_gradients")
         return float(loss.item()), g.cpu().numpy()
+
+    def device_gradients(self, x, t, loss_out=None):
+        """Gradient of the mean squared error on one batch as a device float32 tensor (no host copy)."""
+        import torch
+        xd, td = self._dev(x, torch.float32), self._dev(t, torch.float32)
+        n = xd.shape[0]
+        g = torch.empty(self.nparams, dtype=torch.float32, device=xd.device)
+        ws = self._workspace(n, True)
+        _check(lib().mgx_mlp_gradients(self._h, n, _ptr(xd), _ptr(td), _ptr(g), _ptr(loss_out), _ptr(ws), ws.numel(),
+                                       _stream(xd.device)), "mgx_mlp_gradients")
+        return g
+
+    def adam_step(self, grad, lr=1e-3):
+        """One Adam step on a device gradient (e.g. the replicas' average in data-parallel training)."""
+        _check(lib().mgx_mlp_adam_step(self._h, _ptr(grad), ctypes.c_float(lr), _stream(grad.device)),
+               "mgx_mlp_adam_step")
 
     def train_step(self, x, t, lr=1e-3, loss_out=None):
         import torch

@@ -547,18 +547,29 @@ int mgx_mlp_gradients(mgx_mlp* net, int n, const float* x, const float* t, float
   return MGX_OK;
 }
 
-int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, float lr, float* loss, void* ws, size_t wsb,
-                       void* stream) {
-  int rc = mgx_mlp_gradients(net, n, x, t, nullptr, loss, ws, wsb, stream);
-  if (rc != MGX_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+namespace {
+// one Adam step on gradient g (DEVICE, num_params floats), then the bf16 copies
+int adam_step(mgx_mlp* net, const float* g, float lr, cudaStream_t st) {
   net->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float bc1 = 1.0f - std::pow(b1, (float)net->step), bc2 = 1.0f - std::pow(b2, (float)net->step);
-  adam_kernel<<<(net->L.total + 255) / 256, 256, 0, st>>>(net->L.total, net->p, net->g, net->m, net->v, lr, b1, b2,
-                                                          1e-8f, bc1, bc2);
-  rc = refresh(net, st);
-  return rc;
+  adam_kernel<<<(net->L.total + 255) / 256, 256, 0, st>>>(net->L.total, net->p, g, net->m, net->v, lr, b1, b2, 1e-8f,
+                                                          bc1, bc2);
+  if (cudaGetLastError() != cudaSuccess) return MGX_ERR_CUDA;
+  return refresh(net, st);
+}
+}  // namespace
+
+int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, float lr, float* loss, void* ws, size_t wsb,
+                       void* stream) {
+  const int rc = mgx_mlp_gradients(net, n, x, t, nullptr, loss, ws, wsb, stream);
+  if (rc != MGX_OK) return rc;
+  return adam_step(net, net->g, lr, (cudaStream_t)stream);
+}
+
+int mgx_mlp_adam_step(mgx_mlp* net, const float* grad, float lr, void* stream) {
+  if (!net || !grad) return MGX_ERR_INVALID_ARGUMENT;
+  return adam_step(net, grad, lr, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -3,21 +3,25 @@
 A small MLP learns log|M|^2 over phase space from events the exact path evaluates; it then
 drives stage 1 of a two-stage unweighting whose stage 2 corrects every surviving event with
 its exact |M|^2 (Danziger, Janssen, Schumann, Siegert, arXiv:2109.11964), so the unweighted
-sample stays unbiased and the exact |M|^2 has the last word.  Every arithmetic step runs in the
-library's kernels (phase space, cuts, matrix elements, network, weights, accept/reject,
-compaction); this module sequences the calls and holds device buffers (PyTorch tensors).
+sample stays unbiased and the exact |M|^2 has the last word.  Every arithmetic step of the
+method runs in the library's kernels (phase space, cuts, matrix elements, network, weights,
+accept/reject, compaction); this module sequences the calls and holds device buffers (PyTorch
+tensors).
+
+Data parallelism (one replica per GPU, `dist`): each rank generates and unweights its own
+contiguous range of events.  Every random number of the accept/reject steps is keyed by the
+event's global index, and the maxima come from the weights of all ranks' calibration events,
+so the union of the ranks' unweighted events is exactly the sample one rank would draw from
+all the events.  Training is data-parallel too: each rank's gradient comes from its own
+training events, the ranks average the gradients (one all-reduce per step) and apply the same
+Adam step.
 """
 import ctypes
-import time
 
 import numpy as np
 
 from . import (Mlp, MgxError, Process, _check, _ptr, _stream, lib, rambo, cuts, uniforms, MGX_FP64)
-
-
-def _dev_empty(n, dtype, device):
-    import torch
-    return torch.empty(n, dtype=dtype, device=device)
+from . import dist as _dist
 
 
 class Unweighter:
@@ -41,10 +45,11 @@ class Unweighter:
         self.mean = 0.0
         self.sd = 1.0
         self.exact_calls = 0
+        self.timing = None          # per-phase CUDA-event times of the last profiled call
 
     # ------------------------------------------------------------------ events
     def events(self, n, seed, first=0):
-        """Device momenta, phase-space weights and cut mask of n events."""
+        """Device momenta, phase-space weights and cut mask of events first .. first+n-1."""
         mom, wps = rambo(n, self.sqrts, self.masses, seed, first=first, device=self.dev.index)
         lst, ptmin, etamax, drmin = self.cut
         if lst:
@@ -91,10 +96,9 @@ class Unweighter:
         _check(lib().mgx_gather(m, _ptr(idx), row, _ptr(src), _ptr(dst), _stream(self.dev)), "mgx_gather")
         return dst
 
-    def _accept(self, w, wref, wmax, seed, stream_id):
+    def _accept(self, w, wref, wmax, r):
         import torch
         n = w.shape[0]
-        r = uniforms(n, seed, stream_id, device=self.dev.index)
         keep = torch.empty(n, dtype=torch.uint8, device=self.dev)
         over = torch.empty(n, dtype=torch.float64, device=self.dev)
         _check(lib().mgx_accept(n, _ptr(w), _ptr(wref), float(wmax), _ptr(r), _ptr(keep), _ptr(over),
@@ -120,68 +124,129 @@ class Unweighter:
 
     # ------------------------------------------------------------------ training
     def train(self, ntrain, steps, batch=4096, lr=1e-3, seed=101, lr_decay=0.1):
-        """Generate ntrain events, evaluate them exactly, fit log|M|^2 of those passing the cuts."""
+        """Generate ntrain events (per rank), evaluate them exactly, fit log|M|^2 of those passing
+        the cuts.  With several ranks: each rank trains on its own events and the ranks average
+        their gradients every step (data-parallel replicas, identical parameters throughout)."""
         import torch
-        mom, wps, ok = self.events(ntrain, seed)
+        rank, world = _dist.rank_world()
+        mom, wps, ok = self.events(ntrain, seed, first=rank * ntrain)
         me = self.exact_me(mom)
         keep = ok.bool() & (me > 0)
         x = self.features(mom)[keep].contiguous()
         y = torch.log(me[keep])
-        self.mean = float(y.mean().item())
-        self.sd = float(y.std().item())
+        # standardisation from the moments of all ranks' targets (rank-order sums)
+        s1, s2, cnt = _dist.allreduce_sums([float(y.sum().item()), float((y * y).sum().item()), int(y.numel())],
+                                           device=self.dev)
+        self.mean = s1 / cnt
+        self.sd = float(np.sqrt(max(s2 / cnt - self.mean ** 2, 0.0) * cnt / max(cnt - 1, 1)))
         t = ((y - self.mean) / self.sd).to(torch.float32).contiguous()
         n = x.shape[0]
         g = torch.Generator(device=self.dev)
-        g.manual_seed(seed)
+        g.manual_seed(seed + 7 * rank)
         hist = []
         loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
         for step in range(steps):
             idx = torch.randint(0, n, (batch,), device=self.dev, generator=g)
             frac = step / max(1, steps - 1)
             rate = lr * (lr_decay ** frac)
-            self.net.train_step(x[idx].contiguous(), t[idx].contiguous(), lr=rate, loss_out=loss)
+            if world == 1:
+                self.net.train_step(x[idx].contiguous(), t[idx].contiguous(), lr=rate, loss_out=loss)
+            else:
+                grad = self.net.device_gradients(x[idx].contiguous(), t[idx].contiguous(), loss_out=loss)
+                _dist.allreduce_gradients(grad, batch)
+                self.net.adam_step(grad, lr=rate)
             if step % max(1, steps // 20) == 0 or step == steps - 1:
                 hist.append((step, float(loss.item())))
         return hist
 
     # ------------------------------------------------------------------ calibration
-    def calibrate(self, n, seed=202, q=0.999):
-        """Reference maxima (high quantiles): w_max (plain), s_max and r_max (two-stage)."""
-        mom, wps, ok = self.events(n, seed)
+    def calibration_sample(self, n, seed, first=0):
+        """Exact and surrogate weights (w, s) of events first .. first+n-1."""
+        mom, wps, ok = self.events(n, seed, first)
         w = self._weights(self.exact_me(mom), wps, ok)
         s = self.surrogate_weights(mom, wps, ok)
+        return w, s
+
+    def set_maxima(self, w, s, q=0.999):
+        """Reference maxima from calibration weights: w_max (plain), s_max and r_max (two-stage), the
+        q-quantiles of w, s and w/s over the events with w > 0 and s > 0 (q = 1: the maxima)."""
         sel = (w > 0) & (s > 0)
-        self.w_max = float(w[sel].quantile(q).item()) if sel.sum() < 2 ** 24 else float(w[sel].max().item())
-        self.s_max = float(s[sel].quantile(q).item())
-        self.r_max = float((w[sel] / s[sel]).quantile(q).item())
+        ws, ss = w[sel], s[sel]
+
+        def quant(v):
+            if q >= 1.0:
+                return float(v.max().item())
+            if v.numel() <= 1 << 24:
+                return float(v.quantile(q).item())
+            k = max(0, int(np.ceil(q * v.numel())) - 1)
+            return float(v.kthvalue(k + 1).values.item())
+        self.w_max, self.s_max, self.r_max = quant(ws), quant(ss), quant(ws / ss)
         return self.w_max, self.s_max, self.r_max
 
+    def calibrate(self, n, seed=202, q=0.999):
+        """Reference maxima from n calibration events per rank; with several ranks the quantiles are
+        taken over the weights of all ranks' events (one gather), the same on every rank."""
+        rank, world = _dist.rank_world()
+        w, s = self.calibration_sample(n, seed, first=rank * n)
+        if world > 1:
+            w, s = _dist.gather_samples(w), _dist.gather_samples(s)
+        return self.set_maxima(w, s, q)
+
     # ------------------------------------------------------------------ unweighting
+    def _stats(self, w):
+        """Global (max w, sum w, N) of a batch: one collective across ranks."""
+        mx = float(w.max().item()) if w.numel() else 0.0
+        return _dist.allreduce_weight_stats(mx, float(w.sum().item()), int(w.numel()), device=self.dev)
+
     def plain(self, n, seed, first=0):
-        """Hit-or-miss on the exact weight of every event."""
-        import torch
+        """Hit-or-miss on the exact weight of events first .. first+n-1."""
         mom, wps, ok = self.events(n, seed, first)
         calls = self.exact_calls
         w = self._weights(self.exact_me(mom), wps, ok)
-        keep, over = self._accept(w, None, self.w_max, seed, 11)
+        keep, over = self._accept(w, None, self.w_max, uniforms(n, seed, 11, first=first, device=self.dev.index))
         idx = self._compact(keep)
-        return dict(momenta=self._gather(idx, mom), weight=over[idx.long()], exact_calls=self.exact_calls - calls,
-                    generated=n, all_weights=w, all_momenta=mom)
+        mx, sw, nn = self._stats(w)
+        return dict(momenta=self._gather(idx, mom), weight=over[idx.long()], index=first + idx.long(),
+                    exact_calls=self.exact_calls - calls, generated=n, all_weights=w, all_momenta=mom,
+                    max_w=mx, sum_w=sw, n_events=nn)
 
-    def two_stage(self, n, seed, first=0):
-        """Stage 1 on the surrogate weight, stage 2 on exact / surrogate for the survivors only."""
+    def two_stage(self, n, seed, first=0, profile=False):
+        """Stage 1 on the surrogate weight, stage 2 on exact / surrogate for the survivors only, for
+        events first .. first+n-1.  Both stages draw their random numbers by global event index.
+        profile=True records the time of each phase with CUDA events into self.timing (ms)."""
         import torch
+        stream = torch.cuda.current_stream(self.dev)
+        marks = []
+
+        def mark(name):
+            if profile:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                marks.append((name, e))
+        mark("start")
         mom, wps, ok = self.events(n, seed, first)
+        mark("phase space and cuts")
         s = self.surrogate_weights(mom, wps, ok)
-        keep1, over1 = self._accept(s, None, self.s_max, seed, 12)
+        mark("features, network, surrogate weights")
+        keep1, over1 = self._accept(s, None, self.s_max, uniforms(n, seed, 12, first=first, device=self.dev.index))
         idx1 = self._compact(keep1)
         m1 = self._gather(idx1, mom)
+        wps1 = self._gather(idx1, wps)
+        s1 = self._gather(idx1, s)
+        r2 = self._gather(idx1, uniforms(n, seed + 7919, 13, first=first, device=self.dev.index))
+        mark("stage-1 accept, compaction, gathers")
         calls = self.exact_calls
         me1 = self.exact_me(m1)
-        w1 = self._weights(me1, self._gather(idx1, wps), None)
-        s1 = self._gather(idx1, s)
-        keep2, over2 = self._accept(w1, s1, self.r_max, seed + 7919, 13)
+        mark("exact |M|^2 of the survivors")
+        w1 = self._weights(me1, wps1, None)
+        keep2, over2 = self._accept(w1, s1, self.r_max, r2)
         idx2 = self._compact(keep2)
-        weight = over1[idx1.long()][idx2.long()] * over2[idx2.long()]
-        return dict(momenta=self._gather(idx2, m1), weight=weight, exact_calls=self.exact_calls - calls,
-                    generated=n, stage1=int(idx1.shape[0]))
+        l2 = idx2.long()
+        weight = over1[idx1.long()][l2] * over2[l2]
+        out = dict(momenta=self._gather(idx2, m1), weight=weight, index=first + idx1.long()[l2],
+                   exact_calls=self.exact_calls - calls, generated=n, stage1=int(idx1.shape[0]))
+        mark("stage-2 accept and compaction")
+        if profile:
+            torch.cuda.synchronize(self.dev)
+            self.timing = {name: marks[k - 1][1].elapsed_time(e) for k, (name, e) in enumerate(marks) if k > 0}
+        return out

@@ -42,11 +42,14 @@ WORKLOADS = {
 }
 
 
-def make_inputs(wl, nevt=None, first=0):
+def make_inputs(wl, nevt=None, first=0, alpha_s_range=None):
     """Momenta [nevt, npar, 4], alpha_s [nevt], r_hel [nevt], r_col [nevt] (float64, host).
 
     Events first..first+nevt-1 of the workload's seeded stream.  Random numbers
-    are counter-based, so any sub-range reproduces the same events.
+    are counter-based, so any sub-range reproduces the same events.  alpha_s is
+    the workload's constant unless alpha_s_range = (lo, hi) is given: then each
+    event draws its own value uniformly in [lo, hi) (Philox stream 3 of the
+    workload's random seed), as a run with a dynamical scale would pass.
     """
     n = wl.nevt if nevt is None else nevt
     masses = wl.final_masses()
@@ -54,7 +57,11 @@ def make_inputs(wl, nevt=None, first=0):
     pout, _ = rambo(tot, wl.sqrts, masses, wl.seed_momenta)
     pin = incoming_beams(tot, wl.sqrts)
     mom = np.concatenate([pin, pout], axis=1)[first:]
-    alphas = np.full(n, wl.alpha_s)
+    if alpha_s_range is None:
+        alphas = np.full(n, wl.alpha_s)
+    else:
+        lo, hi = alpha_s_range
+        alphas = lo + (hi - lo) * uniform01(wl.seed_random, 3, tot)[first:]
     rhel = uniform01(wl.seed_random, 1, tot)[first:]
     rcol = uniform01(wl.seed_random, 2, tot)[first:]
     return np.ascontiguousarray(mom), alphas, rhel, rcol

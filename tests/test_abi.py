@@ -24,8 +24,17 @@ def test_exports_every_declared_symbol(libpath):
     L = ctypes.CDLL(libpath)
     names = _declared()
     assert "mgx_compute" in names and "mgx_process_create" in names
+    assert "mgx_compute_noalloc" in names and "mgx_noalloc_scratch_bytes" in names
     for n in names:
         assert hasattr(L, n), n
+
+
+def test_binding_covers_every_declared_symbol(libpath):
+    """The Python binding sets a signature for every entry point the header declares."""
+    import paper_2503_21935_gb300 as pkg
+    L = pkg.lib()
+    for n in _declared():
+        assert getattr(L, n).argtypes is not None or getattr(L, n).restype is not ctypes.c_int, n
 
 
 def test_host_only_calls(libpath):

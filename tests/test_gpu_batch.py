@@ -1,9 +1,12 @@
-"""Batched multi-process launch, CUDA-graph replay and autotuning: results identical to the
+"""Batched multi-process launch, CUDA-graph replay and autotuning: results against the float64
+oracle (float64 and mixed float32 colour sum, per-event alpha_s), and identical to the
 per-process entry point."""
 import numpy as np
 import pytest
 
 from phasespace import WORKLOADS, make_inputs
+from oracle.matrix_element import get as oracle_get
+from _parity import TOL, bounds, check_selection
 
 pytestmark = pytest.mark.gpu
 
@@ -79,3 +82,42 @@ def test_process_autotune_keeps_results():
     assert k in (1, 2)
     got = p.compute(t(mom), t(a))["me"]
     assert torch.equal(got, ref) or (got / ref - 1).abs().max().item() < 1e-14
+
+
+@pytest.mark.parametrize("mode,bound", [(0, TOL), (1, 1e-5)], ids=["fp64", "mixed_fp32"])
+def test_batch_matches_oracle(mode, bound):
+    """Each process of one batched launch against the oracle on a sample of its events (the first,
+    the last and a seeded random choice), with alpha_s drawn per event."""
+    import torch
+    import paper_2503_21935_gb300 as pkg
+    dev = torch.device("cuda:0")
+    sets = [("ggtt", 3000, 64), ("ggttg", 700, 48), ("ggttgg", 300, 32), ("gu_tataggu", 129, 32)]
+    procs, inputs, outs, host = [], [], [], []
+    for name, n, _ in sets:
+        wl = WORKLOADS[name]
+        mom, a, rh, rc = make_inputs(wl, n, alpha_s_range=(0.08, 0.2))
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        procs.append(pkg.Process(wl.process))
+        inputs.append((t(mom), t(a), t(rh), t(rc)))
+        outs.append({"me": torch.full((n,), float("nan"), dtype=torch.float64, device=dev),
+                     "selhel": torch.full((n,), -1, dtype=torch.int32, device=dev),
+                     "selcol": torch.full((n,), -1, dtype=torch.int32, device=dev)})
+        host.append((mom, a, rh, rc))
+    b = pkg.Batch(procs)
+    b.compute(inputs, outs, mode=mode)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(77)
+    for (name, n, k), (mom, a, rh, rc), o in zip(sets, host, outs):
+        wl = WORKLOADS[name]
+        idx = np.unique(np.concatenate([[0, n - 1], rng.choice(n, k - 2, replace=False)]))
+        ref = oracle_get(wl.process).evaluate(mom[idx], a[idx], rh[idx], rc[idx])
+        me = o["me"].cpu().numpy()[idx]
+        rel = np.abs(me / ref["me"] - 1.0)
+        if mode == 0:
+            assert np.all(rel <= bounds(wl.process, mom[idx], a[idx], rel)), f"{name}: max rel {rel.max():.3e}"
+        else:
+            assert rel.max() <= bound, f"{name}: max rel {rel.max():.3e}"
+        check_selection(o["selhel"].cpu().numpy()[idx], ref["selhel"], ref["mh"], rh[idx], bound,
+                        f"batch {name} mode {mode} selhel")
+        check_selection(o["selcol"].cpu().numpy()[idx], ref["selcol"], ref["colw"], rc[idx], TOL,
+                        f"batch {name} mode {mode} selcol")

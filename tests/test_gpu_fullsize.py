@@ -5,8 +5,8 @@ import numpy as np
 import pytest
 
 from phasespace import WORKLOADS, make_inputs
-from oracle.matrix_element import get as oracle_get, near_tie
-from _parity import TOL, bounds
+from oracle.matrix_element import get as oracle_get
+from _parity import TOL, bounds, check_selection
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +36,5 @@ def test_full_size_sampled(name, nsample):
     ref = oracle_get(wl.process).evaluate(mom[idx], a[idx], rh[idx], rc[idx])
     rel = np.abs(me[idx] / ref["me"] - 1.0)
     assert np.all(rel <= bounds(wl.process, mom[idx], a[idx], rel)), f"max rel {rel.max():.3e}"
-    tie_h = near_tie(ref["mh"], rh[idx], TOL)
-    tie_c = near_tie(ref["colw"], rc[idx], TOL)
-    assert np.array_equal(sh[idx][~tie_h], ref["selhel"][~tie_h])
-    assert np.array_equal(sc[idx][~tie_c], ref["selcol"][~tie_c])
+    check_selection(sh[idx], ref["selhel"], ref["mh"], rh[idx], TOL, f"{name} selhel")
+    check_selection(sc[idx], ref["selcol"], ref["colw"], rc[idx], TOL, f"{name} selcol")

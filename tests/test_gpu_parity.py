@@ -10,8 +10,8 @@ import numpy as np
 import pytest
 
 from phasespace import WORKLOADS, make_inputs, rambo, incoming_beams
-from oracle.matrix_element import get as oracle_get, near_tie
-from _parity import TOL, bounds as _bounds
+from oracle.matrix_element import get as oracle_get
+from _parity import TOL, bounds as _bounds, check_selection, check_mode
 
 pytestmark = pytest.mark.gpu
 
@@ -79,13 +79,55 @@ def test_parity_fp64(name, nevt, kernel):
     ctot = ref["colw"].sum(axis=1, keepdims=True)
     dcw = np.abs(got["colw"] - ref["colw"]) / ctot
     assert np.all(dcw <= _bounds(wl.process, mom, a, dcw))
-    tie_h = near_tie(ref["mh"], rh, TOL)
-    tie_c = near_tie(ref["colw"], rc, TOL)
-    assert np.array_equal(got["selhel"][~tie_h], ref["selhel"][~tie_h])
-    assert np.array_equal(got["selcol"][~tie_c], ref["selcol"][~tie_c])
+    check_selection(got["selhel"], ref["selhel"], ref["mh"], rh, TOL, f"{name} {kernel} selhel")
+    check_selection(got["selcol"], ref["selcol"], ref["colw"], rc, TOL, f"{name} {kernel} selcol")
 
 
-@pytest.mark.parametrize("name", ["eemumu", "ggtt", "ggttg", "ggttgg", "gu_tataggu"])
+def _check_fp64(proc, wl, mom, a, rh, rc, got, what):
+    """Every output of a float64 run against the oracle at the float64 bar."""
+    ref = oracle_get(wl.process).evaluate(mom, a, rh, rc)
+    rel = np.abs(got["me"] / ref["me"] - 1.0)
+    assert np.all(rel <= _bounds(wl.process, mom, a, rel)), f"{what}: me max rel {rel.max():.3e}"
+    tot = ref["mh"].sum(axis=1, keepdims=True)
+    dmh = np.abs(got["mh"] - ref["mh"][:, proc.good_helicities]) / tot
+    assert np.all(dmh <= _bounds(wl.process, mom, a, dmh))
+    dcw = np.abs(got["colw"] - ref["colw"]) / ref["colw"].sum(axis=1, keepdims=True)
+    assert np.all(dcw <= _bounds(wl.process, mom, a, dcw))
+    check_selection(got["selhel"], ref["selhel"], ref["mh"], rh, TOL, f"{what} selhel")
+    check_selection(got["selcol"], ref["selcol"], ref["colw"], rc, TOL, f"{what} selcol")
+    return ref
+
+
+@pytest.mark.parametrize("kernel", ["auto", "thread", "cta"])
+@pytest.mark.parametrize("name,nevt", [("ggttg", 200), ("ggttgg", 120), ("gu_tataggu", 100)])
+def test_parity_per_event_alpha_s(name, nevt, kernel):
+    """alpha_s drawn per event in [0.08, 0.2): the per-event coupling (4 pi alpha_s)^p of each event
+    must be its own (a kernel reading another event's alpha_s, or the first one, fails), and me
+    must differ from the constant-alpha_s run by exactly the events' coupling ratio."""
+    wl = WORKLOADS[name]
+    mom, a, rh, rc = make_inputs(wl, nevt, alpha_s_range=(0.08, 0.2))
+    assert a.std() > 0.02
+    proc = _proc(wl.process)
+    proc.set_kernel(KERNELS[kernel])
+    try:
+        got = _run(proc, mom, a, rh, rc)
+    finally:
+        proc.set_kernel(0)
+    _check_fp64(proc, wl, mom, a, rh, rc, got, f"{name} {kernel} per-event alpha_s")
+
+
+@pytest.mark.parametrize("mode,bound", [(1, 1e-5), (2, 1e-5), (3, 1e-5)], ids=["mixed_fp32", "tf32", "bf16x3"])
+def test_parity_per_event_alpha_s_reduced_precision(mode, bound):
+    """The per-event coupling in the reduced-precision colour sums (applied after the colour sum)."""
+    wl = WORKLOADS["ggttgg"]
+    mom, a, rh, rc = make_inputs(wl, 130, alpha_s_range=(0.08, 0.2))
+    proc = _proc(wl.process)
+    got = _run(proc, mom, a, rh, rc, mode=mode)
+    ref = _oracle(wl.process, mom, a, rh, rc)
+    check_mode(proc, got, ref, rh, rc, bound, f"ggttgg mode {mode} per-event alpha_s")
+
+
+@pytest.mark.parametrize("name", ["eemumu", "ggtt", "ggttg", "ggttgg", "ggttggg", "gu_tataggu"])
 def test_helicity_filter_matches_oracle(name):
     wl = WORKLOADS[name]
     proc = _proc(wl.process)
@@ -95,9 +137,15 @@ def test_helicity_filter_matches_oracle(name):
     assert proc.good_helicities == oracle_get(wl.process).helicity_filter(p, np.full(16, 0.118))
 
 
+MODE_CASES = [("eemumu", 64, 1e-5), ("ggtt", 300, 1e-5), ("ggttg", 200, 1e-5), ("ggttgg", 130, 1e-5),
+              ("ggttggg", 12, 1e-5), ("gu_tataggu", 140, 1e-5)]
+
+
 @pytest.mark.parametrize("kernel", ["thread", "cta"])
-@pytest.mark.parametrize("name,nevt,bound", [("ggttgg", 128, 1e-5), ("ggttggg", 12, 1e-5)])
+@pytest.mark.parametrize("name,nevt,bound", MODE_CASES)
 def test_parity_mixed_fp32_colour_sum(name, nevt, bound, kernel):
+    """Float64 amplitudes, float32 colour sum: me, every |M_h|^2 and the helicity selection at the
+    mode's bound; colour weights (float64 jamps) and the colour selection at the float64 bar."""
     if kernel == "cta" and name == "ggttggg":
         pytest.skip("g g > t t~ g g g: current store does not fit in shared memory (thread kernel only)")
     wl = WORKLOADS[name]
@@ -109,7 +157,10 @@ def test_parity_mixed_fp32_colour_sum(name, nevt, bound, kernel):
     finally:
         proc.set_kernel(0)
     ref = _oracle(wl.process, mom, a, rh, rc)
-    assert np.abs(got["me"] / ref["me"] - 1.0).max() <= bound
+    check_mode(proc, got, ref, rh, rc, bound, f"{name} {kernel} mixed_fp32")
+    dcw = np.abs(got["colw"] - ref["colw"]) / ref["colw"].sum(axis=1, keepdims=True)
+    assert np.all(dcw <= _bounds(wl.process, mom, a, dcw))
+    check_selection(got["selcol"], ref["selcol"], ref["colw"], rc, TOL, f"{name} {kernel} mixed_fp32 selcol")
 
 
 def test_auto_kernel_by_batch_size():
@@ -126,25 +177,21 @@ def test_auto_kernel_by_batch_size():
 
 
 @pytest.mark.parametrize("mode", [2, 3], ids=["tf32", "bf16x3"])
-@pytest.mark.parametrize("name,nevt,bound", [("eemumu", 64, 1e-5), ("ggtt", 300, 1e-5), ("ggttg", 200, 1e-5),
-                                             ("ggttgg", 130, 1e-5), ("ggttggg", 12, 1e-5),
-                                             ("gu_tataggu", 140, 1e-5)])
+@pytest.mark.parametrize("name,nevt,bound", MODE_CASES)
 def test_parity_tensor_core_colour_sum(name, nevt, bound, mode):
     """tcgen05 colour sums: jamps as two tf32 terms x the integer-scaled colour matrix (kind::tf32), or
-    three bf16 terms x its two bf16 parts (kind::f16); f32 accumulation in tensor memory."""
+    three bf16 terms x its two bf16 parts (kind::f16); f32 accumulation in tensor memory.  me, every
+    |M_h|^2 and the helicity selection at the mode's bound; colour weights (float64 jamps) and the
+    colour selection at the float64 bar."""
     wl = WORKLOADS[name]
     mom, a, rh, rc = make_inputs(wl, nevt)
     proc = _proc(wl.process)
     got = _run(proc, mom, a, rh, rc, mode=mode)
     ref = _oracle(wl.process, mom, a, rh, rc)
-    assert np.abs(got["me"] / ref["me"] - 1.0).max() <= bound
-    tot = ref["mh"].sum(axis=1, keepdims=True)
-    assert (np.abs(got["mh"] - ref["mh"][:, proc.good_helicities]) / tot).max() <= bound
-    # colour weights come from the float64 jamps in every mode
+    check_mode(proc, got, ref, rh, rc, bound, f"{name} mode {mode}")
     dcw = np.abs(got["colw"] - ref["colw"]) / ref["colw"].sum(axis=1, keepdims=True)
     assert np.all(dcw <= _bounds(wl.process, mom, a, dcw))
-    tie_c = near_tie(ref["colw"], rc, TOL)
-    assert np.array_equal(got["selcol"][~tie_c], ref["selcol"][~tie_c])
+    check_selection(got["selcol"], ref["selcol"], ref["colw"], rc, TOL, f"{name} mode {mode} selcol")
 
 
 # float32 amplitudes and colour sum (the paper's float build); bounds are the measured

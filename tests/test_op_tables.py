@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 from phasespace import WORKLOADS, make_inputs
-from oracle.matrix_element import get as oracle_get, near_tie
-from _parity import TOL, bounds
+from oracle.matrix_element import get as oracle_get
+from _parity import TOL, bounds, check_selection
 from op_emulator import Emulator
 
 CASES = [("eemumu", 64), ("ggtt", 64), ("ggttg", 48), ("ggttgg", 32), ("gu_tataggu", 32), ("ggttggg", 2)]
@@ -22,10 +22,8 @@ def _check(wl, mom, a, rh, rc, got):
     assert np.all(dmh <= bounds(wl.process, mom, a, dmh))
     dcw = np.abs(got["colw"] - ref["colw"]) / ref["colw"].sum(axis=1, keepdims=True)
     assert np.all(dcw <= bounds(wl.process, mom, a, dcw))
-    tie_h = near_tie(ref["mh"], rh, TOL)
-    tie_c = near_tie(ref["colw"], rc, TOL)
-    assert np.array_equal(got["selhel"][~tie_h], ref["selhel"][~tie_h])
-    assert np.array_equal(got["selcol"][~tie_c], ref["selcol"][~tie_c])
+    check_selection(got["selhel"], ref["selhel"], ref["mh"], rh, TOL, f"{wl.name} selhel")
+    check_selection(got["selcol"], ref["selcol"], ref["colw"], rc, TOL, f"{wl.name} selcol")
 
 
 @pytest.mark.parametrize("name,nevt", CASES)

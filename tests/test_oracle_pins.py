@@ -209,7 +209,45 @@ def test_selection_rule_bruteforce():
             if acc > r[e] * tot:
                 break
         assert got[e] == k
-    assert not near_tie(w, r).any() or True
+
+
+def test_near_tie_constructed_cases():
+    """The mask that drops an event from the bit-exact selection comparison (reading P7: some
+    cumulative weight within rel * total of r * total).  Integer weights make every cumulative sum
+    and the total exact, so the distance of r * total to each cumulative sum is known by
+    construction: exactly on a cumulative sum (a tie), half a step inside the window (a tie), four
+    window widths away (not a tie) and halfway between two cumulative sums (not a tie).  A widened,
+    narrowed, inverted or off-by-one mask fails one of these."""
+    rng = np.random.default_rng(11)
+    n, k = 400, 6
+    w = rng.integers(1, 100, size=(n, k)).astype(np.float64)
+    cs = np.cumsum(w, axis=1)
+    tot = cs[:, -1]
+    rel = 1e-12
+    col = rng.integers(0, k - 1, size=n)          # an interior cumulative sum per event
+    c = cs[np.arange(n), col]
+    prev = np.where(col > 0, cs[np.arange(n), np.maximum(col - 1, 0)], 0.0)
+    exact = c / tot                                # r * total lands on cs[col] up to one rounding
+    inside = (c + 0.5 * rel * tot) / tot           # half a window above it
+    outside = (c + 4.0 * rel * tot) / tot          # four windows above it
+    below = (c - 4.0 * rel * tot) / tot
+    midway = 0.5 * (prev + c) / tot                # between two cumulative sums (steps are >= 1)
+    assert near_tie(w, exact, rel).all()
+    assert near_tie(w, inside, rel).all()
+    assert not near_tie(w, outside, rel).any()
+    assert not near_tie(w, below, rel).any()
+    assert not near_tie(w, midway, rel).any()
+    # the window scales with the total, not with the weights' magnitude
+    assert near_tie(1e-30 * w, exact, rel).all() and not near_tie(1e-30 * w, midway, rel).any()
+    # a tie on the last cumulative sum (r -> 1) counts too; the default window is 1e-12
+    assert near_tie(w, 1.0 - 0.5 * rel * np.ones(n)).all()
+    assert not near_tie(w, 1.0 - 4.0 * rel * np.ones(n)).any()
+    # mixed rows: exactly the constructed ties are flagged, row by row
+    pick = rng.random(n) < 0.3
+    r = np.where(pick, inside, midway)
+    assert np.array_equal(near_tie(w, r, rel), pick)
+    # uniform random r: ties have probability ~ k * 2e-12 per event, so none in this sample
+    assert not near_tie(w, rng.random(n), rel).any()
 
 
 def test_selection_frequencies_follow_weights():

@@ -1,10 +1,13 @@
 """The allocation-free entry point (mgx_compute_noalloc) against mgx_compute, through the C ABI.
 
-Callers that cannot allocate device memory (a Fortran event loop without a CUDA allocator, a
-plugin in a framework that owns the device memory pool) use mgx_compute_noalloc, whose workspace
-is a fixed module-scope device array.  Its results must equal those of the ordinary entry point
-(which uses a caller-provided workspace) within the float64 parity tolerance, on two calls in a
-row (the array keeps the previous call's contents).  This file is collected last on purpose.
+Some callers cannot allocate device memory where they evaluate matrix elements: a Fortran event
+loop that links the library but has no CUDA allocator of its own, or a plugin inside a framework
+that owns the device memory pool and forbids cudaMalloc from third-party code.  They call
+mgx_compute_noalloc, whose workspace is a fixed module-scope device array.  Its results must equal
+those of the ordinary entry point (caller-provided workspace, same thread-per-event kernel) within
+the float64 parity tolerance, on two calls in a row (the array keeps the previous call's contents),
+in both modes it accepts.  The file name sorts last so that pytest collects it after every other
+test file: a run that stops at the first failure has then already run all the other tests.
 """
 import ctypes
 
@@ -17,21 +20,12 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
 
-def _noalloc(lib):
-    f = lib.mgx_compute_noalloc
-    P = ctypes.c_void_p
-    f.restype = ctypes.c_int
-    f.argtypes = [P, ctypes.c_int64, P, P, P, P, P, P, P, ctypes.c_int, P]
-    lib.mgx_noalloc_scratch_bytes.restype = ctypes.c_size_t
-    return f
-
-
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed_fp32"])
 @pytest.mark.parametrize("name,nevt", [("ggttgg", 3000), ("ggttggg", 40)])
-def test_noalloc_matches_compute(name, nevt):
+def test_noalloc_matches_compute(name, nevt, mode):
     import torch
     import paper_2503_21935_gb300 as pkg
     lib = pkg.lib()
-    noalloc = _noalloc(lib)
     assert lib.mgx_noalloc_scratch_bytes() == 128 << 20
     wl = WORKLOADS[name]
     mom, a, rh, rc = make_inputs(wl, nevt)
@@ -40,7 +34,7 @@ def test_noalloc_matches_compute(name, nevt):
     M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
     proc = pkg.Process(wl.process, device=0)
     proc.set_kernel(pkg.MGX_KERNEL_THREAD)     # the kernel the fixed-scratch entry point runs
-    ref = proc.compute(M, A, RH, RC, mode=pkg.MGX_FP64)
+    ref = proc.compute(M, A, RH, RC, mode=mode)
     torch.cuda.synchronize()
     ptr = lambda x: ctypes.c_void_p(x.data_ptr())
     stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
@@ -48,9 +42,9 @@ def test_noalloc_matches_compute(name, nevt):
         me = torch.full((nevt,), float("nan"), dtype=torch.float64, device=dev)
         sh = torch.full((nevt,), -1, dtype=torch.int32, device=dev)
         sc = torch.full((nevt,), -1, dtype=torch.int32, device=dev)
-        rc_ = noalloc(proc._h, nevt, ptr(M), ptr(A), ptr(RH), ptr(RC), ptr(me), ptr(sh), ptr(sc),
-                      pkg.MGX_FP64, stream)
-        assert rc_ == 0, lib.mgx_status_string(rc_)
+        rc_ = lib.mgx_compute_noalloc(proc._h, nevt, ptr(M), ptr(A), ptr(RH), ptr(RC), ptr(me), ptr(sh), ptr(sc),
+                                      mode, stream)
+        assert rc_ == 0, f"call {call}: {pkg.status_string(rc_)} ({rc_})"
         torch.cuda.synchronize()
         rel = (me / ref["me"] - 1.0).abs().max().item()
         assert rel <= TOL, f"call {call}: max rel {rel:.3e}"
