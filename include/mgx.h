@@ -60,7 +60,8 @@ enum mgx_status {
 enum mgx_mode {
   MGX_FP64 = 0,       /* float64 amplitudes and colour sum */
   MGX_MIXED_FP32 = 1, /* float64 amplitudes; jamps rounded to float32, float32 quadratic form */
-  MGX_MIXED_TF32 = 2, /* float64 amplitudes; tensor-core colour sum: jamps split into two tf32
+  MGX_MIXED_TF32 = 2, /* float64 amplitudes; tensor-core colour sum (tcgen05, fused into the
+                         thread-per-event kernel): jamps rounded to float32 and split into two tf32
                          terms times the integer-scaled colour matrix (exact in tf32), float32
                          accumulation */
   MGX_MIXED_BF16X3 = 3, /* float64 amplitudes; tensor-core colour sum in bf16: jamps split into three
@@ -165,8 +166,17 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
  * THREAD_SMEM: the thread-per-event kernel with each thread's workspace in shared memory
  * (64 threads per block, no caller workspace needed); available for small processes (e+ e- >
  * mu+ mu-, g g > t t~), and what AUTO picks otherwise when the whole batch fits one block per SM
- * (a latency-bound batch).  All give identical results up to float64 rounding. */
-enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2, MGX_KERNEL_THREAD_SMEM = 3 };
+ * (a latency-bound batch).  HELICITY: the helicity-parallel mapping (Sec. 2: different helicity
+ * combinations of one event processed in parallel, so that far fewer events fill the GPU): the
+ * helicities are split into 2^k groups by their values on k fixed particles, one thread per
+ * (event, group) computes the current variants and amplitudes its group uses, and a second kernel
+ * sums each event's helicities in canonical order and selects; the fixed particles and k come
+ * from a work model of the op table (MGX_FP64, MGX_MIXED_FP32, MGX_FLOAT).  AUTO takes it for a
+ * batch that leaves the thread kernel's grid underfilled when that model predicts at least a
+ * 1.33x gain and the batch is too large for CTA / THREAD_SMEM.  All give identical results up to
+ * float64 rounding. */
+enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2, MGX_KERNEL_THREAD_SMEM = 3,
+                  MGX_KERNEL_HELICITY = 4 };
 int mgx_process_set_kernel(mgx_process* proc, int kernel);  /* INVALID_ARGUMENT if unusable */
 /* the kernel set; for AUTO, THREAD (the choice for throughput batches; AUTO picks CTA or
  * THREAD_SMEM per call for small batches, as above) */
@@ -219,6 +229,18 @@ int mgx_process_autotune(mgx_process* proc, int64_t nevt, const double* momenta,
                          void* workspace, size_t workspace_bytes, void* stream, int* kernel, int* blocks_per_sm,
                          double* me_scratch);
 
+/* Failure detection of the tensor-core colour sum (modes MGX_MIXED_TF32, MGX_MIXED_BF16X3).  Every
+ * wait of a block for its own tensor-core work has a time limit; when one runs out, the block adds 1
+ * to the process's device error counter, writes NaN to me (and -1 to the selections) of its events
+ * from then on, and stops using the tensor cores, so a stuck colour sum shows as NaN, never as a
+ * hang or a wrong number.  mgx_process_device_errors copies the counter to *count (synchronous:
+ * call it after the computes it should cover have completed) and zeroes it when reset != 0. */
+int mgx_process_device_errors(mgx_process* proc, int* count, int reset);
+/* Test hook for that path: with skip_mma != 0 the tensor-core colour sum issues no MMA, so each of
+ * its waits runs out after wait_ms (0 < wait_ms <= 10000; the default limit is 1000 ms); nothing is
+ * in flight when the block frees its tensor memory.  skip_mma = 0 restores normal operation. */
+int mgx_process_set_tc_wait_test(mgx_process* proc, int skip_mma, double wait_ms);
+
 /* Float64 work per event of this process in `mode`, from the op table and per-op
  * instruction counts of the device code: instructions (add, multiply and fused
  * multiply-add each one) and flops (a fused multiply-add counted as two).  Used for
@@ -227,8 +249,8 @@ double mgx_fp64_ops_per_event(const mgx_process* proc, int mode);
 double mgx_fp64_flops_per_event(const mgx_process* proc, int mode);
 
 /* Number of this library's kernels one mgx_compute of nevt events in `mode` launches with the
- * process's current settings (1, or 4 per chunk in the tensor-core modes); -1 on invalid
- * arguments. */
+ * process's current settings (1: every mode, the tensor-core colour sums included, is one fused
+ * kernel); -1 on invalid arguments. */
 int mgx_kernel_launches(const mgx_process* proc, int64_t nevt, int mode);
 
 /* Allocation-free variant of mgx_compute.  The paper has no counterpart: this entry point
@@ -306,6 +328,14 @@ int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, floa
  * averaged across replicas (weighted by their batch sizes).  Replicas that start from the same
  * parameters and apply the same averaged gradient stay identical.  Asynchronous on stream. */
 int mgx_mlp_adam_step(mgx_mlp* net, const float* grad, float lr, void* stream);
+/* Failure detection of the network's tensor-core GEMMs: every wait for the tile's MMAs has a time
+ * limit; a tile whose wait runs out writes NaN to its outputs and adds 1 to the network's device
+ * error counter.  mgx_mlp_device_errors copies the counter to *count (synchronous; call it after
+ * the work it covers has completed) and zeroes it when reset != 0.  mgx_mlp_set_wait_test is the
+ * test hook: with skip_mma != 0 no MMA is issued and each wait runs out after wait_ms
+ * (0 < wait_ms <= 10000, default limit 1000 ms). */
+int mgx_mlp_device_errors(mgx_mlp* net, int* count, int reset);
+int mgx_mlp_set_wait_test(mgx_mlp* net, int skip_mma, double wait_ms);
 
 /* ---- unweighting (plain hit-or-miss and two-stage with the surrogate) ----
  * Plain: keep with probability min(1, w/w_max), weight max(1, w/w_max).  Two-stage

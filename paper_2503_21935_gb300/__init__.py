@@ -64,6 +64,8 @@ def lib():
             "mgx_process_set_kernel": (I, [P, I]),
             "mgx_process_get_kernel": (I, [P]),
             "mgx_process_set_blocks_per_sm": (I, [P, I]),
+            "mgx_process_device_errors": (I, [P, ctypes.POINTER(I), I]),
+            "mgx_process_set_tc_wait_test": (I, [P, I, D]),
             "mgx_process_destroy": (None, [P]),
             "mgx_measure_fma_tflops": (I, [I, I, ctypes.POINTER(D)]),
             "mgx_uniforms": (I, [I64, I64, U64, ctypes.c_uint32, P, P]),
@@ -94,6 +96,8 @@ def lib():
             "mgx_mlp_gradients": (I, [P, I, P, P, P, P, P, SZ, P]),
             "mgx_mlp_train_step": (I, [P, I, P, P, ctypes.c_float, P, P, SZ, P]),
             "mgx_mlp_adam_step": (I, [P, P, ctypes.c_float, P]),
+            "mgx_mlp_device_errors": (I, [P, ctypes.POINTER(I), I]),
+            "mgx_mlp_set_wait_test": (I, [P, I, D]),
             "mgx_noalloc_scratch_bytes": (SZ, []),
             "mgx_compute_noalloc": (I, [P, I64, P, P, P, P, P, P, P, I, P]),
             "mgx_status_string": (ctypes.c_char_p, [I]),
@@ -314,6 +318,16 @@ class Mlp:
                                        _stream(xd.device)), "mgx_mlp_gradients")
         return g
 
+    def device_errors(self, reset=True):
+        """Tensor-core waits of the GEMMs that ran out since the last reset (synchronise first)."""
+        c = ctypes.c_int()
+        _check(lib().mgx_mlp_device_errors(self._h, ctypes.byref(c), int(reset)), "mgx_mlp_device_errors")
+        return c.value
+
+    def set_wait_test(self, skip_mma, wait_ms=1000.0):
+        """Test hook: with skip_mma the GEMMs issue no MMA and their waits run out."""
+        _check(lib().mgx_mlp_set_wait_test(self._h, int(skip_mma), float(wait_ms)), "mgx_mlp_set_wait_test")
+
     def adam_step(self, grad, lr=1e-3):
         """One Adam step on a device gradient (e.g. the replicas' average in data-parallel training)."""
         _check(lib().mgx_mlp_adam_step(self._h, _ptr(grad), ctypes.c_float(lr), _stream(grad.device)),
@@ -417,6 +431,17 @@ class Process:
                "mgx_process_autotune")
         self._ws = {}
         return k.value, b.value
+
+    def device_errors(self, reset=True):
+        """Tensor-core waits that ran out since the last reset (synchronise the stream first)."""
+        c = ctypes.c_int()
+        _check(lib().mgx_process_device_errors(self._h, ctypes.byref(c), int(reset)), "mgx_process_device_errors")
+        return c.value
+
+    def set_tc_wait_test(self, skip_mma, wait_ms=1000.0):
+        """Test hook: with skip_mma the tensor-core colour sum issues no MMA and its waits run out."""
+        _check(lib().mgx_process_set_tc_wait_test(self._h, int(skip_mma), float(wait_ms)),
+               "mgx_process_set_tc_wait_test")
 
     def fp64_ops_per_event(self, mode=MGX_FP64):
         """Float64 instructions per event (fma, mul, add one each)."""

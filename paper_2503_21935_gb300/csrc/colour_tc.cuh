@@ -1,17 +1,22 @@
-// Tensor-core colour sum (modes MGX_MIXED_TF32 and MGX_MIXED_BF16X3), the one dense
-// contraction of the path.
+// Tensor-core colour sum (modes MGX_MIXED_TF32 and MGX_MIXED_BF16X3), the one dense contraction of
+// the path, fused into the thread-per-event amplitude kernel.
 //
-// The jamps of a batch (rounded to float32) form a real matrix X with one row per (event, good
-// helicity, Re/Im):
-// row r = 2 (e ngood + ih) + part, K = ncol.  With the colour matrix scaled to integers,
-// Cs = den C, Y = X Cs is a tcgen05.mma tile of M = 128 rows (f32 accumulate in tensor memory)
-// and |M_h|^2 = (x_Re . y_Re + x_Im . y_Im) / den.  Both operands are split into sums of
-// low-precision parts and the partial products are accumulated into the same tile:
-//   tf32:   X = X0 + X1 (two tf32 terms, ~22 bits of X); Cs exact in tf32 (one part);
-//           products X0 Cs + X1 Cs.
-//   bf16x3: X = X0 + X1 + X2 (three bf16 terms, ~24 bits), Cs = C0 + C1 (two bf16 terms, exact
-//           for integers below 2^16); products X_i C_j with i + j < 3 (the dropped X2 C1 and
-//           X1 C1 ... terms lie below 2^-24 relative).
+// After the 128 threads of a block have run the op table for their 128 events, the jamps of one good
+// helicity h form a real matrix X_h = [128 events x ncol] per part (Re, Im).  With the colour matrix
+// scaled to integers, Cs = den C, Y = X_h Cs is one tcgen05.mma tile (M = 128 rows, N = ncol padded
+// to 16, f32 accumulation in tensor memory) and |M_h|^2 = (x_Re . y_Re + x_Im . y_Im) / den, the dot
+// taken by each thread with its own row.  Both operands are split into sums of low-precision parts
+// and the partial products accumulate into the same tile:
+//   tf32:   x = x0 + x1 (two tf32 terms, ~22 bits of the float32 jamp); Cs exact in tf32 (one part);
+//           products x0 Cs + x1 Cs.
+//   bf16x3: x = x0 + x1 + x2 (three bf16 terms, ~24 bits), Cs = C0 + C1 (two bf16 terms, exact for
+//           integers below 2^16); products x_i C_j with i + j < 3 (the dropped terms lie below 2^-24
+//           relative).
+// The contraction runs over K = ncol in chunks of at most 32 columns (one shared-memory stage each),
+// so a process with many flows needs no more shared memory than one with few.  One thread issues the
+// MMAs; tcgen05.commit arrives on an mbarrier that every thread waits on, with a time limit: a wait
+// that runs out makes the call return false (the kernel then marks the block's events NaN, counts the
+// error and stops using the tensor cores).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -19,12 +24,13 @@
 
 namespace mgx {
 
-constexpr int kTcRows = 128;
+constexpr int kTcRows = 128;   // events per tile = threads per block of the fused kernel
+constexpr int kTcKc = 32;      // contraction columns per shared-memory stage
 
 struct TcTf32 {
   static constexpr uint32_t kFmt = umma::FMT_TF32;
   static constexpr int kElem = 4, kKStep = 8, kAParts = 2, kBParts = 1;
-  __device__ static void split(float x, unsigned char* dst[], uint32_t off) {
+  __device__ static void split(float x, unsigned char* const dst[], uint32_t off) {
     const float hi = umma::to_tf32(x);
     *reinterpret_cast<float*>(dst[0] + off) = hi;
     *reinterpret_cast<float*>(dst[1] + off) = umma::to_tf32(x - hi);
@@ -37,7 +43,7 @@ struct TcTf32 {
 struct TcBf16x3 {
   static constexpr uint32_t kFmt = umma::FMT_BF16;
   static constexpr int kElem = 2, kKStep = 16, kAParts = 3, kBParts = 2;
-  __device__ static void split(float x, unsigned char* dst[], uint32_t off) {
+  __device__ static void split(float x, unsigned char* const dst[], uint32_t off) {
     const __nv_bfloat16 p0 = __float2bfloat16_rn(x);
     const float r1 = x - __bfloat162float(p0);           // exact
     const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
@@ -51,102 +57,112 @@ struct TcBf16x3 {
   }
 };
 
-// shared memory: A parts (128 x kpad each, canonical K-major), B parts (npad x kpad each),
-// mbarrier, TMEM slot
+// Colour matrix and launch constants of the fused colour sum (kernel parameter, by value).
+struct TcArgs {
+  const unsigned char* bchunks;  // integer-scaled colour matrix: per K chunk c, kBParts canonical
+                                 // K-major tiles [npad][kc_c] (kc_c = min(32, kpad - 32 c)), contiguous
+  int ncol, npad, kpad, nchunk;  // kpad: ncol rounded up to the k-step; nchunk = ceil(kpad / 32)
+  uint32_t tcols;                // tensor-memory columns held by each block (power of 2, >= npad)
+  double inv_den;                // 1 / den
+  int* status;                   // device error counter (one increment per block whose wait ran out)
+  int skip_mma;                  // test hook: issue no MMA, so that the waits run out
+  unsigned long long wait_ns;    // time limit of one mbarrier wait
+};
+
+// shared-memory bytes of the colour-sum stage: A parts (128 x kc) and B parts (npad x kc) of one chunk
 template <class F>
-__host__ __device__ inline size_t colour_tc_smem(int kpad, int npad) {
-  return (size_t)F::kAParts * kTcRows * kpad * F::kElem + (size_t)F::kBParts * npad * kpad * F::kElem + 64;
+__host__ __device__ inline size_t tc_stage_bytes(int kpad, int npad) {
+  const int kc = kpad < kTcKc ? kpad : kTcKc;
+  return (size_t)F::kAParts * kTcRows * kc * F::kElem + (size_t)F::kBParts * npad * kc * F::kElem;
 }
 
-template <class F>
-__global__ void __launch_bounds__(kTcRows)
-    colour_tc_kernel(const float* __restrict__ jamps, int64_t nrows, int ncol, int kpad, int npad,
-                     uint32_t tmem_cols, const unsigned char* __restrict__ bcanon, double inv_den,
-                     double* __restrict__ mh, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const size_t a_bytes = (size_t)kTcRows * kpad * F::kElem, b_bytes = (size_t)npad * kpad * F::kElem;
+// Colour sums of every good helicity for the block's 128 events (thread t owns event e, `valid` when
+// e < nevt; the jamps [ngood][ncol][Re, Im] are in the thread's workspace view W).  Writes
+// W[mh_off + ih] = scale |M_h|^2 (and mh_out) for valid events.  Every thread of the block must
+// call it.  Returns false when an mbarrier wait ran out.
+template <class F, class JW>
+__device__ bool tc_colour_sums(const KParams& P, const TcArgs& A, const JW& W, bool valid, int64_t e, double scale,
+                               double* __restrict__ mh_out, unsigned char* stage, uint64_t* mbar, uint32_t tmem,
+                               uint32_t& phase) {
+  const int t = threadIdx.x, warp = t >> 5;
+  const int kc_max = A.kpad < kTcKc ? A.kpad : kTcKc;
+  const size_t a_bytes = (size_t)kTcRows * kc_max * F::kElem;
   unsigned char* a[F::kAParts];
 #pragma unroll
-  for (int p = 0; p < F::kAParts; ++p) a[p] = smem_raw + p * a_bytes;
-  unsigned char* b = smem_raw + F::kAParts * a_bytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b + F::kBParts * b_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // B parts (already in canonical layout) into shared memory
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(bcanon);
-    uint4* dst = reinterpret_cast<uint4*>(b);
-    for (int i = tid; i < (int)(F::kBParts * b_bytes / 16); i += kTcRows) dst[i] = __ldg(src + i);
-  }
-  if (tid == 0) umma::mbar_init(mbar, 1);
-  if (warp == 0) umma::tmem_alloc(tslot, tmem_cols);
-  umma::fence_before_sync();
-  __syncthreads();
-  umma::fence_after_sync();
-  const uint32_t tmem = *tslot;
-  const uint32_t sbo = (uint32_t)(kpad * F::kElem / 16) * 128;
-  const uint32_t id = umma::idesc(F::kFmt, kTcRows, (uint32_t)npad);
-  const uint32_t sb = umma::smem_u32(b);
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int64_t tile = blockIdx.x; tile * kTcRows < nrows; tile += gridDim.x) {
-    const int64_t r = tile * kTcRows + tid;
-    const bool valid = r < nrows;
-    const float* xr = jamps + (r >> 1) * 2 * ncol + (r & 1);
-    for (int k = 0; k < kpad; ++k) {
-      const float x = (valid && k < ncol) ? __ldg(xr + 2 * k) : 0.0f;
-      F::split(x, a, umma::kmajor_offset((uint32_t)tid, (uint32_t)k, (uint32_t)kpad, F::kElem));
-    }
-    umma::fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      umma::fence_after_sync();
-      bool first = true;
-      for (int pa = 0; pa < F::kAParts; ++pa)
-        for (int pb = 0; pb < F::kBParts && pa + pb < F::kAParts; ++pb) {
-          const uint32_t sa = umma::smem_u32(a[pa]), sbp = sb + (uint32_t)(pb * b_bytes);
-          for (int ks = 0; ks < kpad / F::kKStep; ++ks) {
-            F::mma(tmem, umma::smem_desc(sa + ks * 256, 128, sbo), umma::smem_desc(sbp + ks * 256, 128, sbo), id,
-                   first ? 0u : 1u);
-            first = false;
+  for (int p = 0; p < F::kAParts; ++p) a[p] = stage + p * a_bytes;
+  unsigned char* b = stage + F::kAParts * a_bytes;
+  const uint32_t id = umma::idesc(F::kFmt, kTcRows, (uint32_t)A.npad);
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int ncol = A.ncol;
+  for (int ih = 0; ih < P.ngood; ++ih) {
+    float acc = 0.0f;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const int jb = P.jamp_off + 2 * ncol * ih + part;
+      size_t boff = 0;
+      for (int c = 0; c < A.nchunk; ++c) {
+        const int k0 = c * kTcKc;
+        const int kc = A.kpad - k0 < kTcKc ? A.kpad - k0 : kTcKc;
+        const size_t bbytes = (size_t)F::kBParts * A.npad * kc * F::kElem;
+        // this thread's row of the chunk, rounded to float32 and split into parts
+        for (int k = 0; k < kc; ++k) {
+          const int kk = k0 + k;
+          const float x = (valid && kk < ncol) ? __double2float_rn(W[jb + 2 * kk]) : 0.0f;
+          F::split(x, a, umma::kmajor_offset((uint32_t)t, (uint32_t)k, (uint32_t)kc, F::kElem));
+        }
+        // the colour matrix's chunk (already in canonical layout)
+        {
+          const uint4* src = reinterpret_cast<const uint4*>(A.bchunks + boff);
+          uint4* dst = reinterpret_cast<uint4*>(b);
+          for (int i = t; i < (int)(bbytes / 16); i += kTcRows) dst[i] = __ldg(src + i);
+        }
+        umma::fence_proxy_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (t == 0) {
+          umma::fence_after_sync();
+          if (!A.skip_mma) {
+            const uint32_t sbo = (uint32_t)(kc * F::kElem / 16) * 128;
+            const uint32_t b_part = (uint32_t)((size_t)A.npad * kc * F::kElem);
+            bool first = c == 0;
+            for (int pa = 0; pa < F::kAParts; ++pa)
+              for (int pb = 0; pb < F::kBParts && pa + pb < F::kAParts; ++pb) {
+                const uint32_t sa = umma::smem_u32(a[pa]), sb = umma::smem_u32(b) + pb * b_part;
+                for (int ks = 0; ks < kc / F::kKStep; ++ks) {
+                  F::mma(tmem, umma::smem_desc(sa + ks * 256, 128, sbo), umma::smem_desc(sb + ks * 256, 128, sbo), id,
+                         first ? 0u : 1u);
+                  first = false;
+                }
+              }
+            umma::mma_commit(mbar);
           }
         }
-      umma::mma_commit(mbar);
-    }
-    const bool done = umma::mbar_wait(mbar, phase);
-    phase ^= 1;
-    if (!__syncthreads_and(done)) {
-      ok = false;
-      break;
-    }
-    umma::fence_after_sync();
-    // epilogue: this thread's row of Y (TMEM lane = row), dotted with its row of X
-    float acc = 0.0f;
-    for (int c0 = 0; c0 < npad; c0 += 8) {
-      float y[8];
-      umma::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, y);
-      umma::tmem_wait_ld();
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int k = c0 + j;
-        if (valid && k < ncol) acc = fmaf(__ldg(xr + 2 * k), y[j], acc);
+        const bool done = umma::mbar_wait(mbar, phase, A.wait_ns);
+        phase ^= 1;
+        if (!__syncthreads_and(done)) return false;
+        umma::fence_after_sync();
+        boff += bbytes;
       }
+      // epilogue: this thread's row of Y (tensor-memory lane t), dotted with its float32 jamps
+      for (int n0 = 0; n0 < A.npad; n0 += 8) {
+        float y[8];
+        umma::tmem_ld8(tmem + lane_base + (uint32_t)n0, y);
+        umma::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n0 + j;
+          if (valid && n < ncol) acc = fmaf(__double2float_rn(W[jb + 2 * n]), y[j], acc);
+        }
+      }
+      umma::fence_before_sync();   // tensor-memory reads done before the next round's MMAs
     }
-    const float other = __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (valid && (r & 1) == 0) mh[r >> 1] = (double)(acc + other) * inv_den;
-    umma::fence_before_sync();
-    __syncthreads();
+    if (valid) {
+      const double mh = scale * ((double)acc * A.inv_den);
+      W[P.mh_off + ih] = mh;
+      if (mh_out) mh_out[e * P.ngood + ih] = mh;
+    }
   }
-  if (!ok) {
-    if (tid == 0 && err) atomicExch(err, 1);
-    umma::mbar_wait(mbar, phase ^ 1);   // bounded second wait for the MMAs still in flight
-  }
-  __syncthreads();
-  umma::fence_after_sync();
-  if (warp == 0) {
-    umma::tmem_dealloc(tmem, tmem_cols);
-    umma::tmem_relinquish();
-  }
+  return true;
 }
 
 }  // namespace mgx

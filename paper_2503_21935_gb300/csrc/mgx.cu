@@ -174,20 +174,12 @@ __device__ inline void finish_event(const KParams& P, int64_t e, const A& mh, co
 // Each thread owns one event at a time; current variants and jamps live in a per-thread
 // global workspace (offset-major so a warp's accesses coalesce).  Used for processes whose
 // per-event store does not fit in shared memory.
-// One event, evaluated by one thread: the whole op table into the workspace view W, then the
-// colour sum, helicity sum and selections (or, in the tensor-core mode, the export of the jamps).
-// Currents and jamps are of real type R; |M_h|^2 and the colour weights are kept as R in the
-// workspace and summed in float64.
-template <class R>
-__device__ inline void eval_event(const KParams& P, int64_t e, const double* pe, const WST<R>& W,
-                                  const double* __restrict__ alphas, const double* __restrict__ rhel,
-                                  const double* __restrict__ rcol, double* __restrict__ me,
-                                  int32_t* __restrict__ selhel, int32_t* __restrict__ selcol,
-                                  double* __restrict__ mh_out, double* __restrict__ colw_out, int mode,
-                                  float* __restrict__ jexp, double* __restrict__ colw_exp) {
+// The op table of one event, evaluated by one thread into the workspace view W: every current
+// variant, then the jamps [ngood][ncol][Re, Im] at W[jamp_off].  Currents and jamps are of real type R.
+template <class R, class H = AllHel>
+__device__ inline void eval_amplitudes(const KParams& P, const double* pe, const WST<R>& W, const H& hs = H()) {
   using T = Real<R>;
-  const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 below
-  const double scale = coupling_scale(P, alphas[e]);
+  const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 later
   if (P.jamp_zero)
     for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = T::from(0.0);
   for (int iop = 0; iop < P.nops; ++iop) {
@@ -199,12 +191,13 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
         // each bilinear variant is loaded once; the term's phase rotates the product
         const int4 a = __ldg(P.terms + 2 * o.aux);
         const int4 b = __ldg(P.terms + 2 * o.aux + 1);
-        const int nx = 1 << __popc(a.y), ny = 1 << __popc(a.w);
-        for (int ix = 0; ix < nx; ++ix) {
+        for (int ux = 0; ux < hs.count(a.y); ++ux) {
+          const int ix = hs.var(ux, a.y);
           cxT<R> X[4];
           W.load4(a.x + 8 * ix, X);
           const int hx = pdep(ix, a.y);
-          for (int iy = 0; iy < ny; ++iy) {
+          for (int uy = 0; uy < hs.count(a.w); ++uy) {
+            const int iy = hs.var(uy, a.w);
             const int ih = P.hidx[hx | pdep(iy, a.w)];
             if (ih < 0) continue;
             cxT<R> Y[4];
@@ -233,6 +226,7 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
         continue;
       }
       for (int ih = 0; ih < P.ngood; ++ih) {
+        if (!hs.ok(P.good[ih])) continue;
         const cxT<R> amp = group_amp<R>(P.terms, o, P.good[ih], W);
         const int jb = P.jamp_off + 2 * P.ncol * ih;
         // phase rotation by sign-bit and swap selects (no branch per flow), then one add each;
@@ -248,32 +242,33 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
       }
       continue;
     }
-    op_header<R>(P, o, gs, pe, W);
-    op_variants<R>(P, o, 1 << __popc(o.mdst), gs, pe, W);
+    op_header<R>(P, o, gs, pe, W, hs);
+    op_variants<R>(P, o, gs, pe, W, hs);
   }
-  if constexpr (std::is_same<R, double>::value) {
-    if (mode == MGX_MIXED_TF32 || mode == MGX_MIXED_BF16X3) {
-      // export the jamps [ngood][ncol][re, im] rounded to float32 (as in the mixed mode: the
-      // tensor-core kernel then needs no float64 conversions) and the colour weights
-      const int nj = 2 * P.ncol * P.ngood;
-      for (int i = 0; i < nj; ++i) jexp[e * nj + i] = (float)W[P.jamp_off + i];
-      for (int i = 0; i < P.ncol; ++i) {
-        double w = 0.0;
-        for (int ih = 0; ih < P.ngood; ++ih) {
-          const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
-          w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
-        }
-        colw_exp[e * P.ncol + i] = w * scale;
-      }
-      return;
-    }
-  }
+}
+
+// SIMT colour sums: W[mh_off + ih] = scale |M_h|^2 for every good helicity (float64, the mixed
+// float32 form, or float32 throughout)
+template <class R>
+__device__ inline void simt_colour_sums(const KParams& P, int64_t e, const WST<R>& W, double scale,
+                                        double* __restrict__ mh_out, int mode) {
+  using T = Real<R>;
   for (int ih = 0; ih < P.ngood; ++ih) {
     const int jb = P.jamp_off + 2 * P.ncol * ih;
     const double mh = scale * colour_sum<R>(P, [&](int k) { return W[jb + k]; }, P.ncol, mode);
     W[P.mh_off + ih] = T::from(mh);
     if (mh_out) mh_out[e * P.ngood + ih] = mh;
   }
+}
+
+// colour weights w_s = scale sum_h |J_s(h)|^2 from the jamps, then the helicity sum and the
+// selections from W[mh_off ..]
+template <class R>
+__device__ inline void finish_from_workspace(const KParams& P, int64_t e, const WST<R>& W, double scale,
+                                             const double* __restrict__ rhel, const double* __restrict__ rcol,
+                                             double* __restrict__ me, int32_t* __restrict__ selhel,
+                                             int32_t* __restrict__ selcol, double* __restrict__ colw_out) {
+  using T = Real<R>;
   if (selcol || colw_out) {
     for (int i = 0; i < P.ncol; ++i) {
       R w = T::from(0.0);
@@ -288,6 +283,19 @@ __device__ inline void eval_event(const KParams& P, int64_t e, const double* pe,
   }
   finish_event(P, e, [&](int ih) { return T::to_double(W[P.mh_off + ih]); },
                [&](int i) { return T::to_double(W[P.colw_off + i]); }, rhel, rcol, me, selhel, selcol);
+}
+
+// One event, evaluated by one thread: the op table, the colour sum, helicity sum and selections.
+template <class R>
+__device__ inline void eval_event(const KParams& P, int64_t e, const double* pe, const WST<R>& W,
+                                  const double* __restrict__ alphas, const double* __restrict__ rhel,
+                                  const double* __restrict__ rcol, double* __restrict__ me,
+                                  int32_t* __restrict__ selhel, int32_t* __restrict__ selcol,
+                                  double* __restrict__ mh_out, double* __restrict__ colw_out, int mode) {
+  eval_amplitudes<R>(P, pe, W);
+  const double scale = coupling_scale(P, alphas[e]);
+  simt_colour_sums<R>(P, e, W, scale, mh_out, mode);
+  finish_from_workspace<R>(P, e, W, scale, rhel, rcol, me, selhel, selcol, colw_out);
 }
 
 // stage the momenta of events [base, base + nb) (contiguous [events][npar][4]) through shared memory
@@ -309,8 +317,7 @@ __global__ void __launch_bounds__(kThreads, kSmemWs ? 1 : (std::is_same<R, float
     me_kernel(const KParams P, int64_t nevt, const double* __restrict__ mom, const double* __restrict__ alphas,
               const double* __restrict__ rhel, const double* __restrict__ rcol, double* __restrict__ me,
               int32_t* __restrict__ selhel, int32_t* __restrict__ selcol, double* __restrict__ mh_out,
-              double* __restrict__ colw_out, double* __restrict__ ws, int64_t nthreads, int mode,
-              float* __restrict__ jexp, double* __restrict__ colw_exp) {
+              double* __restrict__ colw_out, double* __restrict__ ws, int64_t nthreads, int mode) {
   extern __shared__ double smem[];
   const int npar4 = 4 * P.npar;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -321,8 +328,135 @@ __global__ void __launch_bounds__(kThreads, kSmemWs ? 1 : (std::is_same<R, float
     const int64_t e = base + threadIdx.x;
     if (e >= nevt) continue;
     eval_event<R>(P, e, smem + threadIdx.x * npar4, W, alphas, rhel, rcol, me, selhel, selcol, mh_out, colw_out,
-                  mode, jexp, colw_exp);
+                  mode);
   }
+}
+
+// The thread-per-event kernel with the colour sum on the tensor cores (float64 amplitudes): after the
+// block's 128 threads have run the op table for their events, the block forms every helicity's
+// colour sum with tcgen05.mma (tc_colour_sums), then each thread finishes its event.  The colour-sum
+// stage reuses the shared memory of the staged momenta; the mbarrier and the tensor-memory address
+// sit after it.  If a tensor-core wait runs out, the block counts the error, marks its events NaN
+// (me) and -1 (selections) from then on, and stops using the tensor cores.
+template <class F>
+__global__ void __launch_bounds__(kThreads, 4)
+    me_tc_kernel(const KParams P, const TcArgs A, int64_t nevt, const double* __restrict__ mom,
+                 const double* __restrict__ alphas, const double* __restrict__ rhel, const double* __restrict__ rcol,
+                 double* __restrict__ me, int32_t* __restrict__ selhel, int32_t* __restrict__ selcol,
+                 double* __restrict__ mh_out, double* __restrict__ colw_out, double* __restrict__ ws,
+                 int64_t nthreads, size_t bar_off) {
+  extern __shared__ __align__(1024) double smem[];
+  unsigned char* raw = reinterpret_cast<unsigned char*>(smem);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(raw + bar_off);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int npar4 = 4 * P.npar;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const WS W{ws + tid, nthreads};
+  if (threadIdx.x == 0) umma::mbar_init(mbar, 1);
+  if (threadIdx.x < 32) umma::tmem_alloc(tslot, A.tcols);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  uint32_t phase = 0;
+  bool healthy = true;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nevt; base += nthreads) {
+    const int64_t e = base + threadIdx.x;
+    const bool valid = e < nevt;
+    if (healthy) {
+      stage_momenta(mom, base, min((int64_t)blockDim.x, nevt - base), npar4, smem);
+      if (valid) eval_amplitudes<double>(P, smem + threadIdx.x * npar4, W);
+      const double scale = valid ? coupling_scale(P, alphas[e]) : 0.0;
+      __syncthreads();                      // the staged momenta are dead: the stage reuses them
+      healthy = tc_colour_sums<F>(P, A, W, valid, e, scale, mh_out, raw, mbar, tmem, phase);
+      if (healthy && valid) finish_from_workspace<double>(P, e, W, scale, rhel, rcol, me, selhel, selcol, colw_out);
+      if (!healthy && threadIdx.x == 0 && A.status) atomicAdd(A.status, 1);
+    }
+    if (!healthy && valid) {
+      me[e] = __longlong_as_double(0x7ff8000000000000ll);
+      if (selhel) selhel[e] = -1;
+      if (selcol) selcol[e] = -1;
+    }
+  }
+  if (!healthy) umma::mbar_wait(mbar, phase ^ 1, A.wait_ns);   // bounded wait for MMAs still in flight
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (threadIdx.x < 32) {
+    umma::tmem_dealloc(tmem, A.tcols);
+    umma::tmem_relinquish();
+  }
+}
+
+// ---------------------------------------------------------------- helicity-parallel kernel
+// For batches too small to fill the thread-per-event grid (Sec. 2: processing different helicity
+// combinations of one event in parallel lets far fewer events keep the GPU busy).  The helicities
+// of an event are split into G = 2^|fix| groups by their bits on the fixed legs `fix`; item
+// (e, g) = thread computes the current variants and amplitudes that group g's helicities use (the
+// variants of currents without a fixed leg are computed by every group), their colour sums into
+// mh_buf [nevt][ngood] and the group's share of the colour weights into cw_buf [nevt][G][ncol].
+// finish_hel_kernel then sums each event's helicities in canonical order and selects.  One launch
+// covers every group (a grid dimension rather than one CUDA stream per helicity).
+template <class R>
+__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 4)
+    me_hel_kernel(const KParams P, int64_t nevt, int gshift, int fix, const double* __restrict__ mom,
+                  const double* __restrict__ alphas, double* __restrict__ mh_buf, double* __restrict__ cw_buf,
+                  double* __restrict__ ws, int64_t nthreads, int mode) {
+  using T = Real<R>;
+  extern __shared__ double smem[];
+  const int npar4 = 4 * P.npar;
+  const int G = 1 << gshift;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const WST<R> W{reinterpret_cast<R*>(ws) + tid, nthreads};
+  const int64_t nitems = nevt << gshift;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nitems; base += nthreads) {
+    const int64_t e0 = base >> gshift;                       // blockDim is a multiple of G
+    stage_momenta(mom, e0, min((int64_t)(blockDim.x >> gshift), nevt - e0), npar4, smem);
+    const int64_t item = base + threadIdx.x;
+    if (item >= nitems) continue;
+    const int64_t e = item >> gshift;
+    const int g = (int)(item & (G - 1));
+    const GroupHel hs{fix, pdep(g, fix)};
+    eval_amplitudes<R>(P, smem + (threadIdx.x >> gshift) * npar4, W, hs);
+    const double scale = coupling_scale(P, alphas[e]);
+    for (int ih = 0; ih < P.ngood; ++ih) {
+      if (!hs.ok(P.good[ih])) continue;
+      const int jb = P.jamp_off + 2 * P.ncol * ih;
+      mh_buf[e * P.ngood + ih] = scale * colour_sum<R>(P, [&](int k) { return W[jb + k]; }, P.ncol, mode);
+    }
+    double* cw = cw_buf + (e * G + g) * P.ncol;
+    for (int i = 0; i < P.ncol; ++i) {
+      R w = T::from(0.0);
+      for (int ih = 0; ih < P.ngood; ++ih) {
+        if (!hs.ok(P.good[ih])) continue;
+        const int jb = P.jamp_off + 2 * P.ncol * ih + 2 * i;
+        w = fma(W[jb], W[jb], fma(W[jb + 1], W[jb + 1], w));
+      }
+      cw[i] = T::to_double(w) * scale;
+    }
+  }
+}
+
+// helicity sum (canonical order), colour weights (groups summed in group order) and selections
+__global__ void __launch_bounds__(kThreads)
+    finish_hel_kernel(const KParams P, int64_t nevt, int G, const double* __restrict__ mh_buf,
+                      const double* __restrict__ cw_buf, const double* __restrict__ rhel,
+                      const double* __restrict__ rcol, double* __restrict__ me, int32_t* __restrict__ selhel,
+                      int32_t* __restrict__ selcol, double* __restrict__ mh_out, double* __restrict__ colw_out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nevt) return;
+  const double* m = mh_buf + e * P.ngood;
+  const double* cw = cw_buf + e * G * P.ncol;
+  auto colw = [&](int i) {
+    double w = 0.0;
+    for (int g = 0; g < G; ++g) w += cw[g * P.ncol + i];
+    return w;
+  };
+  if (mh_out)
+    for (int ih = 0; ih < P.ngood; ++ih) mh_out[e * P.ngood + ih] = m[ih];
+  if (colw_out)
+    for (int i = 0; i < P.ncol; ++i) colw_out[e * P.ncol + i] = colw(i);
+  finish_event(P, e, [&](int ih) { return m[ih]; }, colw, rhel, rcol, me, selhel, selcol);
 }
 
 // ---------------------------------------------------------------- batched multi-process kernel
@@ -384,28 +518,9 @@ __global__ void __launch_bounds__(kThreads, 4)
       const int64_t e = base + threadIdx.x;
       if (e < last)
         eval_event<double>(P, e, smem + threadIdx.x * npar4, W, b.alphas, b.rhel, b.rcol, b.me, b.selhel, b.selcol, nullptr,
-                   nullptr, mode, nullptr, nullptr);
+                   nullptr, mode);
     }
   }
-}
-
-// helicity sum and selections after the tensor-core colour sum: mh_tc holds |M_h|^2 / g_s^(2p)
-__global__ void __launch_bounds__(kThreads)
-    finish_kernel(const KParams P, int64_t nevt, const double* __restrict__ alphas, const double* __restrict__ rhel,
-                  const double* __restrict__ rcol, const double* __restrict__ mh_tc,
-                  const double* __restrict__ colw, double* __restrict__ me, int32_t* __restrict__ selhel,
-                  int32_t* __restrict__ selcol, double* __restrict__ mh_out, double* __restrict__ colw_out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nevt) return;
-  const double scale = coupling_scale(P, alphas[e]);
-  const double* m = mh_tc + e * P.ngood;
-  const double* w = colw + e * P.ncol;
-  if (mh_out)
-    for (int ih = 0; ih < P.ngood; ++ih) mh_out[e * P.ngood + ih] = scale * m[ih];
-  if (colw_out)
-    for (int i = 0; i < P.ncol; ++i) colw_out[e * P.ncol + i] = w[i];
-  finish_event(P, e, [&](int ih) { return scale * m[ih]; }, [&](int i) { return w[i]; }, rhel, rcol, me, selhel,
-               selcol);
 }
 
 // ---------------------------------------------------------------- CTA-per-event kernel
@@ -651,11 +766,15 @@ struct mgx_process {
   int4* d_cta_terms = nullptr;
   int* d_cta_items = nullptr;
   int3* d_cta_steps = nullptr;
-  // integer-scaled colour matrix as canonical K-major tiles: tf32 (one part) and bf16 (two parts)
-  unsigned char* d_bcanon = nullptr;
-  unsigned char* d_bcanon16 = nullptr;
+  // integer-scaled colour matrix as canonical K-major tiles per 32-column K chunk: tf32 (one part)
+  // and bf16 (two parts per chunk)
+  unsigned char* d_tc_b32 = nullptr;
+  unsigned char* d_tc_b16 = nullptr;
   int tc_kpad = 0, tc_kpad16 = 0, tc_npad = 0, tc_cols = 0;
   bool bf16_exact = false;    // every integer entry is the sum of its two bf16 parts
+  int* d_status = nullptr;    // device error counter of the tensor-core waits
+  int tc_skip_mma = 0;        // test hook: the tensor-core colour sum issues no MMA
+  unsigned long long tc_wait_ns = 1000000000ull;   // time limit of one tensor-core wait
   int blocks_per_sm = 4;      // thread-per-event kernel
   int kernel = MGX_KERNEL_AUTO;
 };
@@ -728,6 +847,111 @@ bool use_cta_kernel(const mgx_process* pr, const KParams& kp, int64_t nevt, int 
   return pr->kernel == MGX_KERNEL_AUTO && nevt <= per_sm * sm_count(pr->device);
 }
 
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// ---- helicity-parallel plan: fixed legs and group count for one batch
+struct HelPlan {
+  int gshift = 0, fix = 0;   // G = 2^gshift groups by the helicity bits on the legs in `fix`
+};
+
+int host_pdep(int v, int mask) {
+  int r = 0, k = 0;
+  for (int b = 0; b < 31; ++b)
+    if (mask >> b & 1) {
+      if (v >> k & 1) r |= 1 << b;
+      ++k;
+    }
+  return r;
+}
+
+// Float64 instructions one thread executes with fixed legs `fix` (fix = 0: the whole event): the
+// current variants it computes (per variant of its legs, as in the work model of the roofline) plus
+// the amplitudes and colour sums of the group with the most good helicities.
+double hel_thread_work(const mgx_process* pr, int fix, int mode) {
+  const mgx_program_desc* prog = pr->prog;
+  double cur = 0.0, per_hel = 0.0;
+  for (int i = 0; i < prog->nops; ++i) {
+    const int32_t* o = prog->ops + 16 * i;
+    const int code = o[0], mdst = o[5], aux2 = o[12];
+    if (code == OP_AMP) {
+      per_hel += 16.0 * aux2 + 2.0 * o[10];    // closing products and flow updates, per helicity
+      continue;
+    }
+    double w = 8.0 * std::max(0, aux2 - 1);   // OP_SUM: 4-vector adds per further summand
+    switch (code) {
+      case OP_EXT: w = 24; break;
+      case OP_FFV_F: case OP_FFV_FB: w = 64; break;
+      case OP_FFV_V: w = 72; break;
+      case OP_VVV: w = 56; break;
+      case OP_VVVV: w = 32; break;
+      case OP_BIL: w = 56; break;
+      case OP_RBIL: w = 32; break;
+      default: break;
+    }
+    cur += w * (double)(1 << __builtin_popcount((unsigned)(mdst & ~fix)));
+  }
+  const double n = prog->ncol;
+  per_hel += mode == MGX_FP64 ? n * n + 3 * n : 2 * n;
+  int most = 0;
+  const int k = __builtin_popcount((unsigned)fix);
+  for (int g = 0; g < (1 << k); ++g) {
+    const int bits = host_pdep(g, fix);
+    int c = 0;
+    for (int h : pr->good) c += (h & fix) == bits;
+    most = std::max(most, c);
+  }
+  return cur + per_hel * most;
+}
+
+// The cheapest split of a batch of nevt events: estimated time = passes of the persistent grid x
+// the per-thread work; the whole-event thread kernel is gshift = 0.  force: best split with G > 1.
+HelPlan hel_plan(const mgx_process* pr, int64_t nevt, int mode, bool force) {
+  const int bps = mode == MGX_FLOAT ? 2 * pr->blocks_per_sm : pr->blocks_per_sm;
+  const int64_t cap = (int64_t)sm_count(pr->device) * bps * kThreads;
+  const int npar = pr->prog->npar;
+  const double t1 = hel_thread_work(pr, 0, mode) * (double)((nevt + cap - 1) / cap);
+  HelPlan best;
+  double tb = 0.0;
+  for (int fix = 1; fix < (1 << npar); ++fix) {
+    const int k = __builtin_popcount((unsigned)fix);
+    if (k > 6 || (nevt << k) > (int64_t)1 << 40) continue;
+    const double t = hel_thread_work(pr, fix, mode) * (double)(((nevt << k) + cap - 1) / cap);
+    if (best.gshift == 0 || t < tb) {
+      best = HelPlan{k, fix};
+      tb = t;
+    }
+  }
+  if (!force && !(tb < 0.75 * t1)) return HelPlan{};   // the split must be clearly cheaper
+  return best;
+}
+
+struct HelLayout {
+  size_t ws, mh, cw, total;
+};
+HelLayout hel_layout(const mgx_process* pr, const KParams& kp, const HelPlan& hp, int64_t nevt, int mode, int64_t nt) {
+  HelLayout L;
+  L.ws = align256((size_t)nt * thread_ws_bytes(kp, mode));
+  L.mh = align256((size_t)nevt * kp.ngood * sizeof(double));
+  L.cw = align256((size_t)nevt * ((size_t)1 << hp.gshift) * kp.ncol * sizeof(double));
+  L.total = L.ws + L.mh + L.cw;
+  return L;
+}
+
+// the helicity-parallel kernel: chosen explicitly, or by AUTO for a batch that leaves the thread
+// kernel's grid underfilled when the work model says a split is clearly cheaper (float64, mixed
+// float32 and float modes; the tensor-core modes run the fused thread kernel)
+bool use_hel_kernel(const mgx_process* pr, const KParams& kp, int64_t nevt, int mode, HelPlan* plan) {
+  if (!(mode_f64(mode) || mode == MGX_FLOAT) || pr->prog->npar < 2) return false;
+  if (pr->kernel == MGX_KERNEL_HELICITY) {
+    *plan = hel_plan(pr, nevt, mode, true);
+    return plan->gshift > 0;
+  }
+  if (pr->kernel != MGX_KERNEL_AUTO || use_cta_kernel(pr, kp, nevt, mode) || use_smem_ws(pr, kp, nevt, mode))
+    return false;
+  *plan = hel_plan(pr, nevt, mode, false);
+  return plan->gshift > 0;
+}
+
 size_t cta_smem_bytes(const mgx_process* pr, const KParams& kp) {
   const int ngp = kp.ngood <= 32 ? 32 : (kp.ngood <= 64 ? 64 : 128);
   const int G = kCtaThreads / ngp;
@@ -753,86 +977,64 @@ int launch_cta(mgx_process* pr, const KParams& kp, int64_t nevt, const double* m
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
-size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Tensor-core colour-sum mode: events are processed in chunks; per chunk the amplitude kernel
-// exports jamps (f64) and colour weights, the tensor-core kernel forms |M_h|^2, the finish kernel
-// sums helicities and selects.
-struct TcPlan {
-  int64_t chunk = 0;
-  size_t ws = 0, jexp = 0, colw = 0, mh = 0, err = 0, total = 0;
-};
-
-TcPlan tc_plan(const mgx_process* pr, const KParams& kp, int64_t nevt) {
-  TcPlan t;
-  const size_t per_evt = (size_t)kp.ngood * kp.ncol * 2 * sizeof(float);
-  // a chunk is a whole number of passes of the persistent grid (a partial pass would leave most
-  // threads idle), as many as about 4 GiB of exported jamps allow
-  const int64_t full = grid_threads(pr, std::max<int64_t>(nevt, 1));
-  const int64_t budget = (int64_t)(((size_t)4 << 30) / per_evt);
-  t.chunk = std::min<int64_t>(std::max<int64_t>(nevt, 1), std::max<int64_t>(1, budget / full) * full);
-  t.ws = align256((size_t)grid_threads(pr, t.chunk) * kp.ws_doubles * sizeof(double));
-  t.jexp = align256((size_t)t.chunk * per_evt);
-  t.colw = align256((size_t)t.chunk * kp.ncol * sizeof(double));
-  t.mh = align256((size_t)t.chunk * kp.ngood * sizeof(double));
-  t.err = 256;
-  t.total = t.ws + t.jexp + t.colw + t.mh + t.err;
-  return t;
-}
-
-// marks every event of a chunk whose tensor-core colour sum timed out
-__global__ void tc_error_kernel(const int* err, int64_t n, double* me) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n && *err) me[e] = __longlong_as_double(0x7ff8000000000000ll);
-}
-
+// Tensor-core colour-sum modes: the thread-per-event kernel with the fused tcgen05 colour sum; the
+// workspace is that of the float64 thread kernel.
 template <class F>
 int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
               const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh, double* cw,
               void* ws, size_t wsb, cudaStream_t st) {
+  static_assert(kThreads == kTcRows, "one tensor-core row per event of the block");
   const bool bf16 = F::kFmt == umma::FMT_BF16;
   if (bf16 && !pr->bf16_exact) return MGX_ERR_UNSUPPORTED_MODE;
-  const int kpad = bf16 ? pr->tc_kpad16 : pr->tc_kpad;
-  const unsigned char* bcanon = bf16 ? pr->d_bcanon16 : pr->d_bcanon;
-  const TcPlan t = tc_plan(pr, kp, nevt);
-  if (ws == nullptr || wsb < t.total) return MGX_ERR_WORKSPACE_TOO_SMALL;
+  TcArgs A{};
+  A.bchunks = bf16 ? pr->d_tc_b16 : pr->d_tc_b32;
+  A.ncol = kp.ncol;
+  A.npad = pr->tc_npad;
+  A.kpad = bf16 ? pr->tc_kpad16 : pr->tc_kpad;
+  A.nchunk = (A.kpad + kTcKc - 1) / kTcKc;
+  A.tcols = (uint32_t)pr->tc_cols;
+  A.inv_den = 1.0 / pr->prog->col_den;
+  A.status = pr->d_status;
+  A.skip_mma = pr->tc_skip_mma;
+  A.wait_ns = pr->tc_wait_ns;
+  const size_t stage = tc_stage_bytes<F>(A.kpad, A.npad);
+  const size_t moms = (size_t)kThreads * 4 * kp.npar * sizeof(double);
+  const size_t bar_off = align256(std::max(stage, moms));
+  const size_t smem = bar_off + 16;
+  if (cudaFuncSetAttribute(me_tc_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return MGX_ERR_CUDA;
+  // the persistent grid, at most as many blocks per SM as the SM's tensor memory holds
+  const int bps = std::min(pr->blocks_per_sm, 512 / pr->tc_cols);
+  const int64_t cap = (int64_t)sm_count(pr->device) * std::max(1, bps) * kThreads;
+  const int64_t nt = std::max<int64_t>(kThreads, std::min(cap, ((nevt + kThreads - 1) / kThreads) * kThreads));
+  if (ws == nullptr || wsb < (size_t)nt * thread_ws_bytes(kp, MGX_FP64)) return MGX_ERR_WORKSPACE_TOO_SMALL;
+  me_tc_kernel<F><<<(unsigned)(nt / kThreads), kThreads, smem, st>>>(kp, A, nevt, mom, as, rh, rc, me, sh, sc, mh, cw,
+                                                                     (double*)ws, nt, bar_off);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+// the helicity-parallel kernel and its finish kernel
+int launch_hel(mgx_process* pr, const KParams& kp, const HelPlan& hp, int64_t nevt, const double* mom,
+               const double* as, const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh,
+               double* cw, int mode, void* ws, size_t wsb, cudaStream_t st) {
+  const int64_t nt = grid_threads(pr, nevt << hp.gshift, mode);
+  const HelLayout L = hel_layout(pr, kp, hp, nevt, mode, nt);
+  if (ws == nullptr || wsb < L.total) return MGX_ERR_WORKSPACE_TOO_SMALL;
   char* p = (char*)ws;
-  double* w_thr = (double*)p; p += t.ws;
-  float* jexp = (float*)p; p += t.jexp;
-  double* colw = (double*)p; p += t.colw;
-  double* mhb = (double*)p; p += t.mh;
-  int* err = (int*)p;
-  const size_t smem_tc = colour_tc_smem<F>(kpad, pr->tc_npad);
-  if (cudaFuncSetAttribute(colour_tc_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc) !=
-      cudaSuccess)
-    return MGX_ERR_CUDA;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, colour_tc_kernel<F>, kTcRows, smem_tc) != cudaSuccess ||
-      per_sm < 1)
-    return MGX_ERR_CUDA;
-  per_sm = std::min(per_sm, 512 / pr->tc_cols);   // tensor-memory columns of one SM
-  const int npar4 = 4 * kp.npar;
-  const size_t shm = (size_t)kThreads * npar4 * sizeof(double);
-  for (int64_t c0 = 0; c0 < nevt; c0 += t.chunk) {
-    const int64_t n = std::min(t.chunk, nevt - c0);
-    const int64_t nt = grid_threads(pr, n);
-    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return MGX_ERR_CUDA;
-    me_kernel<double, false><<<(unsigned)(nt / kThreads), kThreads, shm, st>>>(kp, n, mom + c0 * npar4, as + c0, nullptr, nullptr,
-                                                                me + c0, nullptr, nullptr, nullptr, nullptr, w_thr, nt,
-                                                                MGX_MIXED_TF32, jexp, colw);
-    const int64_t rows = 2 * n * kp.ngood;
-    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
-    const int64_t blocks = std::min<int64_t>(tiles, (int64_t)per_sm * sm_count(pr->device));
-    colour_tc_kernel<F><<<(unsigned)blocks, kTcRows, smem_tc, st>>>(jexp, rows, kp.ncol, kpad, pr->tc_npad,
-                                                                    (uint32_t)pr->tc_cols, bcanon,
-                                                                    1.0 / pr->prog->col_den, mhb, err);
-    finish_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-        kp, n, as + c0, rh ? rh + c0 : nullptr, rc ? rc + c0 : nullptr, mhb, colw, me + c0, sh ? sh + c0 : nullptr,
-        sc ? sc + c0 : nullptr, mh ? mh + c0 * kp.ngood : nullptr, cw ? cw + c0 * kp.ncol : nullptr);
-    tc_error_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(err, n, me + c0);
-    if (cudaGetLastError() != cudaSuccess) return MGX_ERR_CUDA;
-  }
-  return MGX_OK;
+  double* mh_buf = (double*)(p + L.ws);
+  double* cw_buf = (double*)(p + L.ws + L.mh);
+  const size_t shm = (size_t)kThreads * 4 * kp.npar * sizeof(double);
+  const unsigned blocks = (unsigned)(nt / kThreads);
+  if (mode == MGX_FLOAT)
+    me_hel_kernel<float><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, mom, as, mh_buf, cw_buf,
+                                                        (double*)ws, nt, mode);
+  else
+    me_hel_kernel<double><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, mom, as, mh_buf, cw_buf,
+                                                         (double*)ws, nt, mode);
+  finish_hel_kernel<<<(unsigned)((nevt + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+      kp, nevt, 1 << hp.gshift, mh_buf, cw_buf, rh, rc, me, sh, sc, mh, cw);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
 int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, const double* as,
@@ -843,6 +1045,9 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
   if (mode == MGX_MIXED_BF16X3)
     return launch_tc<TcBf16x3>(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, ws, wsb, st);
   if (use_cta_kernel(pr, kp, nevt, mode)) return launch_cta(pr, kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, st);
+  HelPlan hp;
+  if (use_hel_kernel(pr, kp, nevt, mode, &hp))
+    return launch_hel(pr, kp, hp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, mode, ws, wsb, st);
   if (use_smem_ws(pr, kp, nevt, mode)) {
     const size_t smem = smem_ws_block_bytes(kp, mode);
     auto kern = mode == MGX_FLOAT ? me_kernel<float, true> : me_kernel<double, true>;
@@ -850,7 +1055,7 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
       return MGX_ERR_CUDA;
     const int64_t blocks = std::min<int64_t>((nevt + kSmemThreads - 1) / kSmemThreads, sm_count(pr->device));
     kern<<<(unsigned)blocks, kSmemThreads, smem, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, nullptr,
-                                                       blocks * kSmemThreads, mode, nullptr, nullptr);
+                                                       blocks * kSmemThreads, mode);
     return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
   }
   const int64_t nt = grid_threads(pr, nevt, mode);
@@ -860,10 +1065,10 @@ int launch(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mom, 
   const size_t shm = (size_t)kThreads * 4 * kp.npar * sizeof(double);
   if (mode == MGX_FLOAT)
     me_kernel<float, false><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
-                                                    mode, nullptr, nullptr);
+                                                    mode);
   else
     me_kernel<double, false><<<blocks, kThreads, shm, st>>>(kp, nevt, mom, as, rh, rc, me, sh, sc, mh, cw, (double*)ws, nt,
-                                                     mode, nullptr, nullptr);
+                                                     mode);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
@@ -911,8 +1116,9 @@ void mgx_process_destroy(mgx_process* pr) {
   cudaFree(pr->d_col);
   cudaFree(pr->d_colf);
   cudaFree(pr->d_terms);
-  cudaFree(pr->d_bcanon);
-  cudaFree(pr->d_bcanon16);
+  cudaFree(pr->d_tc_b32);
+  cudaFree(pr->d_tc_b16);
+  cudaFree(pr->d_status);
   cudaFree(pr->d_cta_ops);
   cudaFree(pr->d_cta_flows);
   cudaFree(pr->d_cta_terms);
@@ -1018,30 +1224,44 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
     return MGX_ERR_CUDA;
   }
   if (ok) {
-    // integer-scaled colour matrix as canonical K-major tiles for the tensor-core colour sums
+    // integer-scaled colour matrix Cs = den C as canonical K-major tiles, one per 32-column K chunk
+    // (and per bf16 part), in the order the fused colour sum stages them
     pr->tc_kpad = (n + 7) / 8 * 8;
     pr->tc_kpad16 = (n + 15) / 16 * 16;
     pr->tc_npad = (n + 15) / 16 * 16;
     pr->tc_cols = 32;
     while (pr->tc_cols < pr->tc_npad) pr->tc_cols *= 2;
-    std::vector<float> bc((size_t)pr->tc_npad * pr->tc_kpad, 0.0f);
-    const size_t tile16 = (size_t)pr->tc_npad * pr->tc_kpad16;
-    std::vector<uint16_t> b16(2 * tile16, 0);
+    const int np = pr->tc_npad;
+    std::vector<float> b32;
+    std::vector<uint16_t> b16;
     pr->bf16_exact = true;
-    for (int r = 0; r < n; ++r)
-      for (int k = 0; k < n; ++k) {
-        const float c = (float)(prog->colour[r * n + k] * prog->col_den);
-        bc[umma::kmajor_offset(r, k, pr->tc_kpad, 4) / 4] = c;
-        const uint16_t h = bf16_bits(c), l = bf16_bits(c - bf16_value(h));
-        pr->bf16_exact = pr->bf16_exact && bf16_value(h) + bf16_value(l) == c;
-        const size_t o = umma::kmajor_offset(r, k, pr->tc_kpad16, 2) / 2;
-        b16[o] = h;
-        b16[tile16 + o] = l;
-      }
-    ok = cudaMalloc(&pr->d_bcanon, sizeof(float) * bc.size()) == cudaSuccess &&
-         cudaMemcpy(pr->d_bcanon, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMalloc(&pr->d_bcanon16, sizeof(uint16_t) * b16.size()) == cudaSuccess &&
-         cudaMemcpy(pr->d_bcanon16, b16.data(), sizeof(uint16_t) * b16.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int k0 = 0; k0 < pr->tc_kpad; k0 += kTcKc) {
+      const int kc = std::min(kTcKc, pr->tc_kpad - k0);
+      const size_t o = b32.size();
+      b32.resize(o + (size_t)np * kc, 0.0f);
+      for (int r = 0; r < n; ++r)
+        for (int k = k0; k < std::min(n, k0 + kc); ++k)
+          b32[o + umma::kmajor_offset(r, k - k0, kc, 4) / 4] = (float)(prog->colour[r * n + k] * prog->col_den);
+    }
+    for (int k0 = 0; k0 < pr->tc_kpad16; k0 += kTcKc) {
+      const int kc = std::min(kTcKc, pr->tc_kpad16 - k0);
+      const size_t o = b16.size(), tile = (size_t)np * kc;
+      b16.resize(o + 2 * tile, 0);
+      for (int r = 0; r < n; ++r)
+        for (int k = k0; k < std::min(n, k0 + kc); ++k) {
+          const float c = (float)(prog->colour[r * n + k] * prog->col_den);
+          const uint16_t h = bf16_bits(c), l = bf16_bits(c - bf16_value(h));
+          pr->bf16_exact = pr->bf16_exact && bf16_value(h) + bf16_value(l) == c;
+          const size_t off = umma::kmajor_offset(r, k - k0, kc, 2) / 2;
+          b16[o + off] = h;
+          b16[o + tile + off] = l;
+        }
+    }
+    ok = cudaMalloc(&pr->d_tc_b32, sizeof(float) * b32.size()) == cudaSuccess &&
+         cudaMemcpy(pr->d_tc_b32, b32.data(), sizeof(float) * b32.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMalloc(&pr->d_tc_b16, sizeof(uint16_t) * b16.size()) == cudaSuccess &&
+         cudaMemcpy(pr->d_tc_b16, b16.data(), sizeof(uint16_t) * b16.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMalloc(&pr->d_status, 256) == cudaSuccess && cudaMemset(pr->d_status, 0, 256) == cudaSuccess;
   }
   if (!ok) {
     mgx_process_destroy(pr);
@@ -1136,7 +1356,12 @@ int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* b
   if (!pr || !bytes || nevt < 0) return MGX_ERR_INVALID_ARGUMENT;
   if (!mode_ok(mode)) return MGX_ERR_UNSUPPORTED_MODE;
   if (mode_tc(mode)) {
-    *bytes = nevt == 0 ? 0 : tc_plan(pr, pr->kp, nevt).total;
+    *bytes = nevt == 0 ? 0 : (size_t)grid_threads(pr, nevt) * thread_ws_bytes(pr->kp, MGX_FP64);
+    return MGX_OK;
+  }
+  HelPlan hp;
+  if (nevt > 0 && use_hel_kernel(pr, pr->kp, nevt, mode, &hp)) {
+    *bytes = hel_layout(pr, pr->kp, hp, nevt, mode, grid_threads(pr, nevt << hp.gshift, mode)).total;
     return MGX_OK;
   }
   *bytes = (nevt == 0 || use_cta_kernel(pr, pr->kp, nevt, mode) || use_smem_ws(pr, pr->kp, nevt, mode))
@@ -1218,7 +1443,7 @@ int mgx_compute_host(mgx_process* pr, int64_t nevt, const double* momenta, const
 }
 
 int mgx_process_set_kernel(mgx_process* pr, int kernel) {
-  if (!pr || kernel < MGX_KERNEL_AUTO || kernel > MGX_KERNEL_THREAD_SMEM) return MGX_ERR_INVALID_ARGUMENT;
+  if (!pr || kernel < MGX_KERNEL_AUTO || kernel > MGX_KERNEL_HELICITY) return MGX_ERR_INVALID_ARGUMENT;
   if (kernel == MGX_KERNEL_CTA && !cta_usable(pr, pr->kp)) return MGX_ERR_INVALID_ARGUMENT;
   if (kernel == MGX_KERNEL_THREAD_SMEM && !smem_usable(pr->kp, MGX_FP64)) return MGX_ERR_INVALID_ARGUMENT;
   pr->kernel = kernel;
@@ -1228,7 +1453,25 @@ int mgx_process_set_kernel(mgx_process* pr, int kernel) {
 int mgx_process_get_kernel(const mgx_process* pr) {
   if (!pr) return MGX_ERR_INVALID_ARGUMENT;
   if (use_cta(pr, pr->kp)) return MGX_KERNEL_CTA;
+  if (pr->kernel == MGX_KERNEL_HELICITY) return MGX_KERNEL_HELICITY;
   return pr->kernel == MGX_KERNEL_THREAD_SMEM ? MGX_KERNEL_THREAD_SMEM : MGX_KERNEL_THREAD;
+}
+
+int mgx_process_device_errors(mgx_process* pr, int* count, int reset) {
+  if (!pr || !count) return MGX_ERR_INVALID_ARGUMENT;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return MGX_ERR_CUDA;
+  if (cur != pr->device) return MGX_ERR_DEVICE_MISMATCH;
+  if (cudaMemcpy(count, pr->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MGX_ERR_CUDA;
+  if (reset && cudaMemset(pr->d_status, 0, sizeof(int)) != cudaSuccess) return MGX_ERR_CUDA;
+  return MGX_OK;
+}
+
+int mgx_process_set_tc_wait_test(mgx_process* pr, int skip_mma, double wait_ms) {
+  if (!pr || wait_ms <= 0.0 || wait_ms > 10000.0) return MGX_ERR_INVALID_ARGUMENT;
+  pr->tc_skip_mma = skip_mma ? 1 : 0;
+  pr->tc_wait_ns = (unsigned long long)(wait_ms * 1e6);
+  return MGX_OK;
 }
 
 int mgx_process_set_blocks_per_sm(mgx_process* pr, int blocks_per_sm) {
@@ -1259,7 +1502,8 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
   t += w(vvv_dot) * c[13] + w(vvvv_dot) * c[14];   // per-event child dot tables of VVV / VVVV
   t += w(slash) * c[15] + w(slash_pref) * c[16];  // per-event slash blocks of f f V vertices
   if (mode == MGX_FP64) t += ngood * (flops ? 2 * n * n + 4 * n : n * n + 3 * n);  // quadratic form
-  else if (!flops) t += ngood * 2 * n;                                              // f64 -> f32 conversions
+  else if (!flops) t += ngood * (mode_tc(mode) ? 4 * n : 2 * n);  // f64 -> f32 conversions (the tensor-core
+                                                                   // colour sum converts for the stage and the dot)
   t += ngood * (flops ? 4 * n : 2 * n);                                             // colour weights
   return t;
 }
@@ -1267,9 +1511,8 @@ static double fp64_work(const mgx_process* pr, int mode, bool flops) {
 int mgx_kernel_launches(const mgx_process* pr, int64_t nevt, int mode) {
   if (!pr || nevt < 0 || !mode_ok(mode)) return -1;
   if (nevt == 0) return 0;
-  if (!mode_tc(mode)) return 1;
-  const int64_t chunk = tc_plan(pr, pr->kp, nevt).chunk;
-  return (int)(4 * ((nevt + chunk - 1) / chunk));   // amplitudes, colour sum, finish, error mark
+  HelPlan hp;
+  return use_hel_kernel(pr, pr->kp, nevt, mode, &hp) ? 2 : 1;   // the helicity-parallel kernel and its finish
 }
 
 double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) { return pr ? fp64_work(pr, mode, false) : 0.0; }
@@ -1462,6 +1705,7 @@ extern "C" int mgx_process_autotune(mgx_process* pr, int64_t nevt, const double*
   std::vector<Cand> cands = {{MGX_KERNEL_THREAD, 2}, {MGX_KERNEL_THREAD, 4}};
   if (cta_usable(pr, pr->kp) && mode_f64(mode)) cands.push_back({MGX_KERNEL_CTA, 4});
   if (smem_usable(pr->kp, mode)) cands.push_back({MGX_KERNEL_THREAD_SMEM, 4});
+  if (mode_f64(mode) || mode == MGX_FLOAT) cands.push_back({MGX_KERNEL_HELICITY, 4});
   const int save_k = pr->kernel, save_b = pr->blocks_per_sm;
   float best = 1e30f;
   Cand pick{save_k, save_b};
@@ -1549,8 +1793,7 @@ extern "C" int mgx_compute_noalloc(mgx_process* pr, int64_t nevt, const double* 
   const int64_t nt = blocks * kThreads;
   const size_t shm = (size_t)kThreads * 4 * pr->kp.npar * sizeof(double);
   me_kernel<double, false><<<(unsigned)blocks, kThreads, shm, (cudaStream_t)stream>>>(
-      pr->kp, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, scratch, nt, mode,
-      nullptr, nullptr);
+      pr->kp, nevt, momenta, alpha_s, rnd_hel, rnd_col, me, selhel, selcol, nullptr, nullptr, scratch, nt, mode);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 

@@ -25,6 +25,23 @@ __device__ __forceinline__ Op load_op(const int4* ops, int i) {
   return Op{x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, z.x, z.y, z.z, z.w, w.x, w.y, w.z, w.w};
 }
 
+// Which helicity variants a thread computes.  AllHel: every variant of every current (one thread
+// per event).  GroupHel: the helicity-parallel mapping, in which the 2^|fix| threads of one event
+// each take the helicities whose bits on the fixed legs (mask fix, in the helicity-index bit
+// positions) equal `bits`: a thread computes only the variants of each current that such a
+// helicity uses, and only those helicities' amplitudes.  Variants keep their full-size slots.
+struct AllHel {
+  __device__ __forceinline__ int count(int m) const { return 1 << __popc(m); }   // variants of leg mask m
+  __device__ __forceinline__ int var(int u, int) const { return u; }             // u-th of them
+  __device__ __forceinline__ bool ok(int) const { return true; }                 // helicity h taken
+};
+struct GroupHel {
+  int fix, bits;
+  __device__ __forceinline__ int count(int m) const { return 1 << __popc(m & ~fix); }
+  __device__ __forceinline__ int var(int u, int m) const;
+  __device__ __forceinline__ bool ok(int h) const { return (h & fix) == bits; }
+};
+
 // Shared-memory storage view (contiguous 8-byte slots).
 template <class R>
 struct SST {
@@ -122,25 +139,29 @@ __device__ __forceinline__ SlashT<R> load_slash(const S& W, int off) {
   s.a01 = cneg(sl[2]); s.a10 = cneg(sl[3]); s.b01 = sl[2]; s.b10 = sl[3];
   return s;
 }
-// slash blocks of every variant of child b (the vector) into the header from offset 6
-template <class R, class S>
-__device__ __forceinline__ void header_slashes(const Op& o, const S& W) {
-  const int nv = 1 << __popc(o.mb);
-  for (int i = 0; i < nv; ++i) {
+// slash blocks of every (taken) variant of child b (the vector) into the header from offset 6
+template <class R, class S, class H>
+__device__ __forceinline__ void header_slashes(const Op& o, const S& W, const H& hs) {
+  const int nv = hs.count(o.mb);
+  for (int u = 0; u < nv; ++u) {
+    const int i = hs.var(u, o.mb);
     cxT<R> V[4];
     W.load4(o.vb + 8 * i, V);
     store_slash<R>(W, o.dst + 6 + 8 * i, V);
   }
 }
-template <class R, class S>
-__device__ __forceinline__ void header_slashes(const Op& o, const S& W, cxT<R> pref) {
-  const int nv = 1 << __popc(o.mb);
-  for (int i = 0; i < nv; ++i) {
+template <class R, class S, class H>
+__device__ __forceinline__ void header_slashes(const Op& o, const S& W, cxT<R> pref, const H& hs) {
+  const int nv = hs.count(o.mb);
+  for (int u = 0; u < nv; ++u) {
+    const int i = hs.var(u, o.mb);
     cxT<R> V[4];
     W.load4(o.vb + 8 * i, V);
     store_slash<R>(W, o.dst + 6 + 8 * i, V, pref);
   }
 }
+
+__device__ __forceinline__ int GroupHel::var(int u, int m) const { return pext(pdep(u, m & ~fix) | (bits & m), m); }
 
 // VVVV colour structure j needs the dot products of two child pairs (children 0, 1, 2 = e1, e2, e3):
 // j = 0: (e1.e3, e2.e3), j = 1: (e1.e2, e2.e3), j = 2: (e1.e2, e1.e3)
@@ -156,8 +177,9 @@ __device__ __forceinline__ int child_mask(const Op& o, int k) { return k == 0 ? 
 __device__ __forceinline__ int nvar_of(int mask) { return 1 << __popc(mask); }
 
 // ================================================================ headers
-template <class R, class S>
-__device__ inline void op_header(const KParams& P, const Op& o, double gs, const double* pe, const S& W) {
+template <class R, class S, class H = AllHel>
+__device__ inline void op_header(const KParams& P, const Op& o, double gs, const double* pe, const S& W,
+                                 const H& hs = H()) {
   using T = Real<R>;
   if (o.code == OP_SUM) return;   // no header
   if (o.code == OP_EXT) {
@@ -174,7 +196,7 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
     coupling<R>(P, o.cpl, gs, cl, cr, chiral);
     W[o.dst + 4] = chiral ? T::from(1.0) : cl.r;
     W[o.dst + 5] = chiral ? T::from(0.0) : cl.i;
-    if (o.code == OP_RBIL) header_slashes<R>(o, W);
+    if (o.code == OP_RBIL) header_slashes<R>(o, W, hs);
     return;
   }
   R ka[4], kb[4], k[4];
@@ -197,12 +219,15 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
 #pragma unroll 1
     for (int tab = 0; tab < 2; ++tab) {
       const int x = tab ? x1 : x0, y = tab ? y1 : y0;
-      const int nx = nvar_of(child_mask(o, x)), ny = nvar_of(child_mask(o, y));
+      const int mx = child_mask(o, x), my = child_mask(o, y);
+      const int nx = nvar_of(mx), ny = nvar_of(my);
       const R f = tab ? -sv : sv;
-      for (int iy = 0; iy < ny; ++iy) {
+      for (int uy = 0; uy < hs.count(my); ++uy) {
+        const int iy = hs.var(uy, my);
         cxT<R> ey[4];
         W.load4(child_base(o, y) + 8 * iy, ey);
-        for (int ix = 0; ix < nx; ++ix) {
+        for (int ux = 0; ux < hs.count(mx); ++ux) {
+          const int ix = hs.var(ux, mx);
           cxT<R> ex[4];
           W.load4(child_base(o, x) + 8 * ix, ex);
           const cxT<R> d = rmul(f, mdot(ex, ey));
@@ -229,15 +254,17 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
     W.storek(o.dst + 10, q1);
     W.storek(o.dst + 14, q2);
     // per child variant: a1 = q1 . e1 and a2 = q2 . e2 (each depends on one child only)
-    const int n1 = nvar_of(o.ma), n2 = nvar_of(o.mb);
-    for (int v1 = 0; v1 < n1; ++v1) {
+    const int n1 = nvar_of(o.ma);
+    for (int u1 = 0; u1 < hs.count(o.ma); ++u1) {
+      const int v1 = hs.var(u1, o.ma);
       cxT<R> e[4];
       W.load4(o.va + 8 * v1, e);
       const cxT<R> a = rdot(q1, e);
       W[o.dst + 18 + 2 * v1] = a.r;
       W[o.dst + 18 + 2 * v1 + 1] = a.i;
     }
-    for (int v2 = 0; v2 < n2; ++v2) {
+    for (int u2 = 0; u2 < hs.count(o.mb); ++u2) {
+      const int v2 = hs.var(u2, o.mb);
       cxT<R> e[4];
       W.load4(o.vb + 8 * v2, e);
       const cxT<R> a = rdot(q2, e);
@@ -259,7 +286,7 @@ __device__ inline void op_header(const KParams& P, const Op& o, double gs, const
     W[o.dst + 4] = pref.r;
     W[o.dst + 5] = pref.i;
   } else {
-    header_slashes<R>(o, W, pref);
+    header_slashes<R>(o, W, pref, hs);
   }
 }
 
@@ -546,22 +573,26 @@ __device__ inline void op_variant(const KParams& P, const Op& o, int v, double g
 }
 
 // all nv variants of one op (the thread-per-event kernel): per-op values loaded once
-template <class R, class S>
-__device__ inline void op_variants(const KParams& P, const Op& o, int nv, double gs, const double* pe, const S& W) {
+template <class R, class S, class H = AllHel>
+__device__ inline void op_variants(const KParams& P, const Op& o, double gs, const double* pe, const S& W,
+                                   const H& hs = H()) {
   if (std::is_same<R, float>::value && o.code == OP_VVV) {
     // variants as (first child variant, second child variant) pairs, first child loaded once
     // (float path only: in the float64 kernel the values kept live across the pairs cost spills
     // that outweigh the saved loads)
     R d[4];
     W.loadk(o.dst + 6, d);
-    const int n1 = nvar_of(o.ma), n2 = nvar_of(o.mb);
-    for (int i1 = 0; i1 < n1; ++i1) {
+    const int n1 = nvar_of(o.ma);
+    for (int u1 = 0; u1 < hs.count(o.ma); ++u1) {
+      const int i1 = hs.var(u1, o.ma);
       cxT<R> e1[4];
       W.load4(o.va + 8 * i1, e1);
       const cxT<R> a1 = {W[o.dst + 18 + 2 * i1], W[o.dst + 18 + 2 * i1 + 1]};
       const int h1 = pdep(i1, o.ma);
-      for (int i2 = 0; i2 < n2; ++i2)
+      for (int u2 = 0; u2 < hs.count(o.mb); ++u2) {
+        const int i2 = hs.var(u2, o.mb);
         var_vvv_pair<R>(o, pext(h1 | pdep(i2, o.mb), o.mdst), e1, a1, i2, d, n1, W);
+      }
     }
     return;
   }
@@ -570,12 +601,13 @@ __device__ inline void op_variants(const KParams& P, const Op& o, int nv, double
     // loaded once (the op's legs are the disjoint union of its children's)
     const bool row = o.code == OP_FFV_FB;
     const FfvCtx<R> c = ffv_ctx<R>(P, o, W, row);
-    const int na = nvar_of(o.ma), nb = nvar_of(o.mb);
-    for (int ia = 0; ia < na; ++ia) {
+    for (int ua = 0; ua < hs.count(o.ma); ++ua) {
+      const int ia = hs.var(ua, o.ma);
       cxT<R> psi[4];
       W.load4(o.va + 8 * ia, psi);
       const int ha = pdep(ia, o.ma);
-      for (int ib = 0; ib < nb; ++ib) {
+      for (int ub = 0; ub < hs.count(o.mb); ++ub) {
+        const int ib = hs.var(ub, o.mb);
         const int v = pext(ha | pdep(ib, o.mb), o.mdst);
         if (row)
           var_ffv_fb<R>(P, o, v, ib, psi, gs, c, W);
@@ -585,7 +617,7 @@ __device__ inline void op_variants(const KParams& P, const Op& o, int nv, double
     }
     return;
   }
-  for (int v = 0; v < nv; ++v) op_variant<R>(P, o, v, gs, pe, W);
+  for (int u = 0; u < hs.count(o.mdst); ++u) op_variant<R>(P, o, hs.var(u, o.mdst), gs, pe, W);
 }
 
 // ================================================================ diagram amplitudes

@@ -59,7 +59,9 @@ struct GemmArgs {
   __nv_bfloat16* houtT;
   int ldt;
   float* wout;
-  int* err;
+  int* err;                // device error counter: +1 per tile whose tensor-core wait ran out
+  int skip_mma;            // test hook: issue no MMA, so that the waits run out
+  unsigned long long wait_ns;
 };
 
 // One CTA computes C[m0 .. m0+127][n0 .. n0+NT) with NT = min(N - n0, 256) (multiple of 32).
@@ -106,12 +108,14 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
     __syncthreads();
     if (tid == 0) {
       umma::fence_after_sync();
-      for (int ks = 0; ks < kc / 16; ++ks)
-        umma::mma_f16(tmem, umma::smem_desc(saddr + ks * 256, 128, sbo), umma::smem_desc(sbaddr + ks * 256, 128, sbo),
-                      id, (k0 > 0 || ks > 0) ? 1u : 0u);
-      umma::mma_commit(mbar);
+      if (!g.skip_mma) {
+        for (int ks = 0; ks < kc / 16; ++ks)
+          umma::mma_f16(tmem, umma::smem_desc(saddr + ks * 256, 128, sbo),
+                        umma::smem_desc(sbaddr + ks * 256, 128, sbo), id, (k0 > 0 || ks > 0) ? 1u : 0u);
+        umma::mma_commit(mbar);
+      }
     }
-    const bool done = umma::mbar_wait(mbar, phase);
+    const bool done = umma::mbar_wait(mbar, phase, g.wait_ns);
     phase ^= 1;
     if (!__syncthreads_and(done)) {
       ok = false;
@@ -147,8 +151,27 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
       }
     }
   } else {
-    if (tid == 0 && g.err) atomicExch(g.err, 1);
-    umma::mbar_wait(mbar, phase ^ 1);
+    // the tile's outputs become NaN (never stale values), the error is counted, and the block waits
+    // (bounded) for MMAs still in flight before it frees its tensor memory
+    if (tid == 0 && g.err) atomicAdd(g.err, 1);
+    const int m = m0 + tid;
+    const float nan = __int_as_float(0x7fc00000);
+    if (m < g.M)
+      for (int c = 0; c < NT; ++c) {
+        const int n = n0 + c;
+        if (n >= g.N) break;
+        if (g.epi == EPI_FWD) {
+          g.zout[(size_t)m * g.N + n] = nan;
+          g.hout[(size_t)m * g.N + n] = __float2bfloat16_rn(nan);
+          g.houtT[(size_t)n * g.ldt + m] = __float2bfloat16_rn(nan);
+        } else if (g.epi == EPI_BWD) {
+          g.hout[(size_t)m * g.N + n] = __float2bfloat16_rn(nan);
+          g.houtT[(size_t)n * g.ldt + m] = __float2bfloat16_rn(nan);
+        } else {
+          g.wout[(size_t)m * g.N + n] = nan;
+        }
+      }
+    umma::mbar_wait(mbar, phase ^ 1, g.wait_ns);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -320,6 +343,9 @@ struct mgx_mlp {
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16 *wb = nullptr, *wbT = nullptr;
   int step = 0;
+  int* d_status = nullptr;                         // device error counter of the GEMM waits
+  int skip_mma = 0;                                // test hook
+  unsigned long long wait_ns = 1000000000ull;      // time limit of one tensor-core wait
 };
 
 namespace {
@@ -379,7 +405,8 @@ int forward(mgx_mlp* net, int n, const float* x, const MlpWs& w, cudaStream_t st
     g.B = net->wb + wb_offset(L, l); g.ldb = kin;
     g.M = n; g.N = kWidth; g.K = kin; g.epi = EPI_FWD;
     g.bias = net->p + L.off_b[l];
-    g.zout = w.z[l]; g.hout = w.h[l]; g.houtT = w.hT[l]; g.ldt = w.ldt; g.err = w.err;
+    g.zout = w.z[l]; g.hout = w.h[l]; g.houtT = w.hT[l]; g.ldt = w.ldt;
+    g.err = net->d_status; g.skip_mma = net->skip_mma; g.wait_ns = net->wait_ns;
     const int rc = gemm(g, st);
     if (rc != MGX_OK) return rc;
     in = w.h[l];
@@ -402,7 +429,8 @@ int backward(mgx_mlp* net, int n, const float* t, const MlpWs& w, cudaStream_t s
     gw.A = w.dzT[cur]; gw.lda = w.ldt;
     gw.B = l == 0 ? w.xT : w.hT[l - 1]; gw.ldb = w.ldt;
     gw.M = kWidth; gw.N = kin; gw.K = w.ldt; gw.epi = EPI_DW;
-    gw.wout = net->g + L.off_w[l]; gw.err = w.err;
+    gw.wout = net->g + L.off_w[l];
+    gw.err = net->d_status; gw.skip_mma = net->skip_mma; gw.wait_ns = net->wait_ns;
     int rc = gemm(gw, st);
     if (rc != MGX_OK) return rc;
     colsum_kernel<<<(kWidth + 7) / 8, 256, 0, st>>>(kWidth, n, w.dzT[cur], w.ldt, net->g + L.off_b[l]);
@@ -412,7 +440,8 @@ int backward(mgx_mlp* net, int n, const float* t, const MlpWs& w, cudaStream_t s
     gb.A = w.dz[cur]; gb.lda = kWidth;
     gb.B = net->wbT + wb_offset(L, l); gb.ldb = kWidth;
     gb.M = n; gb.N = kin; gb.K = kWidth; gb.epi = EPI_BWD;
-    gb.zprev = w.z[l - 1]; gb.hout = w.dz[cur ^ 1]; gb.houtT = w.dzT[cur ^ 1]; gb.ldt = w.ldt; gb.err = w.err;
+    gb.zprev = w.z[l - 1]; gb.hout = w.dz[cur ^ 1]; gb.houtT = w.dzT[cur ^ 1]; gb.ldt = w.ldt;
+    gb.err = net->d_status; gb.skip_mma = net->skip_mma; gb.wait_ns = net->wait_ns;
     rc = gemm(gb, st);
     if (rc != MGX_OK) return rc;
     cur ^= 1;
@@ -447,7 +476,8 @@ int mgx_mlp_create(int device, uint64_t seed, mgx_mlp** out) {
             cudaMalloc(&net->m, sizeof(float) * total) == cudaSuccess &&
             cudaMalloc(&net->v, sizeof(float) * total) == cudaSuccess &&
             cudaMalloc(&net->wb, sizeof(__nv_bfloat16) * nwb) == cudaSuccess &&
-            cudaMalloc(&net->wbT, sizeof(__nv_bfloat16) * nwb) == cudaSuccess;
+            cudaMalloc(&net->wbT, sizeof(__nv_bfloat16) * nwb) == cudaSuccess &&
+            cudaMalloc(&net->d_status, 256) == cudaSuccess && cudaMemset(net->d_status, 0, 256) == cudaSuccess;
   // He-uniform initialisation from a seeded 64-bit LCG (weights of padded input columns zero)
   std::vector<float> h(total, 0.0f);
   uint64_t s = seed * 6364136223846793005ull + 1442695040888963407ull;
@@ -481,7 +511,7 @@ int mgx_mlp_create(int device, uint64_t seed, mgx_mlp** out) {
 void mgx_mlp_destroy(mgx_mlp* net) {
   if (!net) return;
   cudaFree(net->p); cudaFree(net->g); cudaFree(net->m); cudaFree(net->v);
-  cudaFree(net->wb); cudaFree(net->wbT);
+  cudaFree(net->wb); cudaFree(net->wbT); cudaFree(net->d_status);
   delete net;
 }
 
@@ -565,6 +595,20 @@ int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, floa
   const int rc = mgx_mlp_gradients(net, n, x, t, nullptr, loss, ws, wsb, stream);
   if (rc != MGX_OK) return rc;
   return adam_step(net, net->g, lr, (cudaStream_t)stream);
+}
+
+int mgx_mlp_device_errors(mgx_mlp* net, int* count, int reset) {
+  if (!net || !count) return MGX_ERR_INVALID_ARGUMENT;
+  if (cudaMemcpy(count, net->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MGX_ERR_CUDA;
+  if (reset && cudaMemset(net->d_status, 0, sizeof(int)) != cudaSuccess) return MGX_ERR_CUDA;
+  return MGX_OK;
+}
+
+int mgx_mlp_set_wait_test(mgx_mlp* net, int skip_mma, double wait_ms) {
+  if (!net || wait_ms <= 0.0 || wait_ms > 10000.0) return MGX_ERR_INVALID_ARGUMENT;
+  net->skip_mma = skip_mma ? 1 : 0;
+  net->wait_ns = (unsigned long long)(wait_ms * 1e6);
+  return MGX_OK;
 }
 
 int mgx_mlp_adam_step(mgx_mlp* net, const float* grad, float lr, void* stream) {

@@ -237,6 +237,41 @@ class Emulator:
         self.mass = [(PARAMS[m], PARAMS[w]) for m, w in P.masses]
         self.C = np.array([[float(x) for x in row] for row in P.colour])
         self.nhel = 1 << P.npar
+        self.fix, self.bits = 0, 0    # helicity-parallel group: helicity bits `bits` on the legs `fix`
+
+    def _allowed(self, mask):
+        """Variants of a current with leg mask `mask` that the current group computes (all of them
+        without a group)."""
+        free = mask & ~self.fix
+        return [pext(pdep(u, free) | (self.bits & mask), mask) for u in range(nvar(free))]
+
+    def evaluate_groups(self, mom, alpha_s, fix, rnd_hel=None, rnd_col=None):
+        """The helicity-parallel program: for each of the 2^|fix| groups (helicity bits on the legs in
+        `fix`), a fresh NaN workspace in which only the group's current variants, header tables and
+        helicity amplitudes are computed; the jamps of each helicity come from its group.  A variant
+        or table read that the group did not compute makes the result NaN."""
+        P = self.P
+        nevt = mom.shape[0]
+        pe = np.transpose(mom, (1, 2, 0))
+        self.terms, self.flows = P.terms, P.flows
+        self.count = Counter()
+        out = np.full((self.nhel, P.ncol, nevt), np.nan + 0j)
+        k = bin(fix).count("1")
+        for g in range(1 << k):
+            self.fix, self.bits = fix, pdep(g, fix)
+            W = Workspace(P.ws_current_doubles, nevt)
+            jamps = np.zeros((self.nhel, P.ncol, nevt), complex) if P.jamp_zero else \
+                np.full((self.nhel, P.ncol, nevt), np.nan + 0j)
+            for op in P.ops:
+                if op[0] == OP_AMP:
+                    self._amp(op, W, jamps)
+                else:
+                    self._header(op, W, pe)
+                    self._variants(op, W, pe)
+            mine = [h for h in range(self.nhel) if h & fix == self.bits]
+            out[mine] = jamps[mine]
+        self.fix, self.bits = 0, 0
+        return self._finish(out, alpha_s, rnd_hel, rnd_col)
 
     def evaluate(self, mom, alpha_s, rnd_hel=None, rnd_col=None):
         """me [nevt], per-helicity |M_h|^2 [nevt, nhel] and colour weights [nevt, ncol] for momenta
@@ -313,9 +348,9 @@ class Emulator:
             cl, cr, chiral = self.cpl[op[9]]
             W.set_cx(dst + 4, np.full(W.w.shape[1], 1.0 if chiral else cl))
             if code == OP_RBIL:
-                nv = nvar(op[7])
-                W.set_vec(dst + 6, np.arange(nv), _slash(W.vec(op[14], np.arange(nv))))
-                self.count["slash_hdr"] += nv
+                iv = self._allowed(op[7])
+                W.set_vec(dst + 6, iv, _slash(W.vec(op[14], iv)))
+                self.count["slash_hdr"] += len(iv)
             return
         k = W.k(op[2]) + W.k(op[3])
         if code == OP_VVVV:
@@ -326,14 +361,15 @@ class Emulator:
             base = dst + 6
             for tab, (x, y) in enumerate(self._vvvv_pairs(op[11])):
                 nx, ny = nvar(op[6 + x]), nvar(op[6 + y])
-                ex = W.vec(op[13 + x], np.arange(nx))
-                ey = W.vec(op[13 + y], np.arange(ny))
-                d = (-sv if tab else sv) * _mdot(ex[:, None], ey[None, :])     # [nx, ny, nevt]
-                for iy in range(ny):
-                    for ix in range(nx):
-                        W.set_cx(base + 2 * (ix + nx * iy), d[ix, iy])
+                ax, ay = self._allowed(op[6 + x]), self._allowed(op[6 + y])
+                ex = W.vec(op[13 + x], ax)
+                ey = W.vec(op[13 + y], ay)
+                d = (-sv if tab else sv) * _mdot(ex[:, None], ey[None, :])     # [len ax, len ay, nevt]
+                for jy, iy in enumerate(ay):
+                    for jx, ix in enumerate(ax):
+                        W.set_cx(base + 2 * (ix + nx * iy), d[jx, jy])
                 base += 2 * nx * ny
-                self.count["vvvv_hdr"] += nx * ny
+                self.count["vvvv_hdr"] += len(ax) * len(ay)
             return
         W.set_k(dst, k)
         k2 = np.einsum("m,me->e", METRIC, k * k)
@@ -345,15 +381,16 @@ class Emulator:
             q2 = -s * (2 * ka + kb)                          # s (k3 - k1)
             W.set_k(dst + 10, q1)
             W.set_k(dst + 14, q2)
-            n1, n2 = nvar(op[6]), nvar(op[7])
-            e1, e2 = W.vec(op[13], np.arange(n1)), W.vec(op[14], np.arange(n2))
+            n1 = nvar(op[6])
+            i1, i2 = self._allowed(op[6]), self._allowed(op[7])
+            e1, e2 = W.vec(op[13], i1), W.vec(op[14], i2)
             a1 = np.einsum("m,me,vme->ve", METRIC, q1, e1)
             a2 = np.einsum("m,me,vme->ve", METRIC, q2, e2)
-            for v in range(n1):
-                W.set_cx(dst + 18 + 2 * v, a1[v])
-            for v in range(n2):
-                W.set_cx(dst + 18 + 2 * (n1 + v), a2[v])
-            self.count["vvv_hdr"] += n1 + n2
+            for j, v in enumerate(i1):
+                W.set_cx(dst + 18 + 2 * v, a1[j])
+            for j, v in enumerate(i2):
+                W.set_cx(dst + 18 + 2 * (n1 + v), a2[j])
+            self.count["vvv_hdr"] += len(i1) + len(i2)
             return
         m, w = self.mass[op[10]]
         inv = 1.0 / (k2 - m * m + 1j * m * w)
@@ -364,10 +401,10 @@ class Emulator:
         if code == OP_FFV_V:
             W.set_cx(dst + 4, pref)
         else:
-            nv = nvar(op[7])
-            W.set_vec(dst + 6, np.arange(nv), pref * _slash(W.vec(op[14], np.arange(nv))))
-            self.count["slash_hdr"] += nv
-            self.count["slash_pref_hdr"] += nv
+            iv = self._allowed(op[7])
+            W.set_vec(dst + 6, iv, pref * _slash(W.vec(op[14], iv)))
+            self.count["slash_hdr"] += len(iv)
+            self.count["slash_pref_hdr"] += len(iv)
 
     @staticmethod
     def _vvvv_pairs(j):
@@ -378,7 +415,7 @@ class Emulator:
     def _variants(self, op, W, pe, vs=None):
         """Variants vs (default: all) of one op."""
         code, dst, mdst = op[0], op[1], op[5]
-        v = np.arange(nvar(mdst)) if vs is None else np.asarray(vs)
+        v = np.asarray(self._allowed(mdst)) if vs is None else np.asarray(vs)
         hb = [pdep(x, mdst) for x in v]
         if code in NAME:
             self.count["var_" + NAME[code]] += len(v)
@@ -499,7 +536,7 @@ class Emulator:
         """Group amplitude for every helicity: runs of terms sharing a bilinear X, the phased
         other operands summed and closed with one product; then added to the group's flows (a
         flow's first update writes, in the thread-per-event program)."""
-        h = np.arange(self.nhel)
+        h = np.array([x for x in range(self.nhel) if x & self.fix == self.bits])
         acc = 0
         s = None
         self.count.update(amp=1, amp_terms=op[12], amp_flows=op[10])
@@ -514,4 +551,4 @@ class Emulator:
         for f in range(op[10]):
             flow, code = self.flows[2 * (op[9] + f):2 * (op[9] + f) + 2]
             j = PHASE[code & 3] * acc
-            jamps[:, flow] = j if first_writes and code & FLOW_FIRST else jamps[:, flow] + j
+            jamps[h, flow] = j if first_writes and code & FLOW_FIRST else jamps[h, flow] + j

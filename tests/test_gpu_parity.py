@@ -38,7 +38,7 @@ def _run(proc, mom, a, rh, rc, mode=0):
 
 
 CASES = [("eemumu", 300), ("ggtt", 300), ("ggttg", 260), ("ggttgg", 160), ("ggttggg", 20), ("gu_tataggu", 140)]
-KERNELS = {"auto": 0, "thread": 1, "cta": 2, "smem": 3}
+KERNELS = {"auto": 0, "thread": 1, "cta": 2, "smem": 3, "helicity": 4}
 SMEM_PROCESSES = ("eemumu", "ggtt")        # per-thread workspace small enough for shared memory
 
 
@@ -47,13 +47,13 @@ _refs = {}
 
 def _oracle(process, mom, a, rh, rc):
     """The oracle's outputs for one seeded sample, computed once per (process, sample size)."""
-    key = (process, mom.shape[0])
+    key = (process, mom.shape[0], hash(mom.tobytes()), hash(a.tobytes()), hash(rh.tobytes()), hash(rc.tobytes()))
     if key not in _refs:
         _refs[key] = oracle_get(process).evaluate(mom, a, rh, rc)
     return _refs[key]
 
 
-@pytest.mark.parametrize("kernel", ["auto", "thread", "cta", "smem"])
+@pytest.mark.parametrize("kernel", ["auto", "thread", "cta", "smem", "helicity"])
 @pytest.mark.parametrize("name,nevt", CASES)
 def test_parity_fp64(name, nevt, kernel):
     wl = WORKLOADS[name]
@@ -98,7 +98,7 @@ def _check_fp64(proc, wl, mom, a, rh, rc, got, what):
     return ref
 
 
-@pytest.mark.parametrize("kernel", ["auto", "thread", "cta"])
+@pytest.mark.parametrize("kernel", ["auto", "thread", "cta", "helicity"])
 @pytest.mark.parametrize("name,nevt", [("ggttg", 200), ("ggttgg", 120), ("gu_tataggu", 100)])
 def test_parity_per_event_alpha_s(name, nevt, kernel):
     """alpha_s drawn per event in [0.08, 0.2): the per-event coupling (4 pi alpha_s)^p of each event
@@ -141,7 +141,7 @@ MODE_CASES = [("eemumu", 64, 1e-5), ("ggtt", 300, 1e-5), ("ggttg", 200, 1e-5), (
               ("ggttggg", 12, 1e-5), ("gu_tataggu", 140, 1e-5)]
 
 
-@pytest.mark.parametrize("kernel", ["thread", "cta"])
+@pytest.mark.parametrize("kernel", ["thread", "cta", "helicity"])
 @pytest.mark.parametrize("name,nevt,bound", MODE_CASES)
 def test_parity_mixed_fp32_colour_sum(name, nevt, bound, kernel):
     """Float64 amplitudes, float32 colour sum: me, every |M_h|^2 and the helicity selection at the
@@ -201,7 +201,7 @@ FLOAT_CASES = [("eemumu", 300, 1e-4), ("ggtt", 300, 1e-4), ("ggttg", 260, 1e-4),
                ("ggttggg", 20, 1e-4), ("gu_tataggu", 140, 1e-2)]
 
 
-@pytest.mark.parametrize("kernel", ["thread", "cta", "smem"])
+@pytest.mark.parametrize("kernel", ["thread", "cta", "smem", "helicity"])
 @pytest.mark.parametrize("name,nevt,bound", FLOAT_CASES)
 def test_parity_float_mode(name, nevt, bound, kernel):
     """Float32 path: me within the stated bound; |M_h|^2 and colour weights relative to the event total too."""
@@ -212,7 +212,7 @@ def test_parity_float_mode(name, nevt, bound, kernel):
         pytest.skip("g g > t t~ g g g: no CTA kernel to select")
     if kernel == "smem" and name not in SMEM_PROCESSES:
         pytest.skip("per-thread workspace too large for the shared-memory kernel")
-    proc.set_kernel(KERNELS[kernel])   # the float path always runs the thread-per-event kernel
+    proc.set_kernel(KERNELS[kernel])   # the float path runs the thread-per-event or helicity-parallel kernel
     try:
         got = _run(proc, mom, a, rh, rc, mode=4)
     finally:
@@ -353,3 +353,30 @@ def test_host_buffer_entry_point():
     dev = _run(proc, mom, a, rh, rc)
     assert np.array_equal(me.numpy(), dev["me"])
     assert np.array_equal(sh.numpy(), dev["selhel"]) and np.array_equal(sc.numpy(), dev["selcol"])
+
+
+def test_helicity_kernel_many_passes_and_auto():
+    """The helicity-parallel kernel over several passes of its grid (a batch larger than the grid
+    holds items) equals the thread kernel; AUTO picks it for a mid-size batch of g g > t t~ g g g
+    (which has no block-per-event schedule), and the thread kernel for a full batch."""
+    import torch
+    import paper_2503_21935_gb300 as pkg
+    wl = WORKLOADS["ggttg"]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 2 * sms * 4 * 128 + 77
+    mom, a, rh, rc = make_inputs(wl, n)
+    proc = _proc(wl.process)
+    proc.set_kernel(4)
+    try:
+        assert proc.kernel == 4 and proc.kernel_launches(n) == 2
+        hp = _run(proc, mom, a, rh, rc)
+    finally:
+        proc.set_kernel(1)
+    try:
+        th = _run(proc, mom, a, rh, rc)
+    finally:
+        proc.set_kernel(0)
+    assert np.abs(hp["me"] / th["me"] - 1.0).max() <= TOL
+    assert np.array_equal(hp["selhel"], th["selhel"]) and np.array_equal(hp["selcol"], th["selcol"])
+    big = _proc(WORKLOADS["ggttggg"].process)
+    assert big.kernel_launches(2000) == 2 and big.kernel_launches(1 << 20) == 1

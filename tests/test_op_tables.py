@@ -58,3 +58,20 @@ def test_work_counts_match_execution(name):
     for k in ("var_ffv_f", "var_ffv_fb", "var_ffv_v", "var_vvv", "var_vvvv", "var_bil", "var_rbil", "sum_adds",
               "vvv_hdr", "vvvv_hdr", "slash_hdr", "slash_pref_hdr", "amp", "amp_terms", "amp_runs", "amp_flows"):
         assert E.count[k] == c[k], (k, E.count[k], c[k])
+
+
+@pytest.mark.parametrize("name,nevt", [c for c in CASES if c[0] != "ggttggg"])
+def test_helicity_groups_match_oracle(name, nevt):
+    """The helicity-parallel program: per group of helicities (their bits on a set of fixed legs),
+    a fresh NaN workspace in which only that group's current variants, header tables and
+    amplitudes are computed.  Every single fixed leg and a seeded choice of larger leg sets must
+    reproduce the oracle, so no group reads a variant or table that only another group computes."""
+    wl = WORKLOADS[name]
+    mom, a, rh, rc = make_inputs(wl, nevt)
+    em = Emulator(wl.process)
+    npar = em.P.npar
+    rng = np.random.default_rng(len(name))
+    fixes = [1 << b for b in range(npar)]
+    fixes += sorted({int(x) for x in rng.integers(1, 1 << npar, size=4)})
+    for fix in fixes:
+        _check(wl, mom, a, rh, rc, em.evaluate_groups(mom, a, fix, rh, rc))
