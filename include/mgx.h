@@ -309,13 +309,21 @@ int mgx_mlp_num_params(void);
 int mgx_mlp_create(int device, uint64_t seed, mgx_mlp** out);
 void mgx_mlp_destroy(mgx_mlp* net);
 /* DEVICE workspace bytes for a training batch of n rows (training != 0, n <= 2^24) or for
- * inference over any n (processed in chunks of 65536 rows). */
+ * inference over any n (processed in passes of at most 2^22 rows, about 1.1 KB per row). */
 int mgx_mlp_workspace_bytes(int64_t n, int training, size_t* bytes);
 /* Host copies of the flat float32 parameter vector (set also refreshes the bfloat16 copies). */
 int mgx_mlp_get_params(const mgx_mlp* net, float* host);
 int mgx_mlp_set_params(mgx_mlp* net, const float* host);
-/* y[n] = network(x[n][24]); DEVICE arrays; asynchronous on stream. */
+/* y[n] = network(x[n][24]); DEVICE arrays; asynchronous on stream.  Inference runs one persistent
+ * tcgen05 kernel per layer: the layer's bf16 weights stay in shared memory, 128-row activation
+ * tiles stream through it by bulk copies, accumulate in tensor memory, and bias + SiLU (and, in the
+ * last layer, the 256 -> 1 output) are applied in the epilogue. */
 int mgx_mlp_forward(mgx_mlp* net, int64_t n, const float* x, float* y, void* ws, size_t wsb, void* stream);
+/* The same from float64 momenta [n][24] (an event's four-momenta in order), the network's inputs
+ * being float32(momenta / scale) (scale: sqrt(s)/2 for the surrogate), without a separate
+ * feature array. */
+int mgx_mlp_forward_momenta(mgx_mlp* net, int64_t n, const double* momenta, double scale, float* y, void* ws,
+                            size_t wsb, void* stream);
 /* Gradient of the mean squared error over one batch of n rows (targets t[n]) into grad
  * (DEVICE, num_params floats, may be NULL) and the loss into loss (DEVICE float, may be NULL). */
 int mgx_mlp_gradients(mgx_mlp* net, int n, const float* x, const float* t, float* grad, float* loss, void* ws,

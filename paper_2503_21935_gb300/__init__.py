@@ -93,6 +93,7 @@ def lib():
             "mgx_mlp_get_params": (I, [P, P]),
             "mgx_mlp_set_params": (I, [P, P]),
             "mgx_mlp_forward": (I, [P, I64, P, P, P, SZ, P]),
+            "mgx_mlp_forward_momenta": (I, [P, I64, P, D, P, P, SZ, P]),
             "mgx_mlp_gradients": (I, [P, I, P, P, P, P, P, SZ, P]),
             "mgx_mlp_train_step": (I, [P, I, P, P, ctypes.c_float, P, P, SZ, P]),
             "mgx_mlp_adam_step": (I, [P, P, ctypes.c_float, P]),
@@ -295,6 +296,16 @@ class Mlp:
         _check(lib().mgx_mlp_forward(self._h, n, _ptr(xd), _ptr(y), _ptr(ws), ws.numel(), _stream(xd.device)),
                "mgx_mlp_forward")
         return y.cpu().numpy() if host else y
+
+    def forward_momenta(self, momenta, scale, out=None):
+        """y[n] = network(float32(momenta / scale)) for device float64 momenta [n, 6, 4]."""
+        import torch
+        n = momenta.shape[0]
+        y = out if out is not None else torch.empty(n, dtype=torch.float32, device=momenta.device)
+        ws = self._workspace(n, False)
+        _check(lib().mgx_mlp_forward_momenta(self._h, n, _ptr(momenta), float(scale), _ptr(y), _ptr(ws), ws.numel(),
+                                             _stream(momenta.device)), "mgx_mlp_forward_momenta")
+        return y
 
     def gradients(self, x, t):
         import torch

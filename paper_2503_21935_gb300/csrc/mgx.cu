@@ -1298,7 +1298,11 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
   ok = ok && cudaMemcpy(d_mom, hmom.data(), sizeof(double) * hmom.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(d_as, as.data(), sizeof(double) * nf, cudaMemcpyHostToDevice) == cudaSuccess;
   int rc = MGX_OK;
+  // the filter evaluates every helicity with the whole-event thread kernel (the good-helicity list
+  // that the other kernels' choices depend on does not exist yet)
+  pr->kernel = MGX_KERNEL_THREAD;
   if (ok) rc = launch(pr, fk, nf, d_mom, d_as, nullptr, nullptr, d_me, nullptr, nullptr, d_mh, nullptr, MGX_FP64, d_ws, wsb, 0);
+  pr->kernel = MGX_KERNEL_AUTO;
   ok = ok && rc == MGX_OK && cudaMemcpy(mh.data(), d_mh, sizeof(double) * mh.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
   cudaFree(d_mom); cudaFree(d_as); cudaFree(d_me); cudaFree(d_mh); cudaFree(d_ws);
   if (!ok) {

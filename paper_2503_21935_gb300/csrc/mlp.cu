@@ -293,8 +293,9 @@ __global__ void adam_kernel(int total, float* __restrict__ p, const float* __res
 }
 
 __global__ void refresh_bf16_kernel(const float* __restrict__ p, ParamLayout L, __nv_bfloat16* __restrict__ wb,
-                                    __nv_bfloat16* __restrict__ wbT) {
-  // wb/wbT: per layer blocks of kWidth * kin[l] in the same order as the float weights
+                                    __nv_bfloat16* __restrict__ wbT, __nv_bfloat16* __restrict__ wc) {
+  // wb/wbT: per layer blocks of kWidth * kin[l] in the same order as the float weights; wc: the same
+  // blocks in the canonical K-major layout [256][kin] that the inference kernel reads from shared memory
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int base = 0;
   for (int l = 0; l < kDepth; ++l) {
@@ -304,9 +305,234 @@ __global__ void refresh_bf16_kernel(const float* __restrict__ p, ParamLayout L, 
       const __nv_bfloat16 v = __float2bfloat16_rn(p[L.off_w[l] + j]);
       wb[base + j] = v;
       wbT[base + (size_t)c * kWidth + r] = v;
+      wc[base + umma::kmajor_offset(r, c, L.kin[l], 2) / 2] = v;
       return;
     }
     base += sz;
+  }
+}
+
+// ---------------------------------------------------------------- inference
+// Activations between layers live in HBM as canonical K-major tiles: tile t (128 rows) of a K-wide
+// activation is K/kc chunks (kc = min(K, 64)) of 128 x kc bf16, each chunk contiguous in exactly the
+// layout tcgen05 reads from shared memory, so every operand load is one bulk copy.
+constexpr int kInfThreads = 192;   // warps 0-3: epilogue (tensor-memory lanes 0-127); 4: loads; 5: MMAs
+constexpr int kInfStages = 4;      // operand chunks in flight
+constexpr int64_t kInferRows = 1 << 22;   // rows per pass of the layer kernels (workspace ~1.1 KB / row)
+
+// x tiles [tile][128 x 32] (canonical, K = 32, columns 24..31 zero) from float32 rows x [n][24] or
+// from float64 momenta [n][24] scaled by inv_scale (rounded to float32 first, then to bf16)
+__global__ void pack_tiles_kernel(int64_t n, int64_t ntiles, const float* __restrict__ x, const double* __restrict__ mom,
+                                  double inv_scale, __nv_bfloat16* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntiles * kRows * (kK0 / 8)) return;
+  const int64_t row = i / (kK0 / 8);
+  const int grp = (int)(i % (kK0 / 8));
+  const int64_t tile = row / kRows;
+  const int r = (int)(row % kRows);
+  __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = grp * 8 + q;
+    float f = 0.0f;
+    if (row < n && c < kNin) f = mom ? (float)(mom[row * kNin + c] * inv_scale) : x[row * kNin + c];
+    v[q] = __float2bfloat16_rn(f);
+  }
+  *reinterpret_cast<uint4*>(out + tile * kRows * kK0 + umma::kmajor_offset(r, grp * 8, kK0, 2) / 2) =
+      *reinterpret_cast<const uint4*>(v);
+}
+
+struct InferArgs {
+  const __nv_bfloat16* a;   // input tiles (K columns)
+  const __nv_bfloat16* w;   // this layer's weights, canonical [256][K]
+  const float* bias;        // [256]
+  int K;                    // 32 or 256
+  int64_t ntiles, nrows;
+  __nv_bfloat16* h;         // middle layers: output tiles (256 columns); nullptr for the last layer
+  const float* w4;          // last layer: the output layer's weights [256] and bias
+  const float* b4;
+  float* y;                 // last layer: y [nrows]
+  int* err;                 // device error counter: +1 per block whose wait ran out
+  int skip_mma;             // test hook: issue no MMA, so that the waits run out
+  unsigned long long wait_ns;
+};
+
+size_t infer_smem(int K) {
+  const int kc = K < 64 ? K : 64;
+  return (size_t)kWidth * K * 2 + (size_t)kInfStages * kRows * kc * 2 + 2 * kWidth * 4 + 16 * 8 + 16;
+}
+
+// One hidden layer (+ the output layer when h == nullptr) over all tiles: a persistent block keeps
+// the layer's weights in shared memory, streams the input tiles through a ring of kInfStages chunk
+// buffers (bulk copies, warp 4), accumulates each tile's 128 x 256 product into one of two
+// tensor-memory accumulators (tcgen05.mma issued by warp 5), and its four epilogue warps apply bias
+// and SiLU to the other accumulator meanwhile and write the bf16 activations (or the scalar output).
+// Every wait is bounded; a wait that runs out sets the block's abort flag, the remaining outputs of
+// the block become NaN and the error is counted.
+__global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferArgs g) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int K = g.K, kc = K < 64 ? K : 64, nch = K / kc;
+  const uint32_t wbytes = (uint32_t)kWidth * K * 2, cbytes = (uint32_t)kRows * kc * 2;
+  unsigned char* sw = sm;
+  unsigned char* sa = sm + wbytes;
+  float* sbias = reinterpret_cast<float*>(sa + kInfStages * cbytes);
+  float* sw4 = sbias + kWidth;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sw4 + kWidth);
+  uint64_t *full = bar, *empty = bar + kInfStages, *accf = bar + 2 * kInfStages, *acce = accf + 2;
+  uint64_t *wfull = acce + 2, *drain = wfull + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  if (t == 0) {
+    for (int i = 0; i < kInfStages; ++i) {
+      umma::mbar_init(full + i, 1);
+      umma::mbar_init(empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      umma::mbar_init(accf + i, 1);
+      umma::mbar_init(acce + i, 4 * 32);
+    }
+    umma::mbar_init(wfull, 1);
+    umma::mbar_init(drain, 1);
+    *abort_flag = 0;
+  }
+  for (int i = t; i < kWidth; i += kInfThreads) {
+    sbias[i] = g.bias[i];
+    sw4[i] = g.w4 ? g.w4[i] : 0.0f;
+  }
+  if (warp == 0) umma::tmem_alloc(tslot, 512);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  if (warp == 4) {
+    if (lane == 0) {
+      // the layer's weights once, then the input tiles' chunks through the ring
+      umma::mbar_arrive_expect_tx(wfull, wbytes);
+      for (uint32_t o = 0; o < wbytes; o += 16384)
+        umma::bulk_g2s(sw + o, reinterpret_cast<const unsigned char*>(g.w) + o, min(16384u, wbytes - o), wfull);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < g.ntiles && ok; tile += gridDim.x)
+        for (int c = 0; c < nch; ++c, ++it) {
+          const int s = (int)(it % kInfStages);
+          if (!umma::mbar_wait(empty + s, ((it / kInfStages) & 1) ^ 1, g.wait_ns) || *abort_flag) {
+            ok = false;
+            *abort_flag = 1;
+            break;
+          }
+          umma::mbar_arrive_expect_tx(full + s, cbytes);
+          umma::bulk_g2s(sa + s * cbytes,
+                         reinterpret_cast<const unsigned char*>(g.a) + ((size_t)tile * nch + c) * cbytes, cbytes,
+                         full + s);
+        }
+      // copies still in flight land before the block can exit
+      for (uint32_t j = it > kInfStages ? it - kInfStages : 0; j < it; ++j)
+        umma::mbar_wait(full + j % kInfStages, (j / kInfStages) & 1, g.wait_ns);
+      umma::mbar_wait(wfull, 0, g.wait_ns);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      bool ok = umma::mbar_wait(wfull, 0, g.wait_ns);
+      if (!ok) *abort_flag = 1;
+      const uint32_t id = umma::idesc(umma::FMT_BF16, kRows, kWidth);
+      const uint32_t sbo_a = (uint32_t)(kc * 2 / 16) * 128, sbo_w = (uint32_t)(K * 2 / 16) * 128;
+      const uint32_t sa_u = umma::smem_u32(sa), sw_u = umma::smem_u32(sw);
+      uint32_t it = 0, lt = 0;
+      for (int64_t tile = blockIdx.x; tile < g.ntiles && ok; tile += gridDim.x, ++lt) {
+        const uint32_t b = lt & 1;
+        if (!umma::mbar_wait(acce + b, ((lt >> 1) & 1) ^ 1, g.wait_ns) || *abort_flag) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        for (int c = 0; c < nch; ++c, ++it) {
+          const int s = (int)(it % kInfStages);
+          if (!umma::mbar_wait(full + s, (it / kInfStages) & 1, g.wait_ns) || *abort_flag) {
+            ok = false;
+            break;
+          }
+          umma::fence_after_sync();
+          if (!g.skip_mma) {
+            for (int ks = 0; ks < kc / 16; ++ks)
+              umma::mma_f16(tmem + b * kWidth, umma::smem_desc(sa_u + s * cbytes + ks * 256, 128, sbo_a),
+                            umma::smem_desc(sw_u + (uint32_t)(c * kc + ks * 16) * 16, 128, sbo_w), id,
+                            (c > 0 || ks > 0) ? 1u : 0u);
+            umma::mma_commit(empty + s);
+          }
+        }
+        if (!ok) break;
+        if (!g.skip_mma) umma::mma_commit(accf + b);
+      }
+      if (!ok) *abort_flag = 1;
+      // every MMA issued has completed before the tensor memory is freed
+      if (!g.skip_mma) {
+        umma::mma_commit(drain);
+        umma::mbar_wait(drain, 0, g.wait_ns);
+      }
+    }
+  } else {
+    // epilogue: thread t owns row t of each tile (tensor-memory lane t)
+    const float nan = __int_as_float(0x7fc00000);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    bool ok = true;
+    uint32_t lt = 0;
+    for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++lt) {
+      const uint32_t b = lt & 1;
+      if (ok) {
+        bool done = umma::mbar_wait(accf + b, (lt >> 1) & 1, g.wait_ns) && !*abort_flag;
+        done = __all_sync(0xffffffffu, done);
+        if (!done) {
+          ok = false;
+          *abort_flag = 1;
+        }
+      }
+      umma::fence_after_sync();
+      const int64_t row = tile * kRows + t;
+      float y = 0.0f;
+      unsigned char* out = g.h ? reinterpret_cast<unsigned char*>(g.h) + (size_t)tile * kRows * kWidth * 2 : nullptr;
+      for (int n0 = 0; n0 < kWidth; n0 += 32) {
+        float v[32];
+        if (ok) {
+          umma::tmem_ld32(tmem + b * kWidth + lane_base + (uint32_t)n0, v);
+          umma::tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = nan;
+        }
+        if (out) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            __align__(16) __nv_bfloat16 hv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float z = v[8 * j + q] + sbias[n0 + 8 * j + q];
+              hv[q] = __float2bfloat16_rn(z * __fdividef(1.0f, 1.0f + __expf(-z)));
+            }
+            const int n = n0 + 8 * j;
+            *reinterpret_cast<uint4*>(out + (n / 64) * (kRows * 64 * 2) + umma::kmajor_offset(t, n % 64, 64, 2)) =
+                *reinterpret_cast<const uint4*>(hv);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const float z = v[q] + sbias[n0 + q];
+            const float h = __bfloat162float(__float2bfloat16_rn(z * __fdividef(1.0f, 1.0f + __expf(-z))));
+            y = fmaf(h, sw4[n0 + q], y);
+          }
+        }
+      }
+      if (!out && row < g.nrows) g.y[row] = ok ? y + g.b4[0] : nan;
+      umma::fence_before_sync();
+      if (ok) umma::mbar_arrive(acce + b);
+    }
+  }
+  __syncthreads();
+  if (t == 0 && *abort_flag && g.err) atomicAdd(g.err, 1);
+  umma::fence_after_sync();
+  if (warp == 0) {
+    umma::tmem_dealloc(tmem, 512);
+    umma::tmem_relinquish();
   }
 }
 
@@ -343,6 +569,7 @@ struct mgx_mlp {
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16 *wb = nullptr, *wbT = nullptr;
   int step = 0;
+  __nv_bfloat16* wc = nullptr;                     // hidden-layer weights in the canonical layout (inference)
   int* d_status = nullptr;                         // device error counter of the GEMM waits
   int skip_mma = 0;                                // test hook
   unsigned long long wait_ns = 1000000000ull;      // time limit of one tensor-core wait
@@ -451,8 +678,70 @@ int backward(mgx_mlp* net, int n, const float* t, const MlpWs& w, cudaStream_t s
 
 int refresh(mgx_mlp* net, cudaStream_t st) {
   const int n = wb_size(net->L);
-  refresh_bf16_kernel<<<(n + 255) / 256, 256, 0, st>>>(net->p, net->L, net->wb, net->wbT);
+  refresh_bf16_kernel<<<(n + 255) / 256, 256, 0, st>>>(net->p, net->L, net->wb, net->wbT, net->wc);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+// inference workspace for passes of `rows` rows: x tiles (K = 32) and two activation tile buffers
+struct InferWs {
+  __nv_bfloat16 *x, *h0, *h1;
+  size_t bytes;
+};
+InferWs infer_layout(char* base, int64_t rows) {
+  const int64_t tiles = (rows + kRows - 1) / kRows;
+  InferWs w{};
+  const size_t xb = (size_t)tiles * kRows * kK0 * 2, hb = (size_t)tiles * kRows * kWidth * 2;
+  w.x = (__nv_bfloat16*)base;
+  w.h0 = (__nv_bfloat16*)(base ? base + xb : nullptr);
+  w.h1 = (__nv_bfloat16*)(base ? base + xb + hb : nullptr);
+  w.bytes = xb + 2 * hb;
+  return w;
+}
+
+// y[n] = network(rows) for rows given as float32 x [n][24] or float64 momenta [n][24] / scale
+int infer(mgx_mlp* net, int64_t n, const float* x, const double* mom, double scale, float* y, void* ws, size_t wsb,
+          cudaStream_t st) {
+  const int64_t chunk = std::min<int64_t>(n, kInferRows);
+  const InferWs w = infer_layout((char*)ws, chunk);
+  if (!ws || wsb < w.bytes) return MGX_ERR_WORKSPACE_TOO_SMALL;
+  const size_t smem = infer_smem(kWidth);     // the largest: also keeps one block (512 tensor-memory columns) per SM
+  static int attr_dev = -1;
+  if (attr_dev != net->device) {
+    if (cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return MGX_ERR_CUDA;
+    attr_dev = net->device;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device);
+  const ParamLayout& L = net->L;
+  for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+    const int64_t m = std::min(chunk, n - r0), tiles = (m + kRows - 1) / kRows;
+    const int64_t packs = tiles * kRows * (kK0 / 8);
+    pack_tiles_kernel<<<(unsigned)((packs + 255) / 256), 256, 0, st>>>(
+        m, tiles, x ? x + r0 * kNin : nullptr, mom ? mom + r0 * kNin : nullptr, 1.0 / scale, w.x);
+    const __nv_bfloat16* in = w.x;
+    for (int l = 0; l < kDepth; ++l) {
+      InferArgs a{};
+      a.a = in;
+      a.w = net->wc + wb_offset(L, l);
+      a.bias = net->p + L.off_b[l];
+      a.K = L.kin[l];
+      a.ntiles = tiles;
+      a.nrows = m;
+      const bool last = l == kDepth - 1;
+      a.h = last ? nullptr : (l % 2 == 0 ? w.h0 : w.h1);
+      a.w4 = net->p + L.off_w4;
+      a.b4 = net->p + L.off_b4;
+      a.y = y + r0;
+      a.err = net->d_status;
+      a.skip_mma = net->skip_mma;
+      a.wait_ns = net->wait_ns;
+      mlp_infer_kernel<<<(unsigned)std::min<int64_t>(tiles, sms), kInfThreads, smem, st>>>(a);
+      in = a.h;
+    }
+    if (cudaGetLastError() != cudaSuccess) return MGX_ERR_CUDA;
+  }
+  return MGX_OK;
 }
 
 }  // namespace
@@ -477,6 +766,7 @@ int mgx_mlp_create(int device, uint64_t seed, mgx_mlp** out) {
             cudaMalloc(&net->v, sizeof(float) * total) == cudaSuccess &&
             cudaMalloc(&net->wb, sizeof(__nv_bfloat16) * nwb) == cudaSuccess &&
             cudaMalloc(&net->wbT, sizeof(__nv_bfloat16) * nwb) == cudaSuccess &&
+            cudaMalloc(&net->wc, sizeof(__nv_bfloat16) * nwb) == cudaSuccess &&
             cudaMalloc(&net->d_status, 256) == cudaSuccess && cudaMemset(net->d_status, 0, 256) == cudaSuccess;
   // He-uniform initialisation from a seeded 64-bit LCG (weights of padded input columns zero)
   std::vector<float> h(total, 0.0f);
@@ -511,16 +801,18 @@ int mgx_mlp_create(int device, uint64_t seed, mgx_mlp** out) {
 void mgx_mlp_destroy(mgx_mlp* net) {
   if (!net) return;
   cudaFree(net->p); cudaFree(net->g); cudaFree(net->m); cudaFree(net->v);
-  cudaFree(net->wb); cudaFree(net->wbT); cudaFree(net->d_status);
+  cudaFree(net->wb); cudaFree(net->wbT); cudaFree(net->wc); cudaFree(net->d_status);
   delete net;
 }
 
-constexpr int64_t kInferChunk = 1 << 16;   // rows per forward pass in mgx_mlp_forward
 
 int mgx_mlp_workspace_bytes(int64_t n, int training, size_t* bytes) {
   if (!bytes || n < 0 || (training && n > (1 << 24))) return MGX_ERR_INVALID_ARGUMENT;
-  const int64_t rows = training ? std::max<int64_t>(n, 1) : std::min<int64_t>(std::max<int64_t>(n, 1), kInferChunk);
-  *bytes = ws_layout(nullptr, (int)rows).bytes;
+  if (training) {
+    *bytes = ws_layout(nullptr, (int)std::max<int64_t>(n, 1)).bytes;
+    return MGX_OK;
+  }
+  *bytes = infer_layout(nullptr, std::min<int64_t>(std::max<int64_t>(n, 1), kInferRows)).bytes;
   return MGX_OK;
 }
 
@@ -540,19 +832,14 @@ int mgx_mlp_set_params(mgx_mlp* net, const float* host) {
 int mgx_mlp_forward(mgx_mlp* net, int64_t n, const float* x, float* y, void* ws, size_t wsb, void* stream) {
   if (!net || n < 0 || (n > 0 && (!x || !y))) return MGX_ERR_INVALID_ARGUMENT;
   if (n == 0) return MGX_OK;
-  const int64_t chunk = std::min<int64_t>(n, kInferChunk);
-  MlpWs w = ws_layout((char*)ws, (int)chunk);
-  if (!ws || wsb < w.bytes) return MGX_ERR_WORKSPACE_TOO_SMALL;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (cudaMemsetAsync(w.err, 0, sizeof(int), st) != cudaSuccess) return MGX_ERR_CUDA;
-  for (int64_t r0 = 0; r0 < n; r0 += chunk) {
-    const int m = (int)std::min<int64_t>(chunk, n - r0);
-    int rc = forward(net, m, x + r0 * kNin, w, st, false);
-    if (rc != MGX_OK) return rc;
-    if (cudaMemcpyAsync(y + r0, w.y, sizeof(float) * m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-      return MGX_ERR_CUDA;
-  }
-  return MGX_OK;
+  return infer(net, n, x, nullptr, 1.0, y, ws, wsb, (cudaStream_t)stream);
+}
+
+int mgx_mlp_forward_momenta(mgx_mlp* net, int64_t n, const double* momenta, double scale, float* y, void* ws,
+                            size_t wsb, void* stream) {
+  if (!net || n < 0 || (n > 0 && (!momenta || !y)) || !(scale > 0.0)) return MGX_ERR_INVALID_ARGUMENT;
+  if (n == 0) return MGX_OK;
+  return infer(net, n, nullptr, momenta, scale, y, ws, wsb, (cudaStream_t)stream);
 }
 
 // gradients of the mean squared error for one batch, into grad (DEVICE, num_params floats)

@@ -116,7 +116,9 @@ class Unweighter:
     def surrogate_weights(self, mom, wps, ok):
         import torch
         n = mom.shape[0]
-        y = self.net.forward(self.features(mom))
+        if 4 * self.npar != 24:
+            raise MgxError("the surrogate network takes 24 momentum components (6 particles)")
+        y = self.net.forward_momenta(mom, 0.5 * self.sqrts)
         s = torch.empty(n, dtype=torch.float64, device=self.dev)
         _check(lib().mgx_surrogate_weight(n, _ptr(y), self.mean, self.sd, _ptr(wps), _ptr(ok), _ptr(s),
                                           _stream(self.dev)), "mgx_surrogate_weight")

@@ -62,7 +62,15 @@ def test_mlp_gemm_wait_runs_out_and_recovers():
     finally:
         net.set_wait_test(False)
     assert np.isnan(y).all()
-    # 4 layers x 3 row tiles, each one wait that ran out
+    # inference: 4 layer launches of 3 persistent blocks (one 128-row tile each), each block gives up once
     assert net.device_errors(reset=True) == 12
+    t = np.zeros(300, dtype=np.float32)
+    net.set_wait_test(True, wait_ms=1.0)
+    try:
+        loss, g = net.gradients(x, t)                 # the training GEMMs under the same hook
+    finally:
+        net.set_wait_test(False)
+    assert np.isnan(g).any() and net.device_errors(reset=True) > 0
     y = net.forward(x)
-    assert np.isfinite(y).all() and net.device_errors(reset=False) == 0
+    loss, g = net.gradients(x, t)
+    assert np.isfinite(y).all() and np.isfinite(g).all() and net.device_errors(reset=False) == 0

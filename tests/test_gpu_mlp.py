@@ -80,3 +80,24 @@ def test_training_fits_smooth_function():
         net.train_step(x[idx], t[idx], lr=1e-3)
     last = net.gradients(x[:4096], t[:4096])[0]
     assert last < 0.1 * first, (first, last)
+
+
+def test_inference_from_momenta_and_across_passes():
+    """The fused inference path: from float64 momenta it equals the float32-feature path bit for bit
+    (both round momenta / scale to float32, then to bf16), and rows of a second pass (beyond 2^22
+    rows) equal the same rows evaluated on their own (every row's result is independent of the
+    tiling)."""
+    import torch
+    net = _net(seed=13)
+    rng = np.random.default_rng(6)
+    n = (1 << 22) + 300
+    mom = torch.from_numpy(rng.normal(scale=500.0, size=(n, 6, 4))).cuda()
+    scale = 750.0
+    y_mom = net.forward_momenta(mom, scale)
+    x = (mom.reshape(n, 24) / scale).to(torch.float32)
+    y_x = net.forward(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y_mom, y_x)
+    tail = net.forward(x[(1 << 22) - 100:].contiguous())
+    assert torch.equal(tail, y_x[(1 << 22) - 100:])
+    assert torch.isfinite(y_x).all()
