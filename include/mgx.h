@@ -171,12 +171,16 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
  * helicities are split into 2^k groups by their values on k fixed particles, one thread per
  * (event, group) computes the current variants and amplitudes its group uses, and a second kernel
  * sums each event's helicities in canonical order and selects; the fixed particles and k come
- * from a work model of the op table (MGX_FP64, MGX_MIXED_FP32, MGX_FLOAT).  AUTO takes it for a
- * batch that leaves the thread kernel's grid underfilled when that model predicts at least a
- * 1.33x gain and the batch is too large for CTA / THREAD_SMEM.  All give identical results up to
- * float64 rounding. */
+ * from a work model of the op table (MGX_FP64, MGX_MIXED_FP32, MGX_FLOAT).  SPLIT: the diagram
+ * split: the process compiler cuts the amplitude groups into 2, 4 or 8 contiguous parts, each with
+ * the current ops its terms need; one thread per (event, helicity group, part) writes partial
+ * jamps, a combine kernel sums them per (event, helicity) and forms the colour sum, and the finish
+ * kernel selects (same modes; the split and the fixed particles from the same work model).  AUTO
+ * takes HELICITY or SPLIT for a batch that leaves the thread kernel's grid underfilled when that
+ * model predicts at least a 1.33x gain and the batch is too large for CTA / THREAD_SMEM.  All give
+ * identical results up to float64 rounding. */
 enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2, MGX_KERNEL_THREAD_SMEM = 3,
-                  MGX_KERNEL_HELICITY = 4 };
+                  MGX_KERNEL_HELICITY = 4, MGX_KERNEL_SPLIT = 5 };
 int mgx_process_set_kernel(mgx_process* proc, int kernel);  /* INVALID_ARGUMENT if unusable */
 /* the kernel set; for AUTO, THREAD (the choice for throughput batches; AUTO picks CTA or
  * THREAD_SMEM per call for small batches, as above) */

@@ -56,6 +56,11 @@ struct mgx_program_desc {
     int store;             // doubles of shared memory for one event's currents
     int chunk;             // terms per chunk
   } cta;
+  struct {
+    int nparts;            // parts of the diagram split into (at most) 2, 4, 8
+    const int32_t* ops;    // op positions of every part, in program order, parts concatenated
+    const int32_t* start;  // [nparts + 1] offsets into ops
+  } split[3];
 };
 
 #include "generated/programs.inc"
@@ -176,13 +181,18 @@ __device__ inline void finish_event(const KParams& P, int64_t e, const A& mh, co
 // per-event store does not fit in shared memory.
 // The op table of one event, evaluated by one thread into the workspace view W: every current
 // variant, then the jamps [ngood][ncol][Re, Im] at W[jamp_off].  Currents and jamps are of real type R.
-template <class R, class H = AllHel>
-__device__ inline void eval_amplitudes(const KParams& P, const double* pe, const WST<R>& W, const H& hs = H()) {
+// kSplit: only the ops list[0 .. nlist) (one part of a diagram split, in program order) into partial
+// jamps that start at zero and to which every flow update adds.
+template <class R, class H = AllHel, bool kSplit = false>
+__device__ inline void eval_amplitudes(const KParams& P, const double* pe, const WST<R>& W, const H& hs = H(),
+                                       const int* __restrict__ list = nullptr, int nlist = 0) {
   using T = Real<R>;
   const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 later
-  if (P.jamp_zero)
+  if (kSplit || P.jamp_zero)
     for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = T::from(0.0);
-  for (int iop = 0; iop < P.nops; ++iop) {
+  const int nloop = kSplit ? nlist : P.nops;
+  for (int li = 0; li < nloop; ++li) {
+    const int iop = kSplit ? __ldg(list + li) : li;
     const Op o = load_op(P.ops, iop);
     if (o.code == OP_AMP) {
       const int2* fl = P.flows + o.cpl;
@@ -217,7 +227,7 @@ __device__ inline void eval_amplitudes(const KParams& P, const double* pe, const
               const int2 q = __ldg(fl + f);
               const int off = jb + 2 * q.x;
               cxT<R> j = rot_phase(q.y & 3, amp);
-              if (!(q.y & 4)) j = cxT<R>{W[off], W[off + 1]} + j;
+              if (kSplit || !(q.y & 4)) j = cxT<R>{W[off], W[off + 1]} + j;
               W[off] = j.r;
               W[off + 1] = j.i;
             }
@@ -235,7 +245,7 @@ __device__ inline void eval_amplitudes(const KParams& P, const double* pe, const
           const int2 q = __ldg(fl + f);
           const int off = jb + 2 * q.x;
           cxT<R> j = rot_phase(q.y & 3, amp);
-          if (!(q.y & 4)) j = cxT<R>{W[off], W[off + 1]} + j;
+          if (kSplit || !(q.y & 4)) j = cxT<R>{W[off], W[off + 1]} + j;
           W[off] = j.r;
           W[off + 1] = j.i;
         }
@@ -457,6 +467,70 @@ __global__ void __launch_bounds__(kThreads)
   if (colw_out)
     for (int i = 0; i < P.ncol; ++i) colw_out[e * P.ncol + i] = colw(i);
   finish_event(P, e, [&](int ih) { return m[ih]; }, colw, rhel, rcol, me, selhel, selcol);
+}
+
+// ---------------------------------------------------------------- diagram-split kernels
+// The amplitude groups of a process are cut into D parts (process compiler: contiguous segments of
+// the program, each with every current op its terms need); item (e, g, d) = one thread runs part d
+// of event e restricted to helicity group g (as in the helicity-parallel kernel; one group when
+// fix = 0) into zeroed partial jamps and writes them to pj [nevt][D][ngood][ncol][Re, Im].
+// split_combine_kernel then sums each (event, helicity)'s D partial jamp vectors, forms the colour
+// sum and the helicity's colour-weight terms, and finish_hel_kernel (with one "group" per
+// helicity) sums the helicities in canonical order and selects.
+template <class R>
+__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 4)
+    me_split_kernel(const KParams P, int64_t nevt, int gshift, int fix, int nparts, const int* __restrict__ part_ops,
+                    const int* __restrict__ part_start, const double* __restrict__ mom, R* __restrict__ pj,
+                    double* __restrict__ ws, int64_t nthreads) {
+  extern __shared__ double smem[];
+  const int npar4 = 4 * P.npar;
+  const int per = nparts << gshift;                           // items per event
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const WST<R> W{reinterpret_cast<R*>(ws) + tid, nthreads};
+  const int64_t nitems = nevt * per;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nitems; base += nthreads) {
+    const int64_t e0 = base / per;                            // the block's items cover events e0 .. e0 + ne - 1
+    const int64_t ne = min((base + blockDim.x - 1) / per - e0 + 1, nevt - e0);
+    stage_momenta(mom, e0, ne, npar4, smem);
+    const int64_t item = base + threadIdx.x;
+    if (item >= nitems) continue;
+    const int64_t e = item / per;
+    const int d = (int)(item % nparts);
+    const int g = (int)((item / nparts) & ((1 << gshift) - 1));
+    const GroupHel hs{fix, pdep(g, fix)};
+    const int s0 = __ldg(part_start + d), s1 = __ldg(part_start + d + 1);
+    eval_amplitudes<R, GroupHel, true>(P, smem + (e - e0) * npar4, W, hs, part_ops + s0, s1 - s0);
+    const int nj = 2 * P.ncol;
+    R* out = pj + (e * nparts + d) * (int64_t)P.ngood * nj;
+    for (int ih = 0; ih < P.ngood; ++ih) {
+      if (!hs.ok(P.good[ih])) continue;
+      for (int k = 0; k < nj; ++k) out[ih * nj + k] = W[P.jamp_off + ih * nj + k];
+    }
+  }
+}
+
+// one thread per (event, good helicity): J = sum of the D partial jamps, then |M_h|^2 (colour sum of
+// the mode) into mh_buf [nevt][ngood] and |J_i|^2 into cwh [nevt][ngood][ncol], both times the
+// event's coupling factor
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+    split_combine_kernel(const KParams P, int64_t nevt, int nparts, const R* __restrict__ pj,
+                         const double* __restrict__ alphas, double* __restrict__ mh_buf, double* __restrict__ cwh,
+                         int mode) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= nevt * P.ngood) return;
+  const int64_t e = item / P.ngood;
+  const int ih = (int)(item % P.ngood);
+  const int nj = 2 * P.ncol;
+  R J[2 * kMaxColFp32];
+  const R* src = pj + (e * nparts * (int64_t)P.ngood + ih) * nj;
+  for (int k = 0; k < nj; ++k) J[k] = src[k];
+  for (int d = 1; d < nparts; ++d)
+    for (int k = 0; k < nj; ++k) J[k] = J[k] + src[(int64_t)d * P.ngood * nj + k];
+  const double scale = coupling_scale(P, alphas[e]);
+  mh_buf[item] = scale * colour_sum<R>(P, [&](int k) { return J[k]; }, P.ncol, mode);
+  for (int i = 0; i < P.ncol; ++i)
+    cwh[item * P.ncol + i] = scale * Real<R>::to_double(fma(J[2 * i], J[2 * i], J[2 * i + 1] * J[2 * i + 1]));
 }
 
 // ---------------------------------------------------------------- batched multi-process kernel
@@ -777,6 +851,13 @@ struct mgx_process {
   unsigned long long tc_wait_ns = 1000000000ull;   // time limit of one tensor-core wait
   int blocks_per_sm = 4;      // thread-per-event kernel
   int kernel = MGX_KERNEL_AUTO;
+  // work model of the helicity-parallel and diagram-split plans (filled after the helicity filter)
+  std::vector<int> most;                // [2^npar]: good helicities of the largest group, per fixed-leg set
+  std::vector<double> cur_work[4];      // [part][2^npar]: current-variant work (whole program, splits 2/4/8)
+  std::vector<double> amp_work[4];      // [part]: amplitude work per helicity
+  int nparts[4] = {1, 1, 1, 1};
+  int* d_split_ops[3] = {nullptr, nullptr, nullptr};
+  int* d_split_start[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -849,9 +930,12 @@ bool use_cta_kernel(const mgx_process* pr, const KParams& kp, int64_t nevt, int 
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// ---- helicity-parallel plan: fixed legs and group count for one batch
+// ---- plans for a batch: the whole-event thread kernel, the helicity-parallel kernel or the
+// diagram-split kernel, chosen by a work model of the op table
 struct HelPlan {
-  int gshift = 0, fix = 0;   // G = 2^gshift groups by the helicity bits on the legs in `fix`
+  int gshift = 0, fix = 0;   // G = 2^gshift helicity groups by the helicity bits on the legs in `fix`
+  int split = 0;             // 0: no diagram split; 1, 2, 3: the split into at most 2, 4, 8 parts
+  int nparts = 1;
 };
 
 int host_pdep(int v, int mask) {
@@ -864,92 +948,129 @@ int host_pdep(int v, int mask) {
   return r;
 }
 
-// Float64 instructions one thread executes with fixed legs `fix` (fix = 0: the whole event): the
-// current variants it computes (per variant of its legs, as in the work model of the roofline) plus
-// the amplitudes and colour sums of the group with the most good helicities.
-double hel_thread_work(const mgx_process* pr, int fix, int mode) {
-  const mgx_program_desc* prog = pr->prog;
-  double cur = 0.0, per_hel = 0.0;
-  for (int i = 0; i < prog->nops; ++i) {
-    const int32_t* o = prog->ops + 16 * i;
-    const int code = o[0], mdst = o[5], aux2 = o[12];
-    if (code == OP_AMP) {
-      per_hel += 16.0 * aux2 + 2.0 * o[10];    // closing products and flow updates, per helicity
-      continue;
-    }
-    double w = 8.0 * std::max(0, aux2 - 1);   // OP_SUM: 4-vector adds per further summand
-    switch (code) {
-      case OP_EXT: w = 24; break;
-      case OP_FFV_F: case OP_FFV_FB: w = 64; break;
-      case OP_FFV_V: w = 72; break;
-      case OP_VVV: w = 56; break;
-      case OP_VVVV: w = 32; break;
-      case OP_BIL: w = 56; break;
-      case OP_RBIL: w = 32; break;
-      default: break;
-    }
-    cur += w * (double)(1 << __builtin_popcount((unsigned)(mdst & ~fix)));
+// float64 instructions per variant of each current kind (as in the roofline's work model); per
+// helicity, an amplitude group costs one closing product per term and an add per flow
+double op_variant_cost(const int32_t* o) {
+  switch (o[0]) {
+    case OP_EXT: return 24;
+    case OP_FFV_F: case OP_FFV_FB: return 64;
+    case OP_FFV_V: return 72;
+    case OP_VVV: return 56;
+    case OP_VVVV: return 32;
+    case OP_BIL: return 56;
+    case OP_RBIL: return 32;
+    default: return 8.0 * std::max(0, o[12] - 1);   // OP_SUM: a 4-vector add per further summand
   }
-  const double n = prog->ncol;
-  per_hel += mode == MGX_FP64 ? n * n + 3 * n : 2 * n;
-  int most = 0;
-  const int k = __builtin_popcount((unsigned)fix);
-  for (int g = 0; g < (1 << k); ++g) {
-    const int bits = host_pdep(g, fix);
-    int c = 0;
-    for (int h : pr->good) c += (h & fix) == bits;
-    most = std::max(most, c);
-  }
-  return cur + per_hel * most;
 }
 
-// The cheapest split of a batch of nevt events: estimated time = passes of the persistent grid x
-// the per-thread work; the whole-event thread kernel is gshift = 0.  force: best split with G > 1.
-HelPlan hel_plan(const mgx_process* pr, int64_t nevt, int mode, bool force) {
-  const int bps = mode == MGX_FLOAT ? 2 * pr->blocks_per_sm : pr->blocks_per_sm;
-  const int64_t cap = (int64_t)sm_count(pr->device) * bps * kThreads;
-  const int npar = pr->prog->npar;
-  const double t1 = hel_thread_work(pr, 0, mode) * (double)((nevt + cap - 1) / cap);
-  HelPlan best;
-  double tb = 0.0;
-  for (int fix = 1; fix < (1 << npar); ++fix) {
-    const int k = __builtin_popcount((unsigned)fix);
-    if (k > 6 || (nevt << k) > (int64_t)1 << 40) continue;
-    const double t = hel_thread_work(pr, fix, mode) * (double)(((nevt << k) + cap - 1) / cap);
-    if (best.gshift == 0 || t < tb) {
-      best = HelPlan{k, fix};
-      tb = t;
+// Work model of a process (after the helicity filter), for every set F of fixed legs: the largest
+// helicity group's good-helicity count, and per part of the whole program (s = 0) and of each
+// diagram split (s = 1..3) the current-variant work a thread does with legs F fixed and its
+// amplitude work per helicity.
+void build_work_model(mgx_process* pr) {
+  const mgx_program_desc* prog = pr->prog;
+  const int nf = 1 << prog->npar;
+  pr->most.assign(nf, 0);
+  for (int F = 0; F < nf; ++F) {
+    const int k = __builtin_popcount((unsigned)F);
+    for (int g = 0; g < (1 << k); ++g) {
+      const int bits = host_pdep(g, F);
+      int c = 0;
+      for (int h : pr->good) c += (h & F) == bits;
+      pr->most[F] = std::max(pr->most[F], c);
     }
   }
-  if (!force && !(tb < 0.75 * t1)) return HelPlan{};   // the split must be clearly cheaper
+  for (int sidx = 0; sidx < 4; ++sidx) {
+    const int np = sidx == 0 ? 1 : prog->split[sidx - 1].nparts;
+    pr->nparts[sidx] = np;
+    pr->cur_work[sidx].assign((size_t)np * nf, 0.0);
+    pr->amp_work[sidx].assign(np, 0.0);
+    for (int d = 0; d < np; ++d) {
+      const int i0 = sidx == 0 ? 0 : prog->split[sidx - 1].start[d];
+      const int i1 = sidx == 0 ? prog->nops : prog->split[sidx - 1].start[d + 1];
+      for (int li = i0; li < i1; ++li) {
+        const int32_t* o = prog->ops + 16 * (sidx == 0 ? li : prog->split[sidx - 1].ops[li]);
+        if (o[0] == OP_AMP) {
+          pr->amp_work[sidx][d] += 16.0 * o[12] + 2.0 * o[10];
+          continue;
+        }
+        const double w = op_variant_cost(o);
+        for (int F = 0; F < nf; ++F)
+          pr->cur_work[sidx][(size_t)d * nf + F] += w * (double)(1 << __builtin_popcount((unsigned)(o[5] & ~F)));
+      }
+    }
+  }
+}
+
+enum { PLAN_ANY = 0, PLAN_HEL = 1, PLAN_SPLIT = 2 };
+
+// The plan of least estimated time = passes of the persistent grid x the work of the busiest thread
+// (plus, for a diagram split, the combine step: one thread per event and helicity).  PLAN_ANY keeps
+// the whole-event thread kernel unless another plan is estimated at least 1.33x faster; PLAN_HEL
+// and PLAN_SPLIT return the best plan of that kind.
+HelPlan best_plan(const mgx_process* pr, int64_t nevt, int mode, int kind) {
+  const int bps = mode == MGX_FLOAT ? 2 * pr->blocks_per_sm : pr->blocks_per_sm;
+  const double cap = (double)sm_count(pr->device) * bps * kThreads;
+  const int nf = 1 << pr->prog->npar;
+  const double n = pr->prog->ncol;
+  const double colour = mode == MGX_FP64 ? n * n + 3 * n : 2 * n;
+  const double ngood = (double)pr->good.size();
+  auto passes = [&](double items) { return std::ceil(items / cap); };
+  const double t_thread = passes((double)nevt) * (pr->cur_work[0][0] + (pr->amp_work[0][0] + colour) * pr->most[0]);
+  HelPlan best;
+  double tb = -1.0;
+  for (int sidx = 0; sidx < 4; ++sidx) {
+    if ((kind == PLAN_HEL && sidx != 0) || (kind == PLAN_SPLIT && sidx == 0)) continue;
+    const int np = pr->nparts[sidx];
+    if (sidx > 0 && np < 2) continue;
+    for (int F = sidx == 0 ? 1 : 0; F < nf; ++F) {
+      const int k = __builtin_popcount((unsigned)F);
+      if (k > 6) continue;
+      double work = 0.0;
+      for (int d = 0; d < np; ++d)
+        work = std::max(work, pr->cur_work[sidx][(size_t)d * nf + F] +
+                                  (pr->amp_work[sidx][d] + (sidx == 0 ? colour : 0.0)) * pr->most[F]);
+      double t = passes((double)nevt * np * (double)(1 << k)) * work;
+      if (sidx > 0) t += passes((double)nevt * ngood) * (colour + 2.0 * n * np);
+      if (tb < 0.0 || t < tb) {
+        tb = t;
+        best = HelPlan{k, F, sidx, np};
+      }
+    }
+  }
+  if (kind == PLAN_ANY && !(tb >= 0.0 && tb < 0.75 * t_thread)) return HelPlan{};
   return best;
 }
 
 struct HelLayout {
-  size_t ws, mh, cw, total;
+  size_t ws, pj, mh, cw, total;
 };
 HelLayout hel_layout(const mgx_process* pr, const KParams& kp, const HelPlan& hp, int64_t nevt, int mode, int64_t nt) {
   HelLayout L;
+  const size_t real = mode == MGX_FLOAT ? sizeof(float) : sizeof(double);
   L.ws = align256((size_t)nt * thread_ws_bytes(kp, mode));
+  L.pj = hp.split ? align256((size_t)nevt * hp.nparts * kp.ngood * 2 * kp.ncol * real) : 0;
   L.mh = align256((size_t)nevt * kp.ngood * sizeof(double));
-  L.cw = align256((size_t)nevt * ((size_t)1 << hp.gshift) * kp.ncol * sizeof(double));
-  L.total = L.ws + L.mh + L.cw;
+  // colour-weight terms: per (event, group) without a split, per (event, helicity) with one
+  L.cw = align256((size_t)nevt * (hp.split ? (size_t)kp.ngood : ((size_t)1 << hp.gshift)) * kp.ncol * sizeof(double));
+  L.total = L.ws + L.pj + L.mh + L.cw;
   return L;
 }
+int64_t plan_items(const HelPlan& hp, int64_t nevt) { return (nevt * hp.nparts) << hp.gshift; }
 
-// the helicity-parallel kernel: chosen explicitly, or by AUTO for a batch that leaves the thread
-// kernel's grid underfilled when the work model says a split is clearly cheaper (float64, mixed
-// float32 and float modes; the tensor-core modes run the fused thread kernel)
+// the helicity-parallel or diagram-split kernels: chosen explicitly, or by AUTO for a batch that
+// leaves the thread kernel's grid underfilled when the work model says a plan is clearly cheaper
+// (float64, mixed float32 and float modes; the tensor-core modes run the fused thread kernel)
 bool use_hel_kernel(const mgx_process* pr, const KParams& kp, int64_t nevt, int mode, HelPlan* plan) {
-  if (!(mode_f64(mode) || mode == MGX_FLOAT) || pr->prog->npar < 2) return false;
-  if (pr->kernel == MGX_KERNEL_HELICITY) {
-    *plan = hel_plan(pr, nevt, mode, true);
-    return plan->gshift > 0;
+  if (!(mode_f64(mode) || mode == MGX_FLOAT) || pr->most.empty()) return false;
+  if (pr->kernel == MGX_KERNEL_HELICITY || pr->kernel == MGX_KERNEL_SPLIT) {
+    *plan = best_plan(pr, nevt, mode, pr->kernel == MGX_KERNEL_HELICITY ? PLAN_HEL : PLAN_SPLIT);
+    return plan->gshift > 0 || plan->split > 0;
   }
   if (pr->kernel != MGX_KERNEL_AUTO || use_cta_kernel(pr, kp, nevt, mode) || use_smem_ws(pr, kp, nevt, mode))
     return false;
-  *plan = hel_plan(pr, nevt, mode, false);
-  return plan->gshift > 0;
+  *plan = best_plan(pr, nevt, mode, PLAN_ANY);
+  return plan->gshift > 0 || plan->split > 0;
 }
 
 size_t cta_smem_bytes(const mgx_process* pr, const KParams& kp) {
@@ -1014,26 +1135,49 @@ int launch_tc(mgx_process* pr, const KParams& kp, int64_t nevt, const double* mo
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
-// the helicity-parallel kernel and its finish kernel
+// the helicity-parallel kernel and its finish kernel, or the diagram-split kernel, its combine
+// kernel and the finish kernel
 int launch_hel(mgx_process* pr, const KParams& kp, const HelPlan& hp, int64_t nevt, const double* mom,
                const double* as, const double* rh, const double* rc, double* me, int32_t* sh, int32_t* sc, double* mh,
                double* cw, int mode, void* ws, size_t wsb, cudaStream_t st) {
-  const int64_t nt = grid_threads(pr, nevt << hp.gshift, mode);
+  const int64_t nt = grid_threads(pr, plan_items(hp, nevt), mode);
   const HelLayout L = hel_layout(pr, kp, hp, nevt, mode, nt);
   if (ws == nullptr || wsb < L.total) return MGX_ERR_WORKSPACE_TOO_SMALL;
   char* p = (char*)ws;
-  double* mh_buf = (double*)(p + L.ws);
-  double* cw_buf = (double*)(p + L.ws + L.mh);
+  void* pj = p + L.ws;
+  double* mh_buf = (double*)(p + L.ws + L.pj);
+  double* cw_buf = (double*)(p + L.ws + L.pj + L.mh);
   const size_t shm = (size_t)kThreads * 4 * kp.npar * sizeof(double);
   const unsigned blocks = (unsigned)(nt / kThreads);
-  if (mode == MGX_FLOAT)
-    me_hel_kernel<float><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, mom, as, mh_buf, cw_buf,
-                                                        (double*)ws, nt, mode);
-  else
-    me_hel_kernel<double><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, mom, as, mh_buf, cw_buf,
-                                                         (double*)ws, nt, mode);
+  const bool f32 = mode == MGX_FLOAT;
+  if (hp.split == 0) {
+    if (f32)
+      me_hel_kernel<float><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, mom, as, mh_buf, cw_buf,
+                                                          (double*)ws, nt, mode);
+    else
+      me_hel_kernel<double><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, mom, as, mh_buf, cw_buf,
+                                                           (double*)ws, nt, mode);
+    finish_hel_kernel<<<(unsigned)((nevt + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        kp, nevt, 1 << hp.gshift, mh_buf, cw_buf, rh, rc, me, sh, sc, mh, cw);
+    return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+  }
+  const int* ops = pr->d_split_ops[hp.split - 1];
+  const int* start = pr->d_split_start[hp.split - 1];
+  const int64_t pairs = nevt * kp.ngood;
+  const unsigned cblocks = (unsigned)((pairs + kThreads - 1) / kThreads);
+  if (f32) {
+    me_split_kernel<float><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, hp.nparts, ops, start, mom,
+                                                          (float*)pj, (double*)ws, nt);
+    split_combine_kernel<float><<<cblocks, kThreads, 0, st>>>(kp, nevt, hp.nparts, (const float*)pj, as, mh_buf,
+                                                              cw_buf, mode);
+  } else {
+    me_split_kernel<double><<<blocks, kThreads, shm, st>>>(kp, nevt, hp.gshift, hp.fix, hp.nparts, ops, start, mom,
+                                                           (double*)pj, (double*)ws, nt);
+    split_combine_kernel<double><<<cblocks, kThreads, 0, st>>>(kp, nevt, hp.nparts, (const double*)pj, as, mh_buf,
+                                                               cw_buf, mode);
+  }
   finish_hel_kernel<<<(unsigned)((nevt + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-      kp, nevt, 1 << hp.gshift, mh_buf, cw_buf, rh, rc, me, sh, sc, mh, cw);
+      kp, nevt, kp.ngood, mh_buf, cw_buf, rh, rc, me, sh, sc, mh, cw);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 
@@ -1119,6 +1263,10 @@ void mgx_process_destroy(mgx_process* pr) {
   cudaFree(pr->d_tc_b32);
   cudaFree(pr->d_tc_b16);
   cudaFree(pr->d_status);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(pr->d_split_ops[i]);
+    cudaFree(pr->d_split_start[i]);
+  }
   cudaFree(pr->d_cta_ops);
   cudaFree(pr->d_cta_flows);
   cudaFree(pr->d_cta_terms);
@@ -1262,6 +1410,15 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
          cudaMalloc(&pr->d_tc_b16, sizeof(uint16_t) * b16.size()) == cudaSuccess &&
          cudaMemcpy(pr->d_tc_b16, b16.data(), sizeof(uint16_t) * b16.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMalloc(&pr->d_status, 256) == cudaSuccess && cudaMemset(pr->d_status, 0, 256) == cudaSuccess;
+    for (int i = 0; i < 3 && ok; ++i) {
+      const auto& sp = prog->split[i];
+      const int nops = sp.start[sp.nparts];
+      ok = cudaMalloc(&pr->d_split_ops[i], sizeof(int) * std::max(1, nops)) == cudaSuccess &&
+           cudaMemcpy(pr->d_split_ops[i], sp.ops, sizeof(int) * nops, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMalloc(&pr->d_split_start[i], sizeof(int) * (sp.nparts + 1)) == cudaSuccess &&
+           cudaMemcpy(pr->d_split_start[i], sp.start, sizeof(int) * (sp.nparts + 1), cudaMemcpyHostToDevice) ==
+               cudaSuccess;
+    }
   }
   if (!ok) {
     mgx_process_destroy(pr);
@@ -1327,6 +1484,7 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
     kp.hidx[pr->good[i]] = (signed char)i;
   }
   set_layout(kp, prog->ws_doubles, kp.ngood, n);
+  build_work_model(pr);
   cudaSetDevice(cur);
   *out = pr;
   return MGX_OK;
@@ -1365,7 +1523,7 @@ int mgx_workspace_bytes(const mgx_process* pr, int64_t nevt, int mode, size_t* b
   }
   HelPlan hp;
   if (nevt > 0 && use_hel_kernel(pr, pr->kp, nevt, mode, &hp)) {
-    *bytes = hel_layout(pr, pr->kp, hp, nevt, mode, grid_threads(pr, nevt << hp.gshift, mode)).total;
+    *bytes = hel_layout(pr, pr->kp, hp, nevt, mode, grid_threads(pr, plan_items(hp, nevt), mode)).total;
     return MGX_OK;
   }
   *bytes = (nevt == 0 || use_cta_kernel(pr, pr->kp, nevt, mode) || use_smem_ws(pr, pr->kp, nevt, mode))
@@ -1447,7 +1605,7 @@ int mgx_compute_host(mgx_process* pr, int64_t nevt, const double* momenta, const
 }
 
 int mgx_process_set_kernel(mgx_process* pr, int kernel) {
-  if (!pr || kernel < MGX_KERNEL_AUTO || kernel > MGX_KERNEL_HELICITY) return MGX_ERR_INVALID_ARGUMENT;
+  if (!pr || kernel < MGX_KERNEL_AUTO || kernel > MGX_KERNEL_SPLIT) return MGX_ERR_INVALID_ARGUMENT;
   if (kernel == MGX_KERNEL_CTA && !cta_usable(pr, pr->kp)) return MGX_ERR_INVALID_ARGUMENT;
   if (kernel == MGX_KERNEL_THREAD_SMEM && !smem_usable(pr->kp, MGX_FP64)) return MGX_ERR_INVALID_ARGUMENT;
   pr->kernel = kernel;
@@ -1457,7 +1615,7 @@ int mgx_process_set_kernel(mgx_process* pr, int kernel) {
 int mgx_process_get_kernel(const mgx_process* pr) {
   if (!pr) return MGX_ERR_INVALID_ARGUMENT;
   if (use_cta(pr, pr->kp)) return MGX_KERNEL_CTA;
-  if (pr->kernel == MGX_KERNEL_HELICITY) return MGX_KERNEL_HELICITY;
+  if (pr->kernel == MGX_KERNEL_HELICITY || pr->kernel == MGX_KERNEL_SPLIT) return pr->kernel;
   return pr->kernel == MGX_KERNEL_THREAD_SMEM ? MGX_KERNEL_THREAD_SMEM : MGX_KERNEL_THREAD;
 }
 
@@ -1516,7 +1674,8 @@ int mgx_kernel_launches(const mgx_process* pr, int64_t nevt, int mode) {
   if (!pr || nevt < 0 || !mode_ok(mode)) return -1;
   if (nevt == 0) return 0;
   HelPlan hp;
-  return use_hel_kernel(pr, pr->kp, nevt, mode, &hp) ? 2 : 1;   // the helicity-parallel kernel and its finish
+  if (!use_hel_kernel(pr, pr->kp, nevt, mode, &hp)) return 1;
+  return hp.split ? 3 : 2;   // split, combine and finish kernels; or the helicity-parallel kernel and its finish
 }
 
 double mgx_fp64_ops_per_event(const mgx_process* pr, int mode) { return pr ? fp64_work(pr, mode, false) : 0.0; }
@@ -1709,7 +1868,10 @@ extern "C" int mgx_process_autotune(mgx_process* pr, int64_t nevt, const double*
   std::vector<Cand> cands = {{MGX_KERNEL_THREAD, 2}, {MGX_KERNEL_THREAD, 4}};
   if (cta_usable(pr, pr->kp) && mode_f64(mode)) cands.push_back({MGX_KERNEL_CTA, 4});
   if (smem_usable(pr->kp, mode)) cands.push_back({MGX_KERNEL_THREAD_SMEM, 4});
-  if (mode_f64(mode) || mode == MGX_FLOAT) cands.push_back({MGX_KERNEL_HELICITY, 4});
+  if (mode_f64(mode) || mode == MGX_FLOAT) {
+    cands.push_back({MGX_KERNEL_HELICITY, 4});
+    cands.push_back({MGX_KERNEL_SPLIT, 4});
+  }
   const int save_k = pr->kernel, save_b = pr->blocks_per_sm;
   float best = 1e30f;
   Cand pick{save_k, save_b};

@@ -47,6 +47,15 @@ def emit(path):
         out.append(_arr("int32_t", pre + "_mass",
                         (str(_PARAM_ID[x]) for pair in P.masses for x in pair)))
         out.append(_arr("int32_t", pre + "_extmass", (str(x) for x in P.ext_mass)))
+        split_init = []
+        for n in (2, 4, 8):
+            parts = P.splits[n]
+            out.append(_arr("int32_t", f"{pre}_split{n}_ops", (str(i) for part in parts for i in part)))
+            starts = [0]
+            for part in parts:
+                starts.append(starts[-1] + len(part))
+            out.append(_arr("int32_t", f"{pre}_split{n}_start", (str(x) for x in starts)))
+            split_init.append(f"{{{len(parts)}, {pre}_split{n}_ops, {pre}_split{n}_start}}")
         c = P.flop_counts
         cta = P.cta
         if cta is not None:
@@ -68,7 +77,7 @@ def emit(path):
             f'{P.nterms}, {P.average_den}, {P.gs_power}, {P.col_den}, {P.jamp_zero}, '
             f'{{{c["var_ffv_f"]}, {c["var_ffv_fb"]}, {c["var_ffv_v"]}, {c["var_vvv"]}, {c["var_vvvv"]}, {c["var_bil"]}, {c["var_rbil"]}, '
             f'{c["ffv_f"] + c["ffv_fb"] + c["ffv_v"] + c["vvv"] + c["vvvv"] + c["bil"] + c["rbil"]}, {c["amp_terms"]}, {c["amp_flows"]}, {c["amp"]}, {c["amp_runs"]}, {c["sum_adds"]}, {c["vvv_hdr"]}, {c["vvvv_hdr"]}, {c["slash_hdr"]}, {c["slash_pref_hdr"]}}}, '
-            f'{cta_init}}},')
+            f'{cta_init}, {{{", ".join(split_init)}}}}},')
     out.append("static const mgx_program_desc mgx_programs[] = {\n" + "\n".join(entries) + "\n};\n")
     out.append(f"static const int mgx_num_programs = {len(BUILTIN)};\n")
     text = "\n".join(out)

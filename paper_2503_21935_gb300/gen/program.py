@@ -453,7 +453,65 @@ def _dfs_schedule(B):
                 seen.add(flows[2 * k])
                 flows[2 * k + 1] |= FLOW_FIRST
     B.all_flows_written = len(seen) == len(B.D_perms)
-    return ops, flows, terms, A.top
+    # positions of the ops each op reads (children of a current; bilinears and other operands of a
+    # group), for the diagram split
+    pos_of = {x: pos for pos, (kind, x) in enumerate(order) if kind == "C"}
+    deps = [sorted({pos_of[u] for u in uses(item)}) for item in order]
+    return ops, flows, terms, A.top, deps
+
+
+# float64 instructions per variant of each current kind (the work model of the roofline), and per
+# helicity of an amplitude group: one closing product per run and an add per flow
+_VAR_COST = {OP_EXT: 24, OP_FFV_F: 64, OP_FFV_FB: 64, OP_FFV_V: 72, OP_VVV: 56, OP_VVVV: 32, OP_BIL: 56, OP_RBIL: 32}
+
+
+def _op_cost(op, nhel):
+    if op[0] == OP_AMP:
+        return nhel * (16 * op[12] + 2 * op[10])
+    w = _VAR_COST.get(op[0], 8 * max(0, op[12] - 1))        # OP_SUM: a 4-vector add per further summand
+    return w << bin(op[5]).count("1")
+
+
+def _diagram_parts(ops, deps, nparts, nhel):
+    """Diagram split: the amplitude groups, in program order, cut into at most `nparts` contiguous
+    segments; each part is its groups plus every op they need (closure over the ops they read), in
+    program order.  The cut minimises the largest part's cost (binary search on a cap with a greedy
+    sweep).  Executing a part's ops in program order is valid with the thread program's block
+    offsets: a block is reused only after the last op that reads it, and a part holds every reader
+    it needs.  Returns the op positions of each part."""
+    cost = [_op_cost(op, nhel) for op in ops]
+    clos = {}
+
+    def closure(i):
+        if i not in clos:
+            out = {i}
+            for d in deps[i]:
+                out |= closure(d)
+            clos[i] = out
+        return clos[i]
+    amps = [i for i, op in enumerate(ops) if op[0] == OP_AMP]
+
+    def sweep(cap):
+        parts, cur, c = [], set(), 0
+        for a in amps:
+            new = cur | closure(a)
+            cn = sum(cost[i] for i in new)
+            if cur and cn > cap:
+                parts.append(cur)
+                cur = set(closure(a))
+            else:
+                cur = new
+        parts.append(cur)
+        return parts
+    lo = max(sum(cost[i] for i in closure(a)) for a in amps)
+    hi = sum(cost)
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if len(sweep(mid)) <= nparts:
+            hi = mid
+        else:
+            lo = mid + 1
+    return [sorted(p) for p in sweep(lo)]
 
 
 def _wave_schedule(B, chunk):
@@ -564,7 +622,7 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
     npar = D.npar
     B = _Builder(D)
     B.D_perms = _perms(D)
-    ops, flows, terms, top = _dfs_schedule(B)
+    ops, flows, terms, top, deps = _dfs_schedule(B)
     counts = dict(ext=0, ffv_f=0, ffv_fb=0, ffv_v=0, vvv=0, vvvv=0, bil=0, rbil=0, amp=0, amp_flows=0,
                   var_ffv_f=0, var_ffv_fb=0, var_ffv_v=0, var_vvv=0, var_vvvv=0, var_bil=0, var_rbil=0)
     name = {OP_EXT: "ext", OP_FFV_F: "ffv_f", OP_FFV_FB: "ffv_fb", OP_FFV_V: "ffv_v", OP_VVV: "vvv",
@@ -612,6 +670,9 @@ def build_program(process, smem_budget=SMEM_STORE_BUDGET):
                    ext_mass=B.ext_mass, ws_current_doubles=top, ndiagrams=D.ndiagrams, nterms=len(D.terms),
                    average_den=4 * ncol_in * ident, flop_counts=counts)
     prog.cta = cta
+    prog.deps = deps
+    # diagram splits into 2, 4 and 8 parts (fewer when the program has fewer amplitude groups)
+    prog.splits = {n: _diagram_parts(ops, deps, n, 1 << npar) for n in (2, 4, 8)}
     prog.gs_power = gsp
     prog.jamp_zero = 0 if B.all_flows_written else 1
     # integer scaling of the colour matrix for the tensor-core colour sum (exact in tf32)

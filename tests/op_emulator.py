@@ -294,6 +294,36 @@ class Emulator:
                 self._variants(op, W, pe)
         return self._finish(jamps, alpha_s, rnd_hel, rnd_col)
 
+    def evaluate_parts(self, mom, alpha_s, parts, fix=0, rnd_hel=None, rnd_col=None):
+        """The diagram-split program: for each part (op positions in program order) and helicity
+        group (bits on the legs in `fix`), a fresh NaN workspace in which only the part's ops run,
+        restricted to the group, into zeroed partial jamps that every flow update adds to; the
+        partial jamps of the parts are summed.  An op that reads a block its part did not compute
+        (or that another op of the part reused) makes the result NaN or wrong."""
+        P = self.P
+        nevt = mom.shape[0]
+        pe = np.transpose(mom, (1, 2, 0))
+        self.terms, self.flows = P.terms, P.flows
+        self.count = Counter()
+        total = np.zeros((self.nhel, P.ncol, nevt), complex)
+        k = bin(fix).count("1")
+        for g in range(1 << k):
+            self.fix, self.bits = fix, pdep(g, fix)
+            for part in parts:
+                W = Workspace(P.ws_current_doubles, nevt)
+                jamps = np.zeros((self.nhel, P.ncol, nevt), complex)
+                for i in part:
+                    op = P.ops[i]
+                    if op[0] == OP_AMP:
+                        self._amp(op, W, jamps, first_writes=False)
+                    else:
+                        self._header(op, W, pe)
+                        self._variants(op, W, pe)
+                mine = [h for h in range(self.nhel) if h & fix == self.bits]
+                total[mine] += jamps[mine]
+        self.fix, self.bits = 0, 0
+        return self._finish(total, alpha_s, rnd_hel, rnd_col)
+
     def evaluate_cta(self, mom, alpha_s, rnd_hel=None, rnd_col=None):
         """The same through the block-per-event schedule: waves of (op, header or variant) items
         that a block's threads run in any order, amplitude steps into zeroed jamps.  Raises if an

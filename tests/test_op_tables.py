@@ -75,3 +75,22 @@ def test_helicity_groups_match_oracle(name, nevt):
     fixes += sorted({int(x) for x in rng.integers(1, 1 << npar, size=4)})
     for fix in fixes:
         _check(wl, mom, a, rh, rc, em.evaluate_groups(mom, a, fix, rh, rc))
+
+
+@pytest.mark.parametrize("name,nevt", [c for c in CASES if c[0] != "ggttggg"])
+def test_diagram_split_parts_match_oracle(name, nevt):
+    """The diagram-split program: every part of the compiler's 2-, 4- and 8-part splits runs only
+    its ops (in program order, with the thread program's block offsets) on a fresh NaN workspace
+    into zeroed partial jamps, alone and within helicity groups; the summed partial jamps must give
+    the oracle's results.  A part missing an op it reads, or reading a block after another of its
+    ops reused it, fails.  The parts cover every amplitude group exactly once."""
+    from op_emulator import OP_AMP
+    wl = WORKLOADS[name]
+    mom, a, rh, rc = make_inputs(wl, nevt)
+    em = Emulator(wl.process)
+    amps = [i for i, op in enumerate(em.P.ops) if op[0] == OP_AMP]
+    for nparts, parts in em.P.splits.items():
+        assert 1 <= len(parts) <= nparts
+        assert sorted(i for p in parts for i in p if em.P.ops[i][0] == OP_AMP) == amps
+        for fix in (0, 1 << (em.P.npar - 1)):
+            _check(wl, mom, a, rh, rc, em.evaluate_parts(mom, a, parts, fix, rh, rc))
