@@ -242,7 +242,9 @@ def extra_modes(pkg, proc, M, A, RH, RC, nevt, stream):
 
 
 def extra_ggttggg(pkg, dev, stream):
-    """g g > t t~ g g g, 2^18 events: float64, mixed float32 colour sum, float32 path."""
+    """g g > t t~ g g g, 2^18 events: float64, mixed float32 colour sum, the two tensor-core colour
+    sums (tcgen05 tf32 and bf16x3, fused into the amplitude kernel) and the float32 path, 3 timed
+    steps after 1 warm-up each."""
     import numpy as np
     import torch
     from phasespace import WORKLOADS, make_inputs
@@ -252,12 +254,42 @@ def extra_ggttggg(pkg, dev, stream):
     M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
     proc = pkg.Process(wl.process, device=dev.index)
     out = {"nevt": wl.nevt, "ndiagrams": proc.ndiagrams, "ncol": proc.ncol, "ngood": proc.ngood}
-    for name in ("fp64", "mixed_fp32", "float"):
+    for name in ("fp64", "mixed_fp32", "mixed_tf32", "mixed_bf16x3", "float"):
         mode = pkg.MODES[name]
-        ms = _timed(lambda: proc.compute(M, A, RH, RC, mode=mode, stream=stream), 1, 1, stream)
+        ms = _timed(lambda: proc.compute(M, A, RH, RC, mode=mode, stream=stream), 3, 1, stream)
         out[name] = {"value": wl.nevt / (ms * 1e-3), "unit": "events/s", "ms_per_step": ms,
                      "fp64_flops_per_event": proc.fp64_flops_per_event(mode)}
     return out
+
+
+def extra_small_batches(pkg, dev, stream):
+    """Batches too small to fill the thread-per-event grid (the paper's O(1000)-event madevent
+    jobs): ms per launch of the whole-event thread kernel, the block-per-event kernel (where the
+    process has one), the helicity-parallel and diagram-split kernels and AUTO's choice, FP64."""
+    import numpy as np
+    import torch
+    from phasespace import WORKLOADS, make_inputs
+    kernels = (("thread", 1), ("cta", 2), ("helicity", 4), ("split", 5), ("auto", 0))
+    out = []
+    for name, sizes in (("ggttgg", (2048, 16384)), ("ggttggg", (512, 4096))):
+        wl = WORKLOADS[name]
+        mom, a, rh, rc = make_inputs(wl, max(sizes))
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+        M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
+        proc = pkg.Process(wl.process, device=dev.index)
+        for n in sizes:
+            row = {"process": name, "nevt": n, "ms": {}}
+            for kname, k in kernels:
+                try:
+                    proc.set_kernel(k)
+                except pkg.MgxError:
+                    continue
+                row["ms"][kname] = _timed(lambda: proc.compute(M[:n], A[:n], RH[:n], RC[:n], stream=stream),
+                                          2 if name == "ggttgg" else 1, 1, stream)
+            proc.set_kernel(0)
+            row["auto_launches"] = proc.kernel_launches(n)
+            out.append(row)
+    return {"rows": out}
 
 
 def extra_eemumu(pkg, dev, stream):
@@ -546,6 +578,7 @@ def run_gpu(args):
             extras = {}
             for key, fn in (("ggttgg_modes", lambda: extra_modes(pkg, proc, M, A, RH, RC, nevt, stream)),
                             ("ggttggg", lambda: extra_ggttggg(pkg, dev, stream)),
+                            ("small_batches", lambda: extra_small_batches(pkg, dev, stream)),
                             ("eemumu", lambda: extra_eemumu(pkg, dev, stream)),
                             ("batched", lambda: extra_batched(pkg, dev, stream)),
                             ("surrogate_unweighting", lambda: extra_surrogate(pkg, dev)),

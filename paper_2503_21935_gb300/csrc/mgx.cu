@@ -1004,19 +1004,25 @@ void build_work_model(mgx_process* pr) {
 
 enum { PLAN_ANY = 0, PLAN_HEL = 1, PLAN_SPLIT = 2 };
 
-// The plan of least estimated time = passes of the persistent grid x the work of the busiest thread
-// (plus, for a diagram split, the combine step: one thread per event and helicity).  PLAN_ANY keeps
-// the whole-event thread kernel unless another plan is estimated at least 1.33x faster; PLAN_HEL
-// and PLAN_SPLIT return the best plan of that kind.
+// Time model of a plan on the GB300, from the float64 thread kernel's measured timings: a thread
+// alone on an SM executes about one work unit (float64 instruction of the work model) per 60 ns,
+// and the full grid about 5.2e11 units per second (152 SMs), scaled by the SM count.  A plan's time
+// is the larger of its busiest thread's latency and its total work at the full-grid rate.
+constexpr double kSecPerUnitLatency = 6.0e-8;
+constexpr double kUnitsPerSecPerSm = 5.2e11 / 152;
+
+// The plan of least estimated time (plus, for a diagram split, the combine step: one thread per
+// event and helicity).  PLAN_ANY keeps the whole-event thread kernel unless another plan is
+// estimated at least 1.33x faster; PLAN_HEL and PLAN_SPLIT return the best plan of that kind.
 HelPlan best_plan(const mgx_process* pr, int64_t nevt, int mode, int kind) {
-  const int bps = mode == MGX_FLOAT ? 2 * pr->blocks_per_sm : pr->blocks_per_sm;
-  const double cap = (double)sm_count(pr->device) * bps * kThreads;
   const int nf = 1 << pr->prog->npar;
   const double n = pr->prog->ncol;
   const double colour = mode == MGX_FP64 ? n * n + 3 * n : 2 * n;
   const double ngood = (double)pr->good.size();
-  auto passes = [&](double items) { return std::ceil(items / cap); };
-  const double t_thread = passes((double)nevt) * (pr->cur_work[0][0] + (pr->amp_work[0][0] + colour) * pr->most[0]);
+  const double rate = kUnitsPerSecPerSm * sm_count(pr->device) * (mode == MGX_FLOAT ? 2.0 : 1.0);
+  auto time = [&](double wmax, double wtotal) { return std::max(wmax * kSecPerUnitLatency, wtotal / rate); };
+  const double w1 = pr->cur_work[0][0] + (pr->amp_work[0][0] + colour) * ngood;
+  const double t_thread = time(w1, w1 * (double)nevt);
   HelPlan best;
   double tb = -1.0;
   for (int sidx = 0; sidx < 4; ++sidx) {
@@ -1026,12 +1032,19 @@ HelPlan best_plan(const mgx_process* pr, int64_t nevt, int mode, int kind) {
     for (int F = sidx == 0 ? 1 : 0; F < nf; ++F) {
       const int k = __builtin_popcount((unsigned)F);
       if (k > 6) continue;
-      double work = 0.0;
-      for (int d = 0; d < np; ++d)
-        work = std::max(work, pr->cur_work[sidx][(size_t)d * nf + F] +
-                                  (pr->amp_work[sidx][d] + (sidx == 0 ? colour : 0.0)) * pr->most[F]);
-      double t = passes((double)nevt * np * (double)(1 << k)) * work;
-      if (sidx > 0) t += passes((double)nevt * ngood) * (colour + 2.0 * n * np);
+      const double groups = (double)(1 << k);
+      double wmax = 0.0, wsum = 0.0;
+      for (int d = 0; d < np; ++d) {
+        const double cur = pr->cur_work[sidx][(size_t)d * nf + F];
+        const double amp = pr->amp_work[sidx][d] + (sidx == 0 ? colour : 0.0);
+        wmax = std::max(wmax, cur + amp * pr->most[F]);
+        wsum += groups * cur + amp * ngood;
+      }
+      double t = time(wmax, wsum * (double)nevt);
+      if (sidx > 0) {
+        const double wc = colour + 2.0 * n * np;     // combine: one thread per (event, helicity)
+        t += time(wc, wc * (double)nevt * ngood);
+      }
       if (tb < 0.0 || t < tb) {
         tb = t;
         best = HelPlan{k, F, sidx, np};

@@ -88,17 +88,21 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 // Wait for completion of the phase with the given parity; gives up after timeout_ns of wall
 // time or max_iter polls, whichever comes first.  Returns false on time-out.
+// The poll is the non-blocking test_wait with a short sleep between polls: a try_wait (potentially
+// blocking) that sees the phase incomplete suspends the thread for a system-dependent time, and
+// measured on the GB300 that cost about half a millisecond per wait on a tcgen05.commit.
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, uint64_t timeout_ns = 1000000000ull,
                                           uint32_t max_iter = 1u << 26) {
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t i = 0; i < max_iter; ++i) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(smem_u32(m)), "r"(parity)
         : "memory");
     if (done) return true;
+    if (i >= 8) __nanosleep(32);
     if ((i & 255) == 255 && globaltimer_ns() - t0 > timeout_ns) return false;
   }
   return false;
