@@ -182,6 +182,9 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
 enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2, MGX_KERNEL_THREAD_SMEM = 3,
                   MGX_KERNEL_HELICITY = 4, MGX_KERNEL_SPLIT = 5 };
 int mgx_process_set_kernel(mgx_process* proc, int kernel);  /* INVALID_ARGUMENT if unusable */
+/* The kernel a compute of nevt events in `mode` runs with the current settings (AUTO resolved), and
+ * for HELICITY / SPLIT the number of helicity groups and diagram parts per event (else 1, 1). */
+int mgx_process_plan(const mgx_process* proc, int64_t nevt, int mode, int* kernel, int* groups, int* parts);
 /* the kernel set; for AUTO, THREAD (the choice for throughput batches; AUTO picks CTA or
  * THREAD_SMEM per call for small batches, as above) */
 int mgx_process_get_kernel(const mgx_process* proc);

@@ -63,6 +63,7 @@ def lib():
             "mgx_kernel_launches": (I, [P, I64, I]),
             "mgx_process_set_kernel": (I, [P, I]),
             "mgx_process_get_kernel": (I, [P]),
+            "mgx_process_plan": (I, [P, I64, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "mgx_process_set_blocks_per_sm": (I, [P, I]),
             "mgx_process_device_errors": (I, [P, ctypes.POINTER(I), I]),
             "mgx_process_set_tc_wait_test": (I, [P, I, D]),
@@ -423,6 +424,13 @@ class Process:
     @property
     def kernel(self):
         return lib().mgx_process_get_kernel(self._h)
+
+    def plan(self, nevt, mode=MGX_FP64):
+        """(kernel, helicity groups, diagram parts) a compute of nevt events would run."""
+        k, g, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().mgx_process_plan(self._h, nevt, mode, ctypes.byref(k), ctypes.byref(g), ctypes.byref(d)),
+               "mgx_process_plan")
+        return k.value, g.value, d.value
 
     def set_blocks_per_sm(self, n):
         _check(lib().mgx_process_set_blocks_per_sm(self._h, n), "mgx_process_set_blocks_per_sm")

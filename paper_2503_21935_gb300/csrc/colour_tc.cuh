@@ -100,22 +100,36 @@ __device__ bool tc_colour_sums(const KParams& P, const TcArgs& A, const JW& W, b
     for (int part = 0; part < 2; ++part) {
       const int jb = P.jamp_off + 2 * ncol * ih + part;
       size_t boff = 0;
+      float xv[kTcKc];   // the last staged chunk of this thread's row (all of it for ncol <= 32)
       for (int c = 0; c < A.nchunk; ++c) {
         const int k0 = c * kTcKc;
         const int kc = A.kpad - k0 < kTcKc ? A.kpad - k0 : kTcKc;
         const size_t bbytes = (size_t)F::kBParts * A.npad * kc * F::kElem;
-        // this thread's row of the chunk, rounded to float32 and split into parts
-        for (int k = 0; k < kc; ++k) {
-          const int kk = k0 + k;
-          const float x = (valid && kk < ncol) ? __double2float_rn(W[jb + 2 * kk]) : 0.0f;
-          F::split(x, a, umma::kmajor_offset((uint32_t)t, (uint32_t)k, (uint32_t)kc, F::kElem));
-        }
-        // the colour matrix's chunk (already in canonical layout)
+        // the colour matrix's chunk (already in canonical layout; at most 16 KB = 8 pieces a thread)
         {
           const uint4* src = reinterpret_cast<const uint4*>(A.bchunks + boff);
           uint4* dst = reinterpret_cast<uint4*>(b);
-          for (int i = t; i < (int)(bbytes / 16); i += kTcRows) dst[i] = __ldg(src + i);
+          const int nv = (int)(bbytes / 16);
+          for (int q0 = 0; q0 < 8; q0 += 4) {
+            uint4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (t + (q0 + q) * kTcRows < nv) v[q] = __ldg(src + t + (q0 + q) * kTcRows);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (t + (q0 + q) * kTcRows < nv) dst[t + (q0 + q) * kTcRows] = v[q];
+          }
         }
+        // this thread's row of the chunk, rounded to float32: every load issued before any store, so
+        // their latencies overlap; then split into parts
+#pragma unroll
+        for (int k = 0; k < kTcKc; ++k) {
+          const int kk = k0 + k;
+          xv[k] = (valid && k < kc && kk < ncol) ? __double2float_rn(W[jb + 2 * kk]) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kTcKc; ++k)
+          if (k < kc) F::split(xv[k], a, umma::kmajor_offset((uint32_t)t, (uint32_t)k, (uint32_t)kc, F::kElem));
         umma::fence_proxy_async_smem();
         umma::fence_before_sync();
         __syncthreads();
@@ -143,15 +157,33 @@ __device__ bool tc_colour_sums(const KParams& P, const TcArgs& A, const JW& W, b
         umma::fence_after_sync();
         boff += bbytes;
       }
-      // epilogue: this thread's row of Y (tensor-memory lane t), dotted with its float32 jamps
-      for (int n0 = 0; n0 < A.npad; n0 += 8) {
-        float y[8];
-        umma::tmem_ld8(tmem + lane_base + (uint32_t)n0, y);
-        umma::tmem_wait_ld();
+      // epilogue: this thread's row of Y (tensor-memory lane t), dotted with its float32 jamps: those
+      // still in registers when the contraction was one chunk (npad <= 32), else reloaded 16 at a time
+      // (loads issued together)
+      if (A.nchunk == 1) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int n = n0 + j;
-          if (valid && n < ncol) acc = fmaf(__double2float_rn(W[jb + 2 * n]), y[j], acc);
+        for (int n0 = 0; n0 < kTcKc; n0 += 16) {
+          if (n0 < A.npad) {
+            float y[16];
+            umma::tmem_ld16(tmem + lane_base + (uint32_t)n0, y);
+            umma::tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (n0 + q < ncol) acc = fmaf(xv[n0 + q], y[q], acc);
+          }
+        }
+      } else {
+        for (int n0 = 0; n0 < A.npad; n0 += 16) {
+          float xe[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            xe[q] = (valid && n0 + q < ncol) ? __double2float_rn(W[jb + 2 * (n0 + q)]) : 0.0f;
+          float y[16];
+          umma::tmem_ld16(tmem + lane_base + (uint32_t)n0, y);
+          umma::tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (n0 + q < ncol) acc = fmaf(xe[q], y[q], acc);
         }
       }
       umma::fence_before_sync();   // tensor-memory reads done before the next round's MMAs

@@ -189,7 +189,10 @@ __device__ inline void eval_amplitudes(const KParams& P, const double* pe, const
   using T = Real<R>;
   const double gs = 1.0;                                   // g_s^(2p) applied to |M|^2 later
   if (kSplit || P.jamp_zero)
-    for (int i = 0; i < 2 * P.ncol * P.ngood; ++i) W[P.jamp_off + i] = T::from(0.0);
+    for (int ih = 0; ih < P.ngood; ++ih) {
+      if (!hs.ok(P.good[ih])) continue;                 // only the helicities this thread computes
+      for (int i = 0; i < 2 * P.ncol; ++i) W[P.jamp_off + 2 * P.ncol * ih + i] = T::from(0.0);
+    }
   const int nloop = kSplit ? nlist : P.nops;
   for (int li = 0; li < nloop; ++li) {
     const int iop = kSplit ? __ldg(list + li) : li;
@@ -504,7 +507,16 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 
     R* out = pj + (e * nparts + d) * (int64_t)P.ngood * nj;
     for (int ih = 0; ih < P.ngood; ++ih) {
       if (!hs.ok(P.good[ih])) continue;
-      for (int k = 0; k < nj; ++k) out[ih * nj + k] = W[P.jamp_off + ih * nj + k];
+      // 8 loads issued before their stores (a store between loads would serialise their latencies)
+      for (int k0 = 0; k0 < nj; k0 += 8) {
+        R v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (k0 + q < nj) v[q] = W[P.jamp_off + ih * nj + k0 + q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (k0 + q < nj) out[ih * nj + k0 + q] = v[q];
+      }
     }
   }
 }
@@ -1630,6 +1642,25 @@ int mgx_process_get_kernel(const mgx_process* pr) {
   if (use_cta(pr, pr->kp)) return MGX_KERNEL_CTA;
   if (pr->kernel == MGX_KERNEL_HELICITY || pr->kernel == MGX_KERNEL_SPLIT) return pr->kernel;
   return pr->kernel == MGX_KERNEL_THREAD_SMEM ? MGX_KERNEL_THREAD_SMEM : MGX_KERNEL_THREAD;
+}
+
+int mgx_process_plan(const mgx_process* pr, int64_t nevt, int mode, int* kernel, int* groups, int* parts) {
+  if (!pr || nevt < 0 || !mode_ok(mode)) return MGX_ERR_INVALID_ARGUMENT;
+  int k = MGX_KERNEL_THREAD, g = 1, d = 1;
+  HelPlan hp;
+  if (nevt > 0 && !mode_tc(mode)) {
+    if (use_cta_kernel(pr, pr->kp, nevt, mode)) k = MGX_KERNEL_CTA;
+    else if (use_smem_ws(pr, pr->kp, nevt, mode)) k = MGX_KERNEL_THREAD_SMEM;
+    else if (use_hel_kernel(pr, pr->kp, nevt, mode, &hp)) {
+      k = hp.split ? MGX_KERNEL_SPLIT : MGX_KERNEL_HELICITY;
+      g = 1 << hp.gshift;
+      d = hp.nparts;
+    }
+  }
+  if (kernel) *kernel = k;
+  if (groups) *groups = g;
+  if (parts) *parts = d;
+  return MGX_OK;
 }
 
 int mgx_process_device_errors(mgx_process* pr, int* count, int reset) {
