@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const WS W{ws + tid, nthreads};
   if (threadIdx.x == 0) umma::mbar_init(mbar, 1);
-  if (threadIdx.x < 32) umma::tmem_alloc(tslot, A.tcols);
+  if (threadIdx.x < 32) umma::tmem_alloc_once(tslot, A.tcols);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -397,7 +397,6 @@ __global__ void __launch_bounds__(kThreads, 4)
   umma::fence_after_sync();
   if (threadIdx.x < 32) {
     umma::tmem_dealloc(tmem, A.tcols);
-    umma::tmem_relinquish();
   }
 }
 

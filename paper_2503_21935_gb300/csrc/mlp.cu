@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
   uint32_t tcols = 32;
   while ((int)tcols < NT) tcols <<= 1;
   if (tid == 0) umma::mbar_init(mbar, 1);
-  if (warp == 0) umma::tmem_alloc(tslot, tcols);
+  if (warp == 0) umma::tmem_alloc_once(tslot, tcols);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
   umma::fence_after_sync();
   if (warp == 0) {
     umma::tmem_dealloc(tmem, tcols);
-    umma::tmem_relinquish();
   }
 }
 
@@ -400,7 +399,7 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
     sbias[i] = g.bias[i];
     sw4[i] = g.w4 ? g.w4[i] : 0.0f;
   }
-  if (warp == 0) umma::tmem_alloc(tslot, 512);
+  if (warp == 0) umma::tmem_alloc_once(tslot, 512);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -532,7 +531,6 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
   umma::fence_after_sync();
   if (warp == 0) {
     umma::tmem_dealloc(tmem, 512);
-    umma::tmem_relinquish();
   }
 }
 

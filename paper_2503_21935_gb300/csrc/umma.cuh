@@ -39,12 +39,21 @@ __host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t M, uint32_t 
 }
 
 // ---- tensor memory
+// A CTA that may still allocate holds the SM's allocation permit: other CTAs' tcgen05.alloc on that SM
+// waits until the permit is relinquished.  Every kernel here allocates once, so it relinquishes the
+// permit right after its allocation (tmem_alloc_once); otherwise the persistent CTAs of one SM run one
+// after another (measured on the GB300: 2.3x slower with 4 CTAs per SM).
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
                : "memory");
 }
 __device__ __forceinline__ void tmem_relinquish() {
   asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+// allocate ncols columns for the CTA (one warp) and give up the permit to allocate again
+__device__ __forceinline__ void tmem_alloc_once(uint32_t* slot, uint32_t ncols) {
+  tmem_alloc(slot, ncols);
+  tmem_relinquish();
 }
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
@@ -88,9 +97,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 // Wait for completion of the phase with the given parity; gives up after timeout_ns of wall
 // time or max_iter polls, whichever comes first.  Returns false on time-out.
-// The poll is the non-blocking test_wait with a short sleep between polls: a try_wait (potentially
-// blocking) that sees the phase incomplete suspends the thread for a system-dependent time, and
-// measured on the GB300 that cost about half a millisecond per wait on a tcgen05.commit.
+// The poll is the non-blocking test_wait with a short sleep between polls, so the time limit is
+// checked on the wall clock whatever the hardware's suspend time for a blocking try_wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, uint64_t timeout_ns = 1000000000ull,
                                           uint32_t max_iter = 1u << 26) {
   const uint64_t t0 = globaltimer_ns();
