@@ -162,7 +162,7 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
  * thread block per event with the event's currents in shared memory; available when the
  * process's current store fits in shared memory and ncol <= 32 (MGX_FP64, MGX_MIXED_FP32), and
  * what AUTO picks in those modes for a batch too small to fill the thread kernel's grid: at most
- * 48 events per SM, or 8 per SM for a process that has THREAD_SMEM (no caller workspace needed).
+ * 64 events per SM, or 8 per SM for a process that has THREAD_SMEM (no caller workspace needed).
  * THREAD_SMEM: the thread-per-event kernel with each thread's workspace in shared memory
  * (64 threads per block, no caller workspace needed); available for small processes (e+ e- >
  * mu+ mu-, g g > t t~), and what AUTO picks otherwise when the whole batch fits one block per SM

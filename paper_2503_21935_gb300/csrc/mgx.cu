@@ -931,11 +931,13 @@ bool use_smem_ws(const mgx_process* pr, const KParams& kp, int64_t nevt, int mod
 // one thread takes for one event, and one block per event (the CTA kernel) takes a fraction of
 // that.  Measured crossovers on GB300 in FP64: about 9.5k events (g g > t t~ g), 12k (g u~ >
 // ta+ ta- g g u~) and 19k (g g > t t~ g g) against the thread kernel, about 2k against the
-// shared-memory thread kernel of the small processes; the limits below stay under them.
+// shared-memory thread kernel of the small processes; at 8192 events the CTA kernel also beats
+// the helicity-parallel and split plans for those processes (12.3 vs 15.7 ms for g g > t t~ g g);
+// the limits below stay under the crossovers.
 bool use_cta_kernel(const mgx_process* pr, const KParams& kp, int64_t nevt, int mode) {
   if (!mode_f64(mode) || !cta_usable(pr, kp)) return false;
   if (pr->kernel == MGX_KERNEL_CTA) return true;
-  const int64_t per_sm = smem_usable(kp, mode) ? 8 : 48;
+  const int64_t per_sm = smem_usable(kp, mode) ? 8 : 64;
   return pr->kernel == MGX_KERNEL_AUTO && nevt <= per_sm * sm_count(pr->device);
 }
 
@@ -1042,7 +1044,9 @@ HelPlan best_plan(const mgx_process* pr, int64_t nevt, int mode, int kind) {
     if (sidx > 0 && np < 2) continue;
     for (int F = sidx == 0 ? 1 : 0; F < nf; ++F) {
       const int k = __builtin_popcount((unsigned)F);
-      if (k > 6) continue;
+      // a split thread zeroes, updates and copies out the partial jamps of all its group's
+      // helicities; measured, splits pay off only with at least 8 helicity groups
+      if (k > 6 || (sidx > 0 && k < 3)) continue;
       const double groups = (double)(1 << k);
       double wmax = 0.0, wsum = 0.0;
       for (int d = 0; d < np; ++d) {
