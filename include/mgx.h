@@ -300,10 +300,24 @@ int mgx_uniforms(int64_t n, int64_t first, uint64_t seed, uint32_t stream_id, do
 int mgx_rambo(int64_t n, int64_t first, double sqrts, int nfinal, const double* masses_dev, uint64_t seed,
               double* momenta, double* weight, void* stream);
 
+/* The same events first + index[r], r < m (index: DEVICE int32 [m]): momenta [m][nfinal+2][4], weight [m],
+ * bit-identical to the corresponding rows of mgx_rambo (regenerating selected events in float64). */
+int mgx_rambo_indexed(int64_t m, const int32_t* index, int64_t first, double sqrts, int nfinal,
+                      const double* masses_dev, uint64_t seed, double* momenta, double* weight, void* stream);
+/* RAMBO in float32 (the same random numbers; momenta and weight to float32 accuracy): cheap proposals
+ * for the first stage of the two-stage unweighting, whose survivors are regenerated in float64. */
+int mgx_rambo_f32(int64_t n, int64_t first, double sqrts, int nfinal, const double* masses_dev, uint64_t seed,
+                  float* momenta, float* weight, void* stream);
+
 /* Generator-level cuts: pass[i] = 1 when every particle listed in list_dev[nlist] (indices into
  * npar) has pT > ptmin and |eta| < etamax and every listed pair has dR > drmin, else 0. */
 int mgx_cuts(int64_t n, int npar, const double* momenta, int nlist, const int* list_dev, double ptmin,
              double etamax, double drmin, uint8_t* pass, void* stream);
+/* The cuts on float32 momenta with thresholds widened by a relative margin (0 <= margin < 0.5):
+ * pT > ptmin (1 - margin), |eta| < etamax (1 + margin), dR > drmin (1 - margin), so that the region
+ * they accept contains the one the float64 cuts accept (for margins well above float32 rounding). */
+int mgx_cuts_f32(int64_t n, int npar, const float* momenta, int nlist, const int* list_dev, double ptmin,
+                 double etamax, double drmin, double margin, uint8_t* pass, void* stream);
 
 /* ---- learned surrogate of log|M|^2 (two-stage unweighting) ----
  * MLP x[24] -> 4 x 256 SiLU -> scalar; float32 master weights, bfloat16 tensor-core products
@@ -331,6 +345,9 @@ int mgx_mlp_forward(mgx_mlp* net, int64_t n, const float* x, float* y, void* ws,
  * feature array. */
 int mgx_mlp_forward_momenta(mgx_mlp* net, int64_t n, const double* momenta, double scale, float* y, void* ws,
                             size_t wsb, void* stream);
+/* The same from float32 momenta (inputs float32(momenta x (1/scale))). */
+int mgx_mlp_forward_momenta_f32(mgx_mlp* net, int64_t n, const float* momenta, double scale, float* y, void* ws,
+                                size_t wsb, void* stream);
 /* Gradient of the mean squared error over one batch of n rows (targets t[n]) into grad
  * (DEVICE, num_params floats, may be NULL) and the loss into loss (DEVICE float, may be NULL). */
 int mgx_mlp_gradients(mgx_mlp* net, int n, const float* x, const float* t, float* grad, float* loss, void* ws,
@@ -363,6 +380,9 @@ int mgx_features(int64_t n, int ncomp, const double* momenta, double scale, floa
 /* s = exp(mean + sd y) * wps * pass (wps, pass may be NULL). */
 int mgx_surrogate_weight(int64_t n, const float* y, double mean, double sd, const double* wps,
                          const uint8_t* pass, double* s, void* stream);
+/* The same with a float32 phase-space weight wps (from mgx_rambo_f32). */
+int mgx_surrogate_weight_f32(int64_t n, const float* y, double mean, double sd, const float* wps,
+                             const uint8_t* pass, double* s, void* stream);
 /* w = me * wps * pass (wps, pass may be NULL). */
 int mgx_exact_weight(int64_t n, const double* me, const double* wps, const uint8_t* pass, double* w,
                      void* stream);

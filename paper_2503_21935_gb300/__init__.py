@@ -72,6 +72,11 @@ def lib():
             "mgx_uniforms": (I, [I64, I64, U64, ctypes.c_uint32, P, P]),
             "mgx_rambo": (I, [I64, I64, D, I, P, U64, P, P, P]),
             "mgx_cuts": (I, [I64, I, P, I, P, D, D, D, P, P]),
+            "mgx_cuts_f32": (I, [I64, I, P, I, P, D, D, D, D, P, P]),
+            "mgx_rambo_indexed": (I, [I64, P, I64, D, I, P, U64, P, P, P]),
+            "mgx_rambo_f32": (I, [I64, I64, D, I, P, U64, P, P, P]),
+            "mgx_surrogate_weight_f32": (I, [I64, P, D, D, P, P, P, P]),
+            "mgx_mlp_forward_momenta_f32": (I, [P, I64, P, D, P, P, SZ, P]),
             "mgx_features": (I, [I64, I, P, D, P, P]),
             "mgx_surrogate_weight": (I, [I64, P, D, D, P, P, P, P]),
             "mgx_exact_weight": (I, [I64, P, P, P, P, P]),
@@ -159,6 +164,43 @@ def rambo(n, sqrts, masses, seed, first=0, device=0):
     _check(lib().mgx_rambo(n, first, float(sqrts), len(masses), _ptr(m), seed, _ptr(mom), _ptr(wt), _stream(dev)),
            "mgx_rambo")
     return mom, wt
+
+
+def rambo_indexed(index, first, sqrts, masses, seed, device=0):
+    """Device float64 RAMBO for events first + index[r] (int32 device tensor): (momenta, weight)."""
+    import torch
+    dev = torch.device(f"cuda:{device}")
+    m = torch.tensor(list(masses), dtype=torch.float64, device=dev)
+    n = index.shape[0]
+    mom = torch.empty((n, len(masses) + 2, 4), dtype=torch.float64, device=dev)
+    wt = torch.empty(n, dtype=torch.float64, device=dev)
+    _check(lib().mgx_rambo_indexed(n, _ptr(index), first, float(sqrts), len(masses), _ptr(m), seed, _ptr(mom),
+                                   _ptr(wt), _stream(dev)), "mgx_rambo_indexed")
+    return mom, wt
+
+
+def rambo_f32(n, sqrts, masses, seed, first=0, device=0):
+    """Device float32 RAMBO (the same events as rambo, to float32 accuracy): (momenta, weight)."""
+    import torch
+    dev = torch.device(f"cuda:{device}")
+    m = torch.tensor(list(masses), dtype=torch.float64, device=dev)
+    mom = torch.empty((n, len(masses) + 2, 4), dtype=torch.float32, device=dev)
+    wt = torch.empty(n, dtype=torch.float32, device=dev)
+    _check(lib().mgx_rambo_f32(n, first, float(sqrts), len(masses), _ptr(m), seed, _ptr(mom), _ptr(wt), _stream(dev)),
+           "mgx_rambo_f32")
+    return mom, wt
+
+
+def cuts_f32(momenta, particles, ptmin, etamax, drmin, margin):
+    """Device uint8 mask of the cuts on float32 momenta with thresholds widened by `margin`."""
+    import torch
+    dev = momenta.device
+    lst = torch.tensor(list(particles), dtype=torch.int32, device=dev)
+    out = torch.empty(momenta.shape[0], dtype=torch.uint8, device=dev)
+    _check(lib().mgx_cuts_f32(momenta.shape[0], momenta.shape[1], _ptr(momenta), len(particles), _ptr(lst),
+                              float(ptmin), float(etamax), float(drmin), float(margin), _ptr(out), _stream(dev)),
+           "mgx_cuts_f32")
+    return out
 
 
 def cuts(momenta, particles, ptmin, etamax, drmin):
@@ -299,13 +341,14 @@ class Mlp:
         return y.cpu().numpy() if host else y
 
     def forward_momenta(self, momenta, scale, out=None):
-        """y[n] = network(float32(momenta / scale)) for device float64 momenta [n, 6, 4]."""
+        """y[n] = network(float32(momenta / scale)) for device momenta [n, 6, 4] (float64 or float32)."""
         import torch
         n = momenta.shape[0]
         y = out if out is not None else torch.empty(n, dtype=torch.float32, device=momenta.device)
         ws = self._workspace(n, False)
-        _check(lib().mgx_mlp_forward_momenta(self._h, n, _ptr(momenta), float(scale), _ptr(y), _ptr(ws), ws.numel(),
-                                             _stream(momenta.device)), "mgx_mlp_forward_momenta")
+        f = lib().mgx_mlp_forward_momenta_f32 if momenta.dtype == torch.float32 else lib().mgx_mlp_forward_momenta
+        _check(f(self._h, n, _ptr(momenta), float(scale), _ptr(y), _ptr(ws), ws.numel(), _stream(momenta.device)),
+               "mgx_mlp_forward_momenta")
         return y
 
     def gradients(self, x, t):

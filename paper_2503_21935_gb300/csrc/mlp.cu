@@ -319,8 +319,9 @@ constexpr int kInfThreads = 192;   // warps 0-3: epilogue (tensor-memory lanes 0
 constexpr int kInfStages = 4;      // operand chunks in flight
 constexpr int64_t kInferRows = 1 << 22;   // rows per pass of the layer kernels (workspace ~1.1 KB / row)
 
-// x tiles [tile][128 x 32] (canonical, K = 32, columns 24..31 zero) from float32 rows x [n][24] or
-// from float64 momenta [n][24] scaled by inv_scale (rounded to float32 first, then to bf16)
+// x tiles [tile][128 x 32] (canonical, K = 32, columns 24..31 zero) from float32 rows x [n][24] times
+// inv_scale (in float32) or from float64 momenta [n][24] times inv_scale (rounded to float32 first,
+// then to bf16)
 __global__ void pack_tiles_kernel(int64_t n, int64_t ntiles, const float* __restrict__ x, const double* __restrict__ mom,
                                   double inv_scale, __nv_bfloat16* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,7 +335,7 @@ __global__ void pack_tiles_kernel(int64_t n, int64_t ntiles, const float* __rest
   for (int q = 0; q < 8; ++q) {
     const int c = grp * 8 + q;
     float f = 0.0f;
-    if (row < n && c < kNin) f = mom ? (float)(mom[row * kNin + c] * inv_scale) : x[row * kNin + c];
+    if (row < n && c < kNin) f = mom ? (float)(mom[row * kNin + c] * inv_scale) : x[row * kNin + c] * (float)inv_scale;
     v[q] = __float2bfloat16_rn(f);
   }
   *reinterpret_cast<uint4*>(out + tile * kRows * kK0 + umma::kmajor_offset(r, grp * 8, kK0, 2) / 2) =
@@ -831,6 +832,13 @@ int mgx_mlp_forward(mgx_mlp* net, int64_t n, const float* x, float* y, void* ws,
   if (!net || n < 0 || (n > 0 && (!x || !y))) return MGX_ERR_INVALID_ARGUMENT;
   if (n == 0) return MGX_OK;
   return infer(net, n, x, nullptr, 1.0, y, ws, wsb, (cudaStream_t)stream);
+}
+
+int mgx_mlp_forward_momenta_f32(mgx_mlp* net, int64_t n, const float* momenta, double scale, float* y, void* ws,
+                                size_t wsb, void* stream) {
+  if (!net || n < 0 || (n > 0 && (!momenta || !y)) || !(scale > 0.0)) return MGX_ERR_INVALID_ARGUMENT;
+  if (n == 0) return MGX_OK;
+  return infer(net, n, momenta, nullptr, scale, y, ws, wsb, (cudaStream_t)stream);
 }
 
 int mgx_mlp_forward_momenta(mgx_mlp* net, int64_t n, const double* momenta, double scale, float* y, void* ws,

@@ -36,6 +36,16 @@ __global__ void surrogate_weight_kernel(int64_t n, const float* __restrict__ y, 
   s[i] = ok ? exp(mean + sd * (double)y[i]) * (wps ? wps[i] : 1.0) : 0.0;
 }
 
+// the same from a float32 phase-space weight (the float32 proposals of the first stage)
+__global__ void surrogate_weight_f32_kernel(int64_t n, const float* __restrict__ y, double mean, double sd,
+                                            const float* __restrict__ wps, const uint8_t* __restrict__ pass,
+                                            double* __restrict__ s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool ok = pass == nullptr || pass[i];
+  s[i] = ok ? exp(mean + sd * (double)y[i]) * (wps ? (double)wps[i] : 1.0) : 0.0;
+}
+
 // exact weight w = me * wps * pass
 __global__ void exact_weight_kernel(int64_t n, const double* __restrict__ me, const double* __restrict__ wps,
                                     const uint8_t* __restrict__ pass, double* __restrict__ w) {
@@ -143,6 +153,15 @@ int mgx_surrogate_weight(int64_t n, const float* y, double mean, double sd, cons
   if (n < 0 || (n > 0 && (!y || !s))) return MGX_ERR_INVALID_ARGUMENT;
   if (n == 0) return MGX_OK;
   surrogate_weight_kernel<<<grid(n), kBlock, 0, (cudaStream_t)stream>>>(n, y, mean, sd, wps, pass, s);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+int mgx_surrogate_weight_f32(int64_t n, const float* y, double mean, double sd, const float* wps, const uint8_t* pass,
+                             double* s, void* stream) {
+  if (n < 0 || (n > 0 && (!y || !s))) return MGX_ERR_INVALID_ARGUMENT;
+  if (n == 0) return MGX_OK;
+  surrogate_weight_f32_kernel<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, (cudaStream_t)stream>>>(
+      n, y, mean, sd, wps, pass, s);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
 

@@ -8,6 +8,12 @@ method runs in the library's kernels (phase space, cuts, matrix elements, networ
 accept/reject, compaction); this module sequences the calls and holds device buffers (PyTorch
 tensors).
 
+Stage 1 runs on float32 proposals: RAMBO and the cuts (thresholds widened by a small margin, so that
+every event the exact cuts accept is proposed) in single precision, the surrogate weight from those
+momenta.  Only the stage-1 survivors are regenerated in float64 (the same random numbers, by event
+index) for the exact cuts, phase-space weight and |M|^2 of stage 2.  The proposal weight s only has
+to be positive wherever the exact weight is, so the unweighted sample stays unbiased.
+
 Data parallelism (one replica per GPU, `dist`): each rank generates and unweights its own
 contiguous range of events.  Every random number of the accept/reject steps is keyed by the
 event's global index, and the maxima come from the weights of all ranks' calibration events,
@@ -20,8 +26,14 @@ import ctypes
 
 import numpy as np
 
-from . import (Mlp, MgxError, Process, _check, _ptr, _stream, lib, rambo, cuts, uniforms, MGX_FP64)
+from . import (Mlp, MgxError, Process, _check, _ptr, _stream, lib, rambo, rambo_f32, rambo_indexed, cuts, cuts_f32,
+               uniforms, MGX_FP64)
 from . import dist as _dist
+
+# relative widening of the cut thresholds applied to the float32 proposals: far above float32
+# rounding of the cut observables (about 1e-6 relative in pT, 1e-3 absolute in eta near |eta| = 5),
+# so the proposals' accepted region contains the exact one
+PROPOSAL_CUT_MARGIN = 1e-2
 
 
 class Unweighter:
@@ -113,15 +125,28 @@ class Unweighter:
                "mgx_exact_weight")
         return w
 
+    def proposals(self, n, seed, first=0):
+        """Float32 momenta, phase-space weights and widened-cut mask of events first .. first+n-1."""
+        mom, wps = rambo_f32(n, self.sqrts, self.masses, seed, first=first, device=self.dev.index)
+        lst, ptmin, etamax, drmin = self.cut
+        if lst:
+            ok = cuts_f32(mom, lst, ptmin, etamax, drmin, PROPOSAL_CUT_MARGIN)
+        else:
+            import torch
+            ok = torch.ones(n, dtype=torch.uint8, device=self.dev)
+        return mom, wps, ok
+
     def surrogate_weights(self, mom, wps, ok):
+        """s = exp(mean + sd y) wps pass, y the network on the momenta (float64, or float32 proposals)."""
         import torch
         n = mom.shape[0]
         if 4 * self.npar != 24:
             raise MgxError("the surrogate network takes 24 momentum components (6 particles)")
         y = self.net.forward_momenta(mom, 0.5 * self.sqrts)
         s = torch.empty(n, dtype=torch.float64, device=self.dev)
-        _check(lib().mgx_surrogate_weight(n, _ptr(y), self.mean, self.sd, _ptr(wps), _ptr(ok), _ptr(s),
-                                          _stream(self.dev)), "mgx_surrogate_weight")
+        f = lib().mgx_surrogate_weight_f32 if wps.dtype == torch.float32 else lib().mgx_surrogate_weight
+        _check(f(n, _ptr(y), self.mean, self.sd, _ptr(wps), _ptr(ok), _ptr(s), _stream(self.dev)),
+               "mgx_surrogate_weight")
         return s
 
     # ------------------------------------------------------------------ training
@@ -163,10 +188,11 @@ class Unweighter:
 
     # ------------------------------------------------------------------ calibration
     def calibration_sample(self, n, seed, first=0):
-        """Exact and surrogate weights (w, s) of events first .. first+n-1."""
+        """Exact and surrogate weights (w, s) of events first .. first+n-1 (s as stage 1 computes it,
+        from the float32 proposals)."""
         mom, wps, ok = self.events(n, seed, first)
         w = self._weights(self.exact_me(mom), wps, ok)
-        s = self.surrogate_weights(mom, wps, ok)
+        s = self.surrogate_weights(*self.proposals(n, seed, first))
         return w, s
 
     def set_maxima(self, w, s, q=0.999):
@@ -226,21 +252,23 @@ class Unweighter:
                 e.record(stream)
                 marks.append((name, e))
         mark("start")
-        mom, wps, ok = self.events(n, seed, first)
+        mom32, wps32, ok32 = self.proposals(n, seed, first)
         mark("phase space and cuts")
-        s = self.surrogate_weights(mom, wps, ok)
+        s = self.surrogate_weights(mom32, wps32, ok32)
         mark("features, network, surrogate weights")
         keep1, over1 = self._accept(s, None, self.s_max, uniforms(n, seed, 12, first=first, device=self.dev.index))
         idx1 = self._compact(keep1)
-        m1 = self._gather(idx1, mom)
-        wps1 = self._gather(idx1, wps)
+        # the survivors again in float64: exact momenta, phase-space weight and cuts
+        m1, wps1 = rambo_indexed(idx1, first, self.sqrts, self.masses, seed, device=self.dev.index)
+        lst, ptmin, etamax, drmin = self.cut
+        ok1 = cuts(m1, lst, ptmin, etamax, drmin) if lst else None
         s1 = self._gather(idx1, s)
         r2 = self._gather(idx1, uniforms(n, seed + 7919, 13, first=first, device=self.dev.index))
-        mark("stage-1 accept, compaction, gathers")
+        mark("stage-1 accept, compaction, float64 survivors")
         calls = self.exact_calls
         me1 = self.exact_me(m1)
         mark("exact |M|^2 of the survivors")
-        w1 = self._weights(me1, wps1, None)
+        w1 = self._weights(me1, wps1, ok1)
         keep2, over2 = self._accept(w1, s1, self.r_max, r2)
         idx2 = self._compact(keep2)
         l2 = idx2.long()

@@ -64,3 +64,39 @@ def test_cuts_match_numpy():
     ref = (pt > 20).all(axis=1) & (np.abs(eta) < 5).all(axis=1) & (dr > 0.4)
     assert np.array_equal(got, ref)
     assert 0.3 < ref.mean() < 0.99
+
+
+@pytest.mark.parametrize("masses", [[0.0, 0.0, 0.0], [173.0, 173.0, 0.0, 0.0]])
+def test_rambo_indexed_and_float32(masses):
+    """Float64 regeneration of selected events equals the corresponding rows bit for bit; the
+    float32 proposals are the same events to float32 accuracy (momenta relative to sqrt(s), weights)."""
+    import torch
+    import paper_2503_21935_gb300 as pkg
+    n, sqrts, seed, first = 1 << 16, 1500.0, 23, 77
+    mom, wt = pkg.rambo(n, sqrts, masses, seed, first=first)
+    idx = torch.tensor(np.sort(np.random.default_rng(0).choice(n, 999, replace=False)).astype(np.int32), device="cuda")
+    mi, wi = pkg.rambo_indexed(idx, first, sqrts, masses, seed)
+    assert torch.equal(mi, mom[idx.long()]) and torch.equal(wi, wt[idx.long()])
+    m32, w32 = pkg.rambo_f32(n, sqrts, masses, seed, first=first)
+    dev = ((m32.double() - mom).abs() / sqrts).amax(dim=(1, 2))
+    assert dev.median().item() < 1e-6 and dev.max().item() < 1e-3
+    assert ((w32.double() / wt - 1).abs().median()).item() < 1e-5
+
+
+def test_float32_cuts_with_margin_contain_float64_cuts():
+    """Every event the float64 cuts accept is accepted by the float32 cuts with the proposal margin
+    (so stage-1 proposals cover the exact support); the widened band is a small fraction."""
+    import torch
+    import paper_2503_21935_gb300 as pkg
+    from paper_2503_21935_gb300.surrogate import PROPOSAL_CUT_MARGIN
+    n, sqrts, seed = 1 << 21, 1500.0, 31
+    masses = [173.0, 173.0, 0.0, 0.0]
+    mom, _ = pkg.rambo(n, sqrts, masses, seed)
+    m32, _ = pkg.rambo_f32(n, sqrts, masses, seed)
+    exact = pkg.cuts(mom, [4, 5], 20.0, 5.0, 0.4).bool()
+    wide = pkg.cuts_f32(m32, [4, 5], 20.0, 5.0, 0.4, PROPOSAL_CUT_MARGIN).bool()
+    assert not (exact & ~wide).any()
+    band = (wide & ~exact).float().mean().item()
+    assert band < 0.02, band
+    same = pkg.cuts_f32(m32, [4, 5], 20.0, 5.0, 0.4, 0.0).bool()
+    assert (same != exact).float().mean().item() < 1e-4
