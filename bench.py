@@ -159,12 +159,20 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the translation unit of the amplitude kernels: mgx.cu, the headers it includes, the generated tables
+_KERNEL_SOURCES = ("mgx.cu", "mgx_ops.cuh", "mgx_kernel.cuh", "real.cuh", "colour_tc.cuh", "umma.cuh",
+                   os.path.join("generated", "programs.inc"))
+
+
 def _source_sha():
+    """Hash of the sources the amplitude kernels are compiled from (a traffic figure taken on other
+    sources no longer describes the kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2503_21935_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in _KERNEL_SOURCES:
+        path = os.path.join(csrc, f)
+        if os.path.exists(path):
+            h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -420,16 +420,19 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 
   const int G = 1 << gshift;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const WST<R> W{reinterpret_cast<R*>(ws) + tid, nthreads};
-  const int64_t nitems = nevt << gshift;
+  // items are numbered group-major over the events padded to whole blocks, so a block (and every
+  // warp) runs one group for consecutive events: the same variants, coalesced workspace accesses
+  const int64_t npad = (nevt + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const int64_t nitems = npad << gshift;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nitems; base += nthreads) {
-    const int64_t e0 = base >> gshift;                       // blockDim is a multiple of G
-    stage_momenta(mom, e0, min((int64_t)(blockDim.x >> gshift), nevt - e0), npar4, smem);
-    const int64_t item = base + threadIdx.x;
-    if (item >= nitems) continue;
-    const int64_t e = item >> gshift;
-    const int g = (int)(item & (G - 1));
+    const int g = (int)(base / npad);
+    const int64_t e0 = base % npad;
+    if (e0 >= nevt) continue;                                 // the whole block is padding
+    stage_momenta(mom, e0, min((int64_t)blockDim.x, nevt - e0), npar4, smem);
+    const int64_t e = e0 + threadIdx.x;
+    if (e >= nevt) continue;
     const GroupHel hs{fix, pdep(g, fix)};
-    eval_amplitudes<R>(P, smem + (threadIdx.x >> gshift) * npar4, W, hs);
+    eval_amplitudes<R>(P, smem + threadIdx.x * npar4, W, hs);
     const double scale = coupling_scale(P, alphas[e]);
     for (int ih = 0; ih < P.ngood; ++ih) {
       if (!hs.ok(P.good[ih])) continue;
@@ -486,22 +489,24 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 8 : 
                     double* __restrict__ ws, int64_t nthreads) {
   extern __shared__ double smem[];
   const int npar4 = 4 * P.npar;
-  const int per = nparts << gshift;                           // items per event
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const WST<R> W{reinterpret_cast<R*>(ws) + tid, nthreads};
-  const int64_t nitems = nevt * per;
+  // items are numbered (group, part)-major over the events padded to whole blocks, so a block (and
+  // every warp) runs one part's op list for one group over consecutive events: no divergence,
+  // coalesced workspace accesses
+  const int64_t npad = (nevt + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const int64_t nitems = (npad * nparts) << gshift;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nitems; base += nthreads) {
-    const int64_t e0 = base / per;                            // the block's items cover events e0 .. e0 + ne - 1
-    const int64_t ne = min((base + blockDim.x - 1) / per - e0 + 1, nevt - e0);
-    stage_momenta(mom, e0, ne, npar4, smem);
-    const int64_t item = base + threadIdx.x;
-    if (item >= nitems) continue;
-    const int64_t e = item / per;
-    const int d = (int)(item % nparts);
-    const int g = (int)((item / nparts) & ((1 << gshift) - 1));
+    const int gd = (int)(base / npad);
+    const int d = gd % nparts, g = gd / nparts;
+    const int64_t e0 = base % npad;
+    if (e0 >= nevt) continue;                                 // the whole block is padding
+    stage_momenta(mom, e0, min((int64_t)blockDim.x, nevt - e0), npar4, smem);
+    const int64_t e = e0 + threadIdx.x;
+    if (e >= nevt) continue;
     const GroupHel hs{fix, pdep(g, fix)};
     const int s0 = __ldg(part_start + d), s1 = __ldg(part_start + d + 1);
-    eval_amplitudes<R, GroupHel, true>(P, smem + (e - e0) * npar4, W, hs, part_ops + s0, s1 - s0);
+    eval_amplitudes<R, GroupHel, true>(P, smem + threadIdx.x * npar4, W, hs, part_ops + s0, s1 - s0);
     const int nj = 2 * P.ncol;
     R* out = pj + (e * nparts + d) * (int64_t)P.ngood * nj;
     for (int ih = 0; ih < P.ngood; ++ih) {
@@ -1084,7 +1089,10 @@ HelLayout hel_layout(const mgx_process* pr, const KParams& kp, const HelPlan& hp
   L.total = L.ws + L.pj + L.mh + L.cw;
   return L;
 }
-int64_t plan_items(const HelPlan& hp, int64_t nevt) { return (nevt * hp.nparts) << hp.gshift; }
+// items of a plan: every (group, part) over the events padded to whole 128-thread blocks
+int64_t plan_items(const HelPlan& hp, int64_t nevt) {
+  return (((nevt + kThreads - 1) / kThreads * kThreads) * hp.nparts) << hp.gshift;
+}
 
 // the helicity-parallel or diagram-split kernels: chosen explicitly, or by AUTO for a batch that
 // leaves the thread kernel's grid underfilled when the work model says a plan is clearly cheaper
