@@ -1882,13 +1882,16 @@ extern "C" int mgx_batch_autotune(mgx_batch* b, const mgx_batch_io* io, int mode
   int bb = b->blocks_per_sm;
   std::vector<int> be = b->epi;
   int rc = MGX_OK;
+  // a candidate replaces the incumbent only when at least 2% faster, so that schedules within the
+  // timing noise of each other do not make the choice vary from run to run
+  const float kGain = 0.98f;
   // stage 1: blocks per SM x one common work-item size
-  for (int bps : {2, 3, 4})
-    for (int e : {128, 512, 2048}) {
+  for (int bps : {4, 3, 2})
+    for (int e : {512, 128, 2048}) {
       std::vector<int> cand(n, e);
       float ms = 0.0f;
       if ((rc = timed(bps, cand, &ms)) != MGX_OK) break;
-      if (ms < best) { best = ms; bb = bps; be = cand; }
+      if (ms < kGain * best) { best = ms; bb = bps; be = cand; }
     }
   // stage 2: each process's work-item size in turn, the others fixed
   for (int p = 0; p < n && rc == MGX_OK; ++p)
@@ -1898,7 +1901,7 @@ extern "C" int mgx_batch_autotune(mgx_batch* b, const mgx_batch_io* io, int mode
       cand[p] = e;
       float ms = 0.0f;
       if ((rc = timed(bb, cand, &ms)) != MGX_OK) break;
-      if (ms < best) { best = ms; be = cand; }
+      if (ms < kGain * best) { best = ms; be = cand; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
