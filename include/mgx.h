@@ -162,7 +162,7 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
  * thread block per event with the event's currents in shared memory; available when the
  * process's current store fits in shared memory and ncol <= 32 (MGX_FP64, MGX_MIXED_FP32), and
  * what AUTO picks in those modes for a batch too small to fill the thread kernel's grid: at most
- * 64 events per SM, or 8 per SM for a process that has THREAD_SMEM (no caller workspace needed).
+ * 32 events per SM, or 8 per SM for a process that has THREAD_SMEM (no caller workspace needed).
  * THREAD_SMEM: the thread-per-event kernel with each thread's workspace in shared memory
  * (64 threads per block, no caller workspace needed); available for small processes (e+ e- >
  * mu+ mu-, g g > t t~), and what AUTO picks otherwise when the whole batch fits one block per SM
@@ -177,7 +177,7 @@ int mgx_compute_host(mgx_process* proc, int64_t nevt, const double* momenta, con
  * jamps, a combine kernel sums them per (event, helicity) and forms the colour sum, and the finish
  * kernel selects (same modes; the split and the fixed particles from the same work model).  AUTO
  * takes HELICITY or SPLIT for a batch that leaves the thread kernel's grid underfilled when that
- * model predicts at least a 1.33x gain and the batch is too large for CTA / THREAD_SMEM.  All give
+ * model predicts at least a 1.1x gain and the batch is too large for CTA / THREAD_SMEM.  All give
  * identical results up to float64 rounding. */
 enum mgx_kernel { MGX_KERNEL_AUTO = 0, MGX_KERNEL_THREAD = 1, MGX_KERNEL_CTA = 2, MGX_KERNEL_THREAD_SMEM = 3,
                   MGX_KERNEL_HELICITY = 4, MGX_KERNEL_SPLIT = 5 };

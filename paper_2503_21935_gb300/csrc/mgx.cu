@@ -936,13 +936,13 @@ bool use_smem_ws(const mgx_process* pr, const KParams& kp, int64_t nevt, int mod
 // one thread takes for one event, and one block per event (the CTA kernel) takes a fraction of
 // that.  Measured crossovers on GB300 in FP64: about 9.5k events (g g > t t~ g), 12k (g u~ >
 // ta+ ta- g g u~) and 19k (g g > t t~ g g) against the thread kernel, about 2k against the
-// shared-memory thread kernel of the small processes; at 8192 events the CTA kernel also beats
-// the helicity-parallel and split plans for those processes (12.3 vs 15.7 ms for g g > t t~ g g);
+// shared-memory thread kernel of the small processes; against the helicity-parallel kernel the
+// CTA kernel wins at 2048 events (g g > t t~ g g: 3.2 vs 3.5 ms) and loses at 8192 (12.4 vs 10.3 ms);
 // the limits below stay under the crossovers.
 bool use_cta_kernel(const mgx_process* pr, const KParams& kp, int64_t nevt, int mode) {
   if (!mode_f64(mode) || !cta_usable(pr, kp)) return false;
   if (pr->kernel == MGX_KERNEL_CTA) return true;
-  const int64_t per_sm = smem_usable(kp, mode) ? 8 : 64;
+  const int64_t per_sm = smem_usable(kp, mode) ? 8 : 32;
   return pr->kernel == MGX_KERNEL_AUTO && nevt <= per_sm * sm_count(pr->device);
 }
 
@@ -1031,7 +1031,7 @@ constexpr double kUnitsPerSecPerSm = 5.2e11 / 152;
 
 // The plan of least estimated time (plus, for a diagram split, the combine step: one thread per
 // event and helicity).  PLAN_ANY keeps the whole-event thread kernel unless another plan is
-// estimated at least 1.33x faster; PLAN_HEL and PLAN_SPLIT return the best plan of that kind.
+// estimated at least 1.1x faster; PLAN_HEL and PLAN_SPLIT return the best plan of that kind.
 HelPlan best_plan(const mgx_process* pr, int64_t nevt, int mode, int kind) {
   const int nf = 1 << pr->prog->npar;
   const double n = pr->prog->ncol;
@@ -1071,7 +1071,7 @@ HelPlan best_plan(const mgx_process* pr, int64_t nevt, int mode, int kind) {
       }
     }
   }
-  if (kind == PLAN_ANY && !(tb >= 0.0 && tb < 0.75 * t_thread)) return HelPlan{};
+  if (kind == PLAN_ANY && !(tb >= 0.0 && tb < 0.9 * t_thread)) return HelPlan{};
   return best;
 }
 

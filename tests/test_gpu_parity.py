@@ -164,15 +164,15 @@ def test_parity_mixed_fp32_colour_sum(name, nevt, bound, kernel):
 
 
 def test_auto_kernel_by_batch_size():
-    """AUTO runs a float64 batch of at most 64 events per SM one block per event (no caller
+    """AUTO runs a float64 batch of at most 32 events per SM one block per event (no caller
     workspace) when the process has a block-per-event schedule; larger batches, the float mode
     and processes without that schedule take a kernel with a workspace."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     proc = _proc(WORKLOADS["ggttgg"].process)
-    assert proc.workspace_bytes(64 * sms) == 0 and proc.workspace_bytes(64 * sms, mode=1) == 0
-    assert proc.plan(64 * sms)[0] == 2
-    assert proc.workspace_bytes(64 * sms + 1) > 0
+    assert proc.workspace_bytes(32 * sms) == 0 and proc.workspace_bytes(32 * sms, mode=1) == 0
+    assert proc.plan(32 * sms)[0] == 2
+    assert proc.workspace_bytes(32 * sms + 1) > 0
     assert proc.workspace_bytes(1000, mode=4) > 0
     assert _proc(WORKLOADS["ggttggg"].process).workspace_bytes(100) > 0
 
