@@ -62,6 +62,8 @@ struct GemmArgs {
   int* err;                // device error counter: +1 per tile whose tensor-core wait ran out
   int skip_mma;            // test hook: issue no MMA, so that the waits run out
   unsigned long long wait_ns;
+  int ksplit;              // weights: the contraction is cut into ksplit slices (grid z), slice z writing
+                           // its partial product to wout + z M N (summed afterwards in slice order)
 };
 
 // One CTA computes C[m0 .. m0+127][n0 .. n0+NT) with NT = min(N - n0, 256) (multiple of 32).
@@ -88,7 +90,12 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
   const uint32_t saddr = umma::smem_u32(sa), sbaddr = umma::smem_u32(sb);
   uint32_t phase = 0;
   bool ok = true;
-  for (int k0 = 0; k0 < g.K; k0 += kc) {
+  // this CTA's slice of the contraction (the whole of it unless the weight gradient is split)
+  const int nslice = g.ksplit > 1 ? g.ksplit : 1;
+  const int chunks = (g.K + kc - 1) / kc, per = (chunks + nslice - 1) / nslice;
+  const int kbeg = (int)blockIdx.z * per * kc, kend = min(g.K, kbeg + per * kc);
+  float* wout = g.wout ? g.wout + (size_t)blockIdx.z * g.M * g.N : nullptr;
+  for (int k0 = kbeg; k0 < kend; k0 += kc) {
     // stage A rows (row tid) and B rows; 16-byte pieces = one core-matrix row each
     const int row = m0 + tid;
     for (int c = 0; c < kc / 8; ++c) {
@@ -111,7 +118,7 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
       if (!g.skip_mma) {
         for (int ks = 0; ks < kc / 16; ++ks)
           umma::mma_f16(tmem, umma::smem_desc(saddr + ks * 256, 128, sbo),
-                        umma::smem_desc(sbaddr + ks * 256, 128, sbo), id, (k0 > 0 || ks > 0) ? 1u : 0u);
+                        umma::smem_desc(sbaddr + ks * 256, 128, sbo), id, (k0 > kbeg || ks > 0) ? 1u : 0u);
         umma::mma_commit(mbar);
       }
     }
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
           g.hout[(size_t)m * g.N + n] = d;
           g.houtT[(size_t)n * g.ldt + m] = d;
         } else {
-          g.wout[(size_t)m * g.N + n] = acc[j];
+          wout[(size_t)m * g.N + n] = kbeg < kend ? acc[j] : 0.0f;   // an empty slice contributes 0
         }
       }
     }
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
           g.hout[(size_t)m * g.N + n] = __float2bfloat16_rn(nan);
           g.houtT[(size_t)n * g.ldt + m] = __float2bfloat16_rn(nan);
         } else {
-          g.wout[(size_t)m * g.N + n] = nan;
+          wout[(size_t)m * g.N + n] = nan;
         }
       }
     umma::mbar_wait(mbar, phase ^ 1, g.wait_ns);
@@ -195,7 +202,7 @@ int gemm(const GemmArgs& g, cudaStream_t st) {
     attr = true;
   }
   const int NT = std::min(g.N, kWidth);
-  dim3 grid((g.M + kRows - 1) / kRows, (g.N + NT - 1) / NT);
+  dim3 grid((g.M + kRows - 1) / kRows, (g.N + NT - 1) / NT, g.ksplit > 1 ? g.ksplit : 1);
   gemm_bf16_kernel<<<grid, kRows, smem, st>>>(g);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
@@ -236,6 +243,15 @@ __global__ void output_backward_kernel(int n, const float* __restrict__ y, const
   const __nv_bfloat16 v = __float2bfloat16_rn(d * w4[c] * silu_grad(z4[i]));
   dz[i] = v;
   dzT[(size_t)c * ldt + r] = v;
+}
+
+// out[i] = sum over slices z (in order) of part[z][i]: the split weight gradient, deterministically
+__global__ void slice_sum_kernel(int n, int nslice, const float* __restrict__ part, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc = 0.0f;
+  for (int z = 0; z < nslice; ++z) acc += part[(size_t)z * n + i];
+  out[i] = acc;
 }
 
 // column sums over rows of a transposed bf16 matrix [ncol][ld] (bias gradients), one warp per column
@@ -583,9 +599,12 @@ int wb_offset(const ParamLayout& L, int l) {
 }
 
 // workspace for n rows (n padded to a multiple of 128 for the transposed buffers)
+constexpr int kDwSlices = 32;   // slices of the batch contraction of a weight gradient (grid z)
+
 struct MlpWs {
   __nv_bfloat16 *x, *xT, *h[kDepth], *hT[kDepth], *dz[2], *dzT[2];
   float *z[kDepth], *y, *dy, *loss;
+  float* part;            // [kDwSlices][256][256] partial weight gradients
   int* err;
   int ldt;
   size_t bytes;
@@ -615,6 +634,7 @@ MlpWs ws_layout(char* base, int n) {
   w.y = (float*)take((size_t)ldt * 4);
   w.dy = (float*)take((size_t)ldt * 4);
   w.loss = (float*)take(256);
+  w.part = (float*)take((size_t)kDwSlices * kWidth * kWidth * 4);
   w.err = (int*)take(256);
   w.bytes = off;
   return w;
@@ -655,10 +675,18 @@ int backward(mgx_mlp* net, int n, const float* t, const MlpWs& w, cudaStream_t s
     gw.A = w.dzT[cur]; gw.lda = w.ldt;
     gw.B = l == 0 ? w.xT : w.hT[l - 1]; gw.ldb = w.ldt;
     gw.M = kWidth; gw.N = kin; gw.K = w.ldt; gw.epi = EPI_DW;
-    gw.wout = net->g + L.off_w[l];
+    // the contraction over the batch is cut into slices (more CTAs than the 2 row tiles of dW), each
+    // writing a partial product; the slices are summed in order (deterministic)
+    const int chunks = (w.ldt + kKc - 1) / kKc;
+    gw.ksplit = std::min(kDwSlices, chunks);
+    gw.wout = gw.ksplit > 1 ? w.part : net->g + L.off_w[l];
     gw.err = net->d_status; gw.skip_mma = net->skip_mma; gw.wait_ns = net->wait_ns;
     int rc = gemm(gw, st);
     if (rc != MGX_OK) return rc;
+    if (gw.ksplit > 1) {
+      const int nw = kWidth * kin;
+      slice_sum_kernel<<<(nw + 255) / 256, 256, 0, st>>>(nw, gw.ksplit, w.part, net->g + L.off_w[l]);
+    }
     colsum_kernel<<<(kWidth + 7) / 8, 256, 0, st>>>(kWidth, n, w.dzT[cur], w.ldt, net->g + L.off_b[l]);
     if (l == 0) break;
     // dZ_{l-1} = (dZ_l W_l) * silu'(Z_{l-1})
