@@ -8,6 +8,10 @@ every diagram amplitude, jamps, colour sum, helicity sum, helicity and colour
 selection.  Metric: |M|^2 evaluations per second (whole job).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|mixed_fp32|mixed_tf32|mixed_bf16x3|float] [--impl reference]
+                  [--workload ggttgg|ggttggg] [--kernel auto|thread|cta|smem|helicity|split]
+
+--workload ggttggg (g g > t t~ g g g) and --kernel (a fixed schedule instead of AUTO's choice) serve
+profiling captures of the other kernels; the default line is the one above.
 
 Under torchrun each rank processes its own 2^20 events (weak scaling, no data
 collective); rank 0 prints one JSON line.  --impl reference times the float64
@@ -29,6 +33,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "ggttgg"
 NEVT = 1 << 20
 METRIC = "gg->ttgg |M|^2 evals/s (FP64)"
+METRICS = {"ggttgg": METRIC, "ggttggg": "gg->ttggg |M|^2 evals/s (FP64)"}
+KERNELS = {"auto": 0, "thread": 1, "cta": 2, "smem": 3, "helicity": 4, "split": 5}
 # FP64 pipe: 152 SMs x 2 DFMA/clk/SM (measured: 1.20 TFLOP/s at 1995 MHz) x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_PEAK_GINST = 152 * 2 * 2.070e9 / 1e9       # float64 instructions per second, any of fma/mul/add
@@ -46,6 +52,8 @@ def _args():
     ap.add_argument("--nevt", type=int, default=NEVT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METRICS))
+    ap.add_argument("--kernel", default="auto", choices=list(KERNELS))
     return ap.parse_args()
 
 
@@ -189,12 +197,17 @@ def _traffic_per_event(kernel, workload):
     return None
 
 
-def _workload_config(nevt, mode):
+def _workload_config(nevt, mode, workload=WORKLOAD, ws_bytes=None):
     from phasespace import WORKLOADS
-    wl = WORKLOADS[WORKLOAD]
-    return {"workload": f"g g > t t~ g g, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, alpha_s=0.118",
-            "process": wl.process, "nevt_per_gpu": nevt, "mode": mode,
-            "l2": "inputs larger than L2 (192 MiB momenta, 5.0 GB workspace)"}
+    wl = WORKLOADS[workload]
+    cfg = {"workload": f"{wl.process}, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, alpha_s=0.118",
+           "process": wl.process, "nevt_per_gpu": nevt, "mode": mode}
+    if ws_bytes is None:
+        cfg["l2"] = "inputs larger than L2 (192 MiB momenta, 5.0 GB workspace)"
+    else:
+        cfg["l2"] = (f"workspace {ws_bytes / 2**30:.1f} GiB, "
+                     + ("larger than L2" if ws_bytes > (129 << 20) else "smaller than L2 (a profiling case)"))
+    return cfg
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
@@ -206,15 +219,15 @@ def run_reference(args):
     per_core = 384
     rates = []
     for i in range(args.warmup + args.steps):
-        r, n, busy, wall = cpu_oracle_rate(WORKLOAD, per_core, cores)
+        r, n, busy, wall = cpu_oracle_rate(args.workload, per_core, cores)
         if i >= args.warmup:
             rates.append((r, n, busy))
     value = statistics.median(r for r, _, _ in rates)
     n = rates[0][1]
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRICS[args.workload], "value": value, "unit": "events/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(b for _, _, b in rates),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(_workload_config(args.nevt, args.mode),
+            "config": dict(_workload_config(args.nevt, args.mode, args.workload),
                            sample=f"each step evaluates {n} events of this workload on the host cores"),
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_core} events per core x {cores} spawn processes per step"},
@@ -267,6 +280,11 @@ def extra_ggttggg(pkg, dev, stream):
         ms = _timed(lambda: proc.compute(M, A, RH, RC, mode=mode, stream=stream), 3, 1, stream)
         out[name] = {"value": wl.nevt / (ms * 1e-3), "unit": "events/s", "ms_per_step": ms,
                      "fp64_flops_per_event": proc.fp64_flops_per_event(mode)}
+        if name == "fp64":
+            # FP64 roofline of the thread kernel, and its DRAM traffic where a capture on these sources exists
+            out[name]["frac_fp64_peak"] = out[name]["value"] * proc.fp64_flops_per_event(mode) / 1e12 / FP64_PEAK_TFLOPS
+            per_evt = _traffic_per_event("me_kernel", "ggttggg")
+            out[name]["traffic_per_launch"] = None if per_evt is None else per_evt * wl.nevt
     return out
 
 
@@ -423,13 +441,19 @@ def extra_surrogate(pkg, dev):
     from paper_2503_21935_gb300.surrogate import Unweighter
     U = Unweighter("g g > t t~ g g", 1500.0, [173.0, 173.0, 0.0, 0.0], cut_particles=[4, 5], device=dev.index,
                    seed=5)
+    # 16000 steps of 16384: a measured sweep (4000 x 8192 -> 16000 x 16384) took the exact |M|^2
+    # calls per unweighted event from 2.64 to 1.47, at 24 s of training on the 2^22 events
+    steps, batch = 16000, 16384
     t0 = time.perf_counter()
-    hist = U.train(1 << 22, steps=4000, batch=8192, lr=2e-3)
+    hist = U.train(1 << 22, steps=steps, batch=batch, lr=3e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     U.calibrate(1 << 20)
-    res = {"training": {"events": 1 << 22, "steps": 4000, "batch": 8192, "seconds": train_s,
-                        "loss_first": hist[0][1], "loss_last": hist[-1][1]}}
+    torch.cuda.synchronize()
+    calib_s = time.perf_counter() - t0
+    res = {"training": {"events": 1 << 22, "steps": steps, "batch": batch, "seconds": train_s,
+                        "calibration_seconds": calib_s, "loss_first": hist[0][1], "loss_last": hist[-1][1]}}
     # the two-stage leg runs until 10^6 unweighted events; the plain leg (about 8x slower per
     # unweighted event) is timed over a fixed 4 batches of 2^22, its rate being what is compared
     legs = (("plain", lambda b, prof: U.plain(1 << 22, seed=901, first=b << 22), None, 4),
@@ -460,6 +484,9 @@ def extra_surrogate(pkg, dev):
             res[name]["phase_ms"] = phases
             res[name]["phase_ms_sum"] = sum(phases.values())
     res["gain"] = res["surrogate"]["value"] / res["plain"]["value"] if res["plain"]["value"] else None
+    # the same 10^6 unweighted events with the one-off training and calibration counted in
+    sur = res["surrogate"]
+    sur["value_including_training"] = sur["unweighted"] / (sur["seconds"] + train_s + calib_s)
     return res
 
 
@@ -484,8 +511,8 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         cores = _host_cores()
         per_core = 8 * ORACLE_CHUNK        # about 10 s of oracle work per host process
-        rate, n, busy, wall = cpu_oracle_rate(WORKLOAD, per_core, cores)
-        r1, n1, busy1, _ = cpu_oracle_rate(WORKLOAD, per_core, 1)
+        rate, n, busy, wall = cpu_oracle_rate(args.workload, per_core, cores)
+        r1, n1, busy1, _ = cpu_oracle_rate(args.workload, per_core, 1)
         cpu = {"value": rate, "unit": "events/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} events of the same workload ({per_core} per single-threaded spawn process), "
                          f"{busy:.1f} s busy",
@@ -493,7 +520,7 @@ def run_gpu(args):
                                  "sample": f"{n1} events in one single-threaded process, {busy1:.1f} s"}}
 
     from paper_2503_21935_gb300.dist import event_range, max_over_ranks
-    wl = WORKLOADS[WORKLOAD]
+    wl = WORKLOADS[args.workload]
     nevt = args.nevt
     mode = pkg.MODES[args.mode]
     first, _ = event_range(rank, world, nevt)
@@ -502,6 +529,9 @@ def run_gpu(args):
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     M, A, RH, RC = t(mom), t(a), t(rh), t(rc)
     proc = pkg.Process(wl.process, device=local)
+    if args.kernel != "auto":
+        proc.set_kernel(KERNELS[args.kernel])
+    default_case = args.workload == WORKLOAD and nevt == NEVT and args.kernel == "auto"
     out = {"me": torch.empty(nevt, dtype=torch.float64, device=dev),
            "selhel": torch.empty(nevt, dtype=torch.int32, device=dev),
            "selcol": torch.empty(nevt, dtype=torch.int32, device=dev)}
@@ -555,9 +585,9 @@ def run_gpu(args):
         achieved = flops / launch_s / 1e12
         peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
         peak_inst = FP32_PEAK_GINST if f32 else FP64_PEAK_GINST
-        per_evt = _traffic_per_event("me_kernel_float" if f32 else "me_kernel", WORKLOAD) \
-            if args.mode in ("fp64", "float") else None
-        line = {"metric": METRIC.replace("FP64", {"fp64": "FP64", "mixed_fp32": "mixed FP32 colour sum",
+        per_evt = _traffic_per_event("me_kernel_float" if f32 else "me_kernel", args.workload) \
+            if args.mode in ("fp64", "float") and args.kernel in ("auto", "thread") else None
+        line = {"metric": METRICS[args.workload].replace("FP64", {"fp64": "FP64", "mixed_fp32": "mixed FP32 colour sum",
                                                    "mixed_tf32": "tcgen05 TF32 colour sum",
                                                    "mixed_bf16x3": "tcgen05 BF16x3 colour sum",
                                                    "float": "FP32"}[args.mode]),
@@ -565,7 +595,9 @@ def run_gpu(args):
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed_fp32": "f64+f32", "mixed_tf32": "f64+tf32", "mixed_bf16x3": "f64+bf16",
                           "float": "f32"}[args.mode], "data": "synthetic",
-                "config": dict(_workload_config(nevt, args.mode), ngood=proc.ngood, ndiagrams=proc.ndiagrams,
+                "config": dict(_workload_config(nevt, args.mode, args.workload,
+                                                None if default_case else proc.workspace_bytes(nevt, mode)),
+                               **({} if args.kernel == "auto" else {"kernel": args.kernel}), ngood=proc.ngood, ndiagrams=proc.ndiagrams,
                                ncol=proc.ncol),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak,
@@ -582,7 +614,7 @@ def run_gpu(args):
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu,
                 "wall_s_timed": wall}
-        if not args.no_extras and world == 1:
+        if not args.no_extras and world == 1 and default_case:
             extras = {}
             for key, fn in (("ggttgg_modes", lambda: extra_modes(pkg, proc, M, A, RH, RC, nevt, stream)),
                             ("ggttggg", lambda: extra_ggttggg(pkg, dev, stream)),

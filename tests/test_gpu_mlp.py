@@ -14,11 +14,13 @@ def _net(seed=3):
     return pkg.Mlp(seed=seed)
 
 
-def test_gradients_match_cpu_reference():
+@pytest.mark.parametrize("n", [300, 2112, 4096])
+def test_gradients_match_cpu_reference(n):
+    """300 rows: one batch chunk per contraction slice; 2112: slices past the last chunk are empty
+    (they must contribute zero); 4096: two chunks per slice."""
     import torch
     net = _net()
     rng = np.random.default_rng(1)
-    n = 300
     x = rng.normal(size=(n, 24)).astype(np.float32)
     t = rng.normal(size=n).astype(np.float32)
     loss, g = net.gradients(x, t)
