@@ -441,9 +441,10 @@ def extra_surrogate(pkg, dev):
     from paper_2503_21935_gb300.surrogate import Unweighter
     U = Unweighter("g g > t t~ g g", 1500.0, [173.0, 173.0, 0.0, 0.0], cut_particles=[4, 5], device=dev.index,
                    seed=5)
-    # 16000 steps of 16384: a measured sweep (4000 x 8192 -> 16000 x 16384) took the exact |M|^2
-    # calls per unweighted event from 2.64 to 1.47, at 24 s of training on the 2^22 events
-    steps, batch = 16000, 16384
+    # 32000 steps of 16384: in a measured sweep the exact |M|^2 calls per unweighted event fell from
+    # 2.64 (4000 x 8192) to 1.50 (16000 x 16384) and 1.24 (32000 x 16384, 16.5 s of training on the
+    # 2^22 events); 64000 steps gave 1.16 for twice the training time
+    steps, batch = 32000, 16384
     t0 = time.perf_counter()
     hist = U.train(1 << 22, steps=steps, batch=batch, lr=3e-3)
     torch.cuda.synchronize()

@@ -47,7 +47,7 @@ struct GemmArgs {
   int lda;
   const __nv_bfloat16* B;  // [N][ldb]
   int ldb;
-  int M, N, K;             // C is M x N, contraction K (multiple of 16; of kKc when K > kKc)
+  int M, N, K;             // C is M x N (N a multiple of 32), contraction K (a multiple of min(K, kKc) and of 16)
   int epi;
   // forward: Z fp32 [M][N], H bf16 [M][N], HT bf16 [N][ldt], bias [N]
   // backward: zprev fp32 [M][N] (silu' source), out bf16 [M][N], outT bf16 [N][ldt]
@@ -64,22 +64,42 @@ struct GemmArgs {
   unsigned long long wait_ns;
   int ksplit;              // weights: the contraction is cut into ksplit slices (grid z), slice z writing
                            // its partial product to wout + z M N (summed afterwards in slice order)
+  int nt;                  // columns per tile (64, 128 or 256; set by gemm())
 };
 
-// One CTA computes C[m0 .. m0+127][n0 .. n0+NT) with NT = min(N - n0, 256) (multiple of 32).
+constexpr int kGemmStages = 2;   // shared-memory stages of the contraction (copy of chunk k+1 during MMA k)
+
+// 16-byte asynchronous global -> shared copy (zero-filled when !valid; src must still be a mapped address)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// One CTA computes C[m0 .. m0+127][n0 .. n0+nt).  The contraction runs in chunks of kc = min(K, 64)
+// through two shared-memory stages: the 16-byte cp.async copies of chunk k+1 (canonical K-major
+// layout, rows past M or N zero-filled) are in flight while the tensor cores run chunk k; each
+// stage's MMAs commit to their own mbarrier, waited on before the stage is refilled.  The epilogue
+// reads 32 accumulator columns at a time (TMEM lane = row) and stores them with 16-byte stores.
 __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int NT = min(g.N, kWidth);
+  const int NT = g.nt;
   const int kc = min(g.K, kKc);
-  unsigned char* sa = sm;                                  // 128 x kc bf16
-  unsigned char* sb = sa + (size_t)kRows * kc * 2;         // NT x kc bf16
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sb + (size_t)NT * kc * 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const size_t a_bytes = (size_t)kRows * kc * 2, stage_bytes = a_bytes + (size_t)NT * kc * 2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kGemmStages * stage_bytes);   // one per stage
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kGemmStages);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int m0 = blockIdx.x * kRows, n0 = blockIdx.y * NT;
   uint32_t tcols = 32;
   while ((int)tcols < NT) tcols <<= 1;
-  if (tid == 0) umma::mbar_init(mbar, 1);
+  if (tid == 0)
+    for (int s = 0; s < kGemmStages; ++s) umma::mbar_init(&mbar[s], 1);
   if (warp == 0) umma::tmem_alloc_once(tslot, tcols);
   umma::fence_before_sync();
   __syncthreads();
@@ -87,81 +107,138 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
   const uint32_t tmem = *tslot;
   const uint32_t sbo = (uint32_t)(kc / 8) * 128;
   const uint32_t id = umma::idesc(umma::FMT_BF16, kRows, (uint32_t)NT);
-  const uint32_t saddr = umma::smem_u32(sa), sbaddr = umma::smem_u32(sb);
-  uint32_t phase = 0;
-  bool ok = true;
   // this CTA's slice of the contraction (the whole of it unless the weight gradient is split)
   const int nslice = g.ksplit > 1 ? g.ksplit : 1;
   const int chunks = (g.K + kc - 1) / kc, per = (chunks + nslice - 1) / nslice;
   const int kbeg = (int)blockIdx.z * per * kc, kend = min(g.K, kbeg + per * kc);
+  const int nk = kbeg < kend ? (kend - kbeg) / kc : 0;
   float* wout = g.wout ? g.wout + (size_t)blockIdx.z * g.M * g.N : nullptr;
-  for (int k0 = kbeg; k0 < kend; k0 += kc) {
-    // stage A rows (row tid) and B rows; 16-byte pieces = one core-matrix row each
+
+  auto issue = [&](int k) {   // copies of chunk k into stage k % 2
+    const int k0 = kbeg + k * kc;
+    unsigned char* sa = sm + (size_t)(k % kGemmStages) * stage_bytes;
+    unsigned char* sb = sa + a_bytes;
     const int row = m0 + tid;
-    for (int c = 0; c < kc / 8; ++c) {
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (row < g.M) v = __ldg(reinterpret_cast<const uint4*>(g.A + (size_t)row * g.lda + k0 + 8 * c));
-      *reinterpret_cast<uint4*>(sa + umma::kmajor_offset(tid, 8 * c, kc, 2)) = v;
-    }
+    const bool va = row < g.M;
+    const __nv_bfloat16* ar = g.A + (size_t)(va ? row : 0) * g.lda + k0;
+    for (int c = 0; c < kc / 8; ++c) cp_async16(umma::smem_u32(sa + umma::kmajor_offset(tid, 8 * c, kc, 2)), ar + 8 * c, va);
     for (int r = tid; r < NT; r += kRows) {
       const int nrow = n0 + r;
-      for (int c = 0; c < kc / 8; ++c) {
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (nrow < g.N) v = __ldg(reinterpret_cast<const uint4*>(g.B + (size_t)nrow * g.ldb + k0 + 8 * c));
-        *reinterpret_cast<uint4*>(sb + umma::kmajor_offset(r, 8 * c, kc, 2)) = v;
+      const bool vb = nrow < g.N;
+      const __nv_bfloat16* br = g.B + (size_t)(vb ? nrow : 0) * g.ldb + k0;
+      for (int c = 0; c < kc / 8; ++c) cp_async16(umma::smem_u32(sb + umma::kmajor_offset(r, 8 * c, kc, 2)), br + 8 * c, vb);
+    }
+    cp_async_commit();
+  };
+  // chunk j's MMAs commit to mbarrier j % 2 as its (j / 2)-th phase; a stage is refilled only after
+  // the chunk that last read it was waited on, so no mbarrier completes twice unobserved
+  auto wait_one = [&](int j) {
+    return umma::mbar_wait(&mbar[j % kGemmStages], (uint32_t)((j / kGemmStages) & 1), g.wait_ns);
+  };
+  bool ok = true;
+  int waited = 0, issued = 0, failed = -1;   // chunks known complete / whose MMA step ran / timed out
+  if (nk > 0) issue(0);
+  for (int k = 0; k < nk; ++k) {
+    if (k + 1 < nk) {
+      // stage (k+1) % 2 was last read by the MMAs of chunk k-1
+      if (k >= 1) {
+        if (!__syncthreads_and(wait_one(k - 1))) {
+          ok = false;
+          failed = k - 1;
+          break;
+        }
+        waited = k;
       }
+      issue(k + 1);
+      cp_async_wait<1>();   // this thread's copies of chunk k have landed
+    } else {
+      cp_async_wait<0>();
     }
     umma::fence_proxy_async_smem();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !g.skip_mma) {
       umma::fence_after_sync();
-      if (!g.skip_mma) {
-        for (int ks = 0; ks < kc / 16; ++ks)
-          umma::mma_f16(tmem, umma::smem_desc(saddr + ks * 256, 128, sbo),
-                        umma::smem_desc(sbaddr + ks * 256, 128, sbo), id, (k0 > kbeg || ks > 0) ? 1u : 0u);
-        umma::mma_commit(mbar);
-      }
+      const uint32_t sa = umma::smem_u32(sm + (size_t)(k % kGemmStages) * stage_bytes);
+      const uint32_t sb = sa + (uint32_t)a_bytes;
+      for (int ks = 0; ks < kc / 16; ++ks)
+        umma::mma_f16(tmem, umma::smem_desc(sa + ks * 256, 128, sbo), umma::smem_desc(sb + ks * 256, 128, sbo), id,
+                      (k > 0 || ks > 0) ? 1u : 0u);
+      umma::mma_commit(&mbar[k % kGemmStages]);
     }
-    const bool done = umma::mbar_wait(mbar, phase, g.wait_ns);
-    phase ^= 1;
-    if (!__syncthreads_and(done)) {
-      ok = false;
-      break;
-    }
-    umma::fence_after_sync();
+    issued = k + 1;
   }
+  for (int j = waited; ok && j < issued; ++j) {
+    if (!__syncthreads_and(wait_one(j))) {
+      ok = false;
+      failed = j;
+    } else {
+      waited = j + 1;
+    }
+  }
+  cp_async_wait<0>();   // no copy of this block in flight past this point
+  umma::fence_after_sync();
+  const int m = m0 + tid;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   if (ok) {
-    // epilogue: TMEM lane tid = row m0 + tid
-    const int m = m0 + tid;
-    for (int c0 = 0; c0 < NT; c0 += 8) {
-      float acc[8];
-      umma::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+    for (int c0 = 0; c0 < NT; c0 += 32) {
+      float acc[32];
+      umma::tmem_ld32(tmem + lane_base + (uint32_t)c0, acc);
       umma::tmem_wait_ld();
-      if (m >= g.M) continue;
+      const int nb = n0 + c0;
+      if (m >= g.M || nb >= g.N) continue;
+      if (g.epi == EPI_FWD) {
+        const float4* b4 = reinterpret_cast<const float4*>(g.bias + nb);
+        float4* z4 = reinterpret_cast<float4*>(g.zout + (size_t)m * g.N + nb);
+        uint4* h4 = reinterpret_cast<uint4*>(g.hout + (size_t)m * g.N + nb);
+        float bv[32];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int n = n0 + c0 + j;
-        if (n >= g.N) continue;
-        if (g.epi == EPI_FWD) {
-          const float z = acc[j] + g.bias[n];
-          const __nv_bfloat16 h = __float2bfloat16_rn(siluf(z));
-          g.zout[(size_t)m * g.N + n] = z;
-          g.hout[(size_t)m * g.N + n] = h;
-          g.houtT[(size_t)n * g.ldt + m] = h;
-        } else if (g.epi == EPI_BWD) {
-          const __nv_bfloat16 d = __float2bfloat16_rn(acc[j] * silu_grad(g.zprev[(size_t)m * g.N + n]));
-          g.hout[(size_t)m * g.N + n] = d;
-          g.houtT[(size_t)n * g.ldt + m] = d;
-        } else {
-          wout[(size_t)m * g.N + n] = kbeg < kend ? acc[j] : 0.0f;   // an empty slice contributes 0
+        for (int q = 0; q < 8; ++q) {
+          const float4 t = __ldg(b4 + q);
+          bv[4 * q] = t.x; bv[4 * q + 1] = t.y; bv[4 * q + 2] = t.z; bv[4 * q + 3] = t.w;
         }
+        uint32_t hp[16];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] += bv[j];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hp[j] = pack_bf16x2(siluf(acc[2 * j]), siluf(acc[2 * j + 1]));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) z4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h4[q] = make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+        const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(hp);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) g.houtT[(size_t)(nb + j) * g.ldt + m] = hb[j];
+      } else if (g.epi == EPI_BWD) {
+        const float4* zp = reinterpret_cast<const float4*>(g.zprev + (size_t)m * g.N + nb);
+        float zv[32];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 t = __ldg(zp + q);
+          zv[4 * q] = t.x; zv[4 * q + 1] = t.y; zv[4 * q + 2] = t.z; zv[4 * q + 3] = t.w;
+        }
+        uint32_t dp[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          dp[j] = pack_bf16x2(acc[2 * j] * silu_grad(zv[2 * j]), acc[2 * j + 1] * silu_grad(zv[2 * j + 1]));
+        uint4* d4 = reinterpret_cast<uint4*>(g.hout + (size_t)m * g.N + nb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d4[q] = make_uint4(dp[4 * q], dp[4 * q + 1], dp[4 * q + 2], dp[4 * q + 3]);
+        const __nv_bfloat16* db = reinterpret_cast<const __nv_bfloat16*>(dp);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) g.houtT[(size_t)(nb + j) * g.ldt + m] = db[j];
+      } else {
+        float4* w4 = reinterpret_cast<float4*>(wout + (size_t)m * g.N + nb);
+        const bool any = nk > 0;   // an empty slice contributes 0
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          w4[q] = any ? make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3])
+                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       }
     }
   } else {
     // the tile's outputs become NaN (never stale values), the error is counted, and the block waits
     // (bounded) for MMAs still in flight before it frees its tensor memory
     if (tid == 0 && g.err) atomicAdd(g.err, 1);
-    const int m = m0 + tid;
     const float nan = __int_as_float(0x7fc00000);
     if (m < g.M)
       for (int c = 0; c < NT; ++c) {
@@ -178,7 +255,9 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
           wout[(size_t)m * g.N + n] = nan;
         }
       }
-    umma::mbar_wait(mbar, phase ^ 1, g.wait_ns);
+    // MMAs really committed and not seen complete: the chunk that timed out, once more, and later ones
+    if (!g.skip_mma)
+      for (int j = failed; j >= 0 && j < issued; ++j) wait_one(j);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -188,12 +267,32 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
   }
 }
 
-size_t gemm_smem(const GemmArgs& g) {
-  const int NT = std::min(g.N, kWidth), kc = std::min(g.K, kKc);
-  return (size_t)kRows * kc * 2 + (size_t)NT * kc * 2 + 64;
+int sm_count_cached() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    if (n <= 0) n = 148;
+  }
+  return n;
 }
 
-int gemm(const GemmArgs& g, cudaStream_t st) {
+size_t gemm_smem(const GemmArgs& g) {
+  const int kc = std::min(g.K, kKc);
+  return (size_t)kGemmStages * ((size_t)kRows * kc * 2 + (size_t)g.nt * kc * 2) + 64;
+}
+
+int gemm(GemmArgs g, cudaStream_t st) {
+  const int kc = std::min(g.K, kKc);
+  if (g.M <= 0 || g.N <= 0 || g.N % 32 != 0 || g.K <= 0 || g.K % 16 != 0 || g.K % kc != 0)
+    return MGX_ERR_INVALID_ARGUMENT;
+  // the widest tile (256, 128 or 64 columns) that still gives every SM 3 CTAs: the kernel is bound by
+  // the latency of its copies, MMA round trips and epilogue stores, which more resident warps hide
+  const int zs = g.ksplit > 1 ? g.ksplit : 1;
+  const int64_t mtiles = (int64_t)((g.M + kRows - 1) / kRows) * zs;
+  g.nt = std::min(g.N, kWidth);
+  while (g.nt > 64 && g.N % (g.nt / 2) == 0 && mtiles * ((g.N + g.nt - 1) / g.nt) < 3 * sm_count_cached()) g.nt /= 2;
   const size_t smem = gemm_smem(g);
   static bool attr = false;
   if (!attr) {
@@ -201,8 +300,7 @@ int gemm(const GemmArgs& g, cudaStream_t st) {
       return MGX_ERR_CUDA;
     attr = true;
   }
-  const int NT = std::min(g.N, kWidth);
-  dim3 grid((g.M + kRows - 1) / kRows, (g.N + NT - 1) / NT, g.ksplit > 1 ? g.ksplit : 1);
+  dim3 grid((g.M + kRows - 1) / kRows, (g.N + g.nt - 1) / g.nt, zs);
   gemm_bf16_kernel<<<grid, kRows, smem, st>>>(g);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
 }
@@ -230,19 +328,42 @@ __global__ void output_kernel(int n, const __nv_bfloat16* __restrict__ h, const 
   if (lane == 0) y[row] = acc + b4[0];
 }
 
-// dy = 2 (y - t)/n, loss partial sums; dZ4 = dy w4 * silu'(Z4) (bf16, row-major and transposed)
+// dy = 2 (y - t)/n; dZ4 = dy w4 * silu'(Z4) (bf16, row-major and transposed).  Block (32, 8) per
+// 32 x 32 tile: rows are read and written along the lanes, the transposed copy goes through shared
+// memory so that its stores run along the rows too.
 __global__ void output_backward_kernel(int n, const float* __restrict__ y, const float* __restrict__ t,
                                        const float* __restrict__ w4, const float* __restrict__ z4,
                                        float* __restrict__ dy, __nv_bfloat16* __restrict__ dz,
                                        __nv_bfloat16* __restrict__ dzT, int ldt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * kWidth) return;
-  const int r = i / kWidth, c = i % kWidth;
-  const float d = 2.0f * (y[r] - t[r]) / (float)n;
-  if (c == 0) dy[r] = d;
-  const __nv_bfloat16 v = __float2bfloat16_rn(d * w4[c] * silu_grad(z4[i]));
-  dz[i] = v;
-  dzT[(size_t)c * ldt + r] = v;
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + tx;
+    if (r < n) {
+      const float d = 2.0f * (y[r] - t[r]) / (float)n;
+      if (c == 0) dy[r] = d;
+      const __nv_bfloat16 v = __float2bfloat16_rn(d * w4[c] * silu_grad(z4[(size_t)r * kWidth + c]));
+      dz[(size_t)r * kWidth + c] = v;
+      tile[i][tx] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + tx, c = c0 + i;
+    if (r < n) dzT[(size_t)c * ldt + r] = tile[tx][i];
+  }
+}
+
+// sum of one value per thread over a block of 256 threads, in a fixed order (deterministic)
+__device__ float block_sum256(float v) {
+  __shared__ float part[8];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.0f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) s += part[w];
+  return s;   // valid in thread 0
 }
 
 // out[i] = sum over slices z (in order) of part[z][i]: the split weight gradient, deterministically
@@ -254,37 +375,71 @@ __global__ void slice_sum_kernel(int n, int nslice, const float* __restrict__ pa
   out[i] = acc;
 }
 
-// column sums over rows of a transposed bf16 matrix [ncol][ld] (bias gradients), one warp per column
+// column sums over rows of a transposed bf16 matrix [ncol][ld] (bias gradients), one block of 256
+// threads per column
 __global__ void colsum_kernel(int ncol, int n, const __nv_bfloat16* __restrict__ mT, int ld, float* __restrict__ out) {
-  const int c = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (c >= ncol) return;
+  const int c = blockIdx.x;
+  const __nv_bfloat16* row = mT + (size_t)c * ld;   // ld is a multiple of 128: rows are 16-byte aligned
+  const int n8 = n / 8;
   float acc = 0.0f;
-  for (int r = lane; r < n; r += 32) acc += __bfloat162float(mT[(size_t)c * ld + r]);
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) out[c] = acc;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < n8; i += 256) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + i);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __bfloat1622float2(h[q]);
+      acc += f.x + f.y;
+    }
+  }
+  for (int r = 8 * n8 + threadIdx.x; r < n; r += 256) acc += __bfloat162float(row[r]);
+  acc = block_sum256(acc);
+  if (threadIdx.x == 0) out[c] = acc;
 }
 
-// output-layer gradients: dw4[k] = sum_r dy[r] h4[r][k], db4 = sum_r dy[r]; loss = mean (y - t)^2
+// output-layer gradients, one block of 256 threads per result: dw4[k] = sum_r dy[r] h4[r][k] (blocks
+// k < 256), db4 = sum_r dy[r] (block 256), loss = mean (y - t)^2 (block 257)
 __global__ void output_grad_kernel(int n, const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h4T, int ld,
                                    const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ dw4,
                                    float* __restrict__ db4, float* __restrict__ loss) {
-  const int c = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (c > kWidth) return;
+  const int c = blockIdx.x;
+  const int n8 = n / 8;   // rows in groups of 8: 16-byte loads (dy, y: workspace rows; t: the caller's
+                          // targets, read with 4-byte loads as its alignment is not known)
   float acc = 0.0f;
-  for (int r = lane; r < n; r += 32) {
-    if (c < kWidth) acc = fmaf(dy[r], __bfloat162float(h4T[(size_t)c * ld + r]), acc);
-    else acc += dy[r];
+  if (c < kWidth) {
+    const uint4* hr = reinterpret_cast<const uint4*>(h4T + (size_t)c * ld);
+    const float4* d4 = reinterpret_cast<const float4*>(dy);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n8; i += 256) {
+      const uint4 v = __ldg(hr + i);
+      const float4 a = __ldg(d4 + 2 * i), b = __ldg(d4 + 2 * i + 1);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+      const float2 h0 = __bfloat1622float2(h[0]), h1 = __bfloat1622float2(h[1]), h2 = __bfloat1622float2(h[2]),
+                   h3 = __bfloat1622float2(h[3]);
+      acc = fmaf(a.x, h0.x, acc); acc = fmaf(a.y, h0.y, acc); acc = fmaf(a.z, h1.x, acc); acc = fmaf(a.w, h1.y, acc);
+      acc = fmaf(b.x, h2.x, acc); acc = fmaf(b.y, h2.y, acc); acc = fmaf(b.z, h3.x, acc); acc = fmaf(b.w, h3.y, acc);
+    }
+    for (int r = 8 * n8 + threadIdx.x; r < n; r += 256) acc = fmaf(dy[r], __bfloat162float(h4T[(size_t)c * ld + r]), acc);
+  } else if (c == kWidth) {
+    const float4* d4 = reinterpret_cast<const float4*>(dy);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < 2 * n8; i += 256) {
+      const float4 a = __ldg(d4 + i);
+      acc += (a.x + a.y) + (a.z + a.w);
+    }
+    for (int r = 8 * n8 + threadIdx.x; r < n; r += 256) acc += dy[r];
+  } else {
+#pragma unroll 8
+    for (int r = threadIdx.x; r < n; r += 256) {
+      const float e = y[r] - __ldg(t + r);
+      acc = fmaf(e, e, acc);
+    }
   }
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) {
+  acc = block_sum256(acc);
+  if (threadIdx.x == 0) {
     if (c < kWidth) dw4[c] = acc;
-    else db4[0] = acc;
-  }
-  if (c == kWidth && loss) {
-    float l = 0.0f;
-    for (int r = lane; r < n; r += 32) l += (y[r] - t[r]) * (y[r] - t[r]);
-    for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if (lane == 0) loss[0] = l / (float)n;
+    else if (c == kWidth) db4[0] = acc;
+    else if (loss) loss[0] = acc / (float)n;
   }
 }
 
@@ -665,8 +820,8 @@ int forward(mgx_mlp* net, int n, const float* x, const MlpWs& w, cudaStream_t st
 // gradients of the mean squared error into net->g
 int backward(mgx_mlp* net, int n, const float* t, const MlpWs& w, cudaStream_t st) {
   const ParamLayout& L = net->L;
-  output_grad_kernel<<<(kWidth + 1 + 7) / 8, 256, 0, st>>>(n, w.dy, w.hT[kDepth - 1], w.ldt, w.y, t, net->g + L.off_w4,
-                                                          net->g + L.off_b4, w.loss);
+  output_grad_kernel<<<kWidth + 2, 256, 0, st>>>(n, w.dy, w.hT[kDepth - 1], w.ldt, w.y, t, net->g + L.off_w4,
+                                                net->g + L.off_b4, w.loss);
   int cur = 0;
   for (int l = kDepth - 1; l >= 0; --l) {
     const int kin = L.kin[l];
@@ -687,7 +842,7 @@ int backward(mgx_mlp* net, int n, const float* t, const MlpWs& w, cudaStream_t s
       const int nw = kWidth * kin;
       slice_sum_kernel<<<(nw + 255) / 256, 256, 0, st>>>(nw, gw.ksplit, w.part, net->g + L.off_w[l]);
     }
-    colsum_kernel<<<(kWidth + 7) / 8, 256, 0, st>>>(kWidth, n, w.dzT[cur], w.ldt, net->g + L.off_b[l]);
+    colsum_kernel<<<kWidth, 256, 0, st>>>(kWidth, n, w.dzT[cur], w.ldt, net->g + L.off_b[l]);
     if (l == 0) break;
     // dZ_{l-1} = (dZ_l W_l) * silu'(Z_{l-1})
     GemmArgs gb{};
@@ -883,12 +1038,22 @@ int mgx_mlp_gradients(mgx_mlp* net, int n, const float* x, const float* t, float
   MlpWs w = ws_layout((char*)ws, n);
   if (!ws || wsb < w.bytes) return MGX_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t st = (cudaStream_t)stream;
-  // zero the padded rows of the transposed buffers (they enter the batch contractions)
-  if (cudaMemsetAsync(ws, 0, w.bytes, st) != cudaSuccess) return MGX_ERR_CUDA;
+  // zero the padded batch columns [n, ldt) of the transposed buffers (they enter the batch
+  // contractions); every other element the step reads is written first
+  if (w.ldt > n) {
+    const size_t pitch = (size_t)w.ldt * 2, width = (size_t)(w.ldt - n) * 2;
+    auto pad = [&](__nv_bfloat16* buf, int rows) {
+      return cudaMemset2DAsync(buf + n, pitch, 0, width, rows, st) == cudaSuccess;
+    };
+    bool okz = pad(w.xT, kK0);
+    for (int l = 0; l < kDepth; ++l) okz = okz && pad(w.hT[l], kWidth);
+    for (int j = 0; j < 2; ++j) okz = okz && pad(w.dzT[j], kWidth);
+    if (!okz) return MGX_ERR_CUDA;
+  }
   int rc = forward(net, n, x, w, st, true);
   if (rc != MGX_OK) return rc;
-  output_backward_kernel<<<(n * kWidth + 255) / 256, 256, 0, st>>>(n, w.y, t, net->p + net->L.off_w4, w.z[kDepth - 1],
-                                                                  w.dy, w.dz[0], w.dzT[0], w.ldt);
+  output_backward_kernel<<<dim3((n + 31) / 32, kWidth / 32), dim3(32, 8), 0, st>>>(
+      n, w.y, t, net->p + net->L.off_w4, w.z[kDepth - 1], w.dy, w.dz[0], w.dzT[0], w.ldt);
   rc = backward(net, n, t, w, st);
   if (rc != MGX_OK) return rc;
   if (grad && cudaMemcpyAsync(grad, net->g, sizeof(float) * net->L.total, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
