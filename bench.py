@@ -465,8 +465,11 @@ def extra_surrogate(pkg, dev):
         n_unw = gen = calls = over = 0
         b = 0
         phases = {}
+        batch_s = []
         t0 = time.perf_counter()
         while (target is not None and n_unw < target) or (nbatch is not None and b < nbatch):
+            tb = time.perf_counter()
+            r = None                                 # the previous batch's buffers go back first
             r = fn(b, name == "surrogate")
             n_unw += int(r["weight"].shape[0])
             gen += r["generated"]
@@ -476,11 +479,13 @@ def extra_surrogate(pkg, dev):
                 for k, v in U.timing.items():
                     phases[k] = phases.get(k, 0.0) + v
             b += 1
+            batch_s.append(time.perf_counter() - tb)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         res[name] = {"value": n_unw / dt, "unit": "unweighted events/s", "generated": gen,
                      "unweighted": n_unw, "exact_me_calls": calls, "seconds": dt, "batches": b,
-                     "overweight_fraction": over / n_unw if n_unw else None}
+                     "overweight_fraction": over / n_unw if n_unw else None,
+                     "batch_seconds": [round(x, 4) for x in batch_s]}
         if phases:
             res[name]["phase_ms"] = phases
             res[name]["phase_ms_sum"] = sum(phases.values())

@@ -355,6 +355,16 @@ int mgx_mlp_gradients(mgx_mlp* net, int n, const float* x, const float* t, float
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on one batch. */
 int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, float lr, float* loss, void* ws,
                        size_t wsb, void* stream);
+/* The same two calls on a batch the library draws from a training set of ntotal examples (x
+ * [ntotal][24], t [ntotal], DEVICE): batch row r (0 <= r < batch) takes example
+ * j = floor(u ntotal), where u is the first 32-bit word of the Philox-4x32-10 block with counter
+ * (r, step mod 2^32, 0x4D4C5053, 0) under the 64-bit key seed, divided by 2^32 (sampling with
+ * replacement; a replica uses its own seed).  The batch rows are gathered into the workspace
+ * (workspace bytes as for a training batch of `batch` rows). */
+int mgx_mlp_gradients_sampled(mgx_mlp* net, int ntotal, const float* x, const float* t, int batch, uint64_t seed,
+                              uint64_t step, float* grad, float* loss, void* ws, size_t wsb, void* stream);
+int mgx_mlp_train_step_sampled(mgx_mlp* net, int ntotal, const float* x, const float* t, int batch, uint64_t seed,
+                               uint64_t step, float lr, float* loss, void* ws, size_t wsb, void* stream);
 /* One Adam step on a gradient the caller supplies (DEVICE, num_params floats): the update half of a
  * data-parallel training step, after the per-replica gradients of mgx_mlp_gradients have been
  * averaged across replicas (weighted by their batch sizes).  Replicas that start from the same
@@ -395,6 +405,31 @@ int mgx_compact(int64_t n, const uint8_t* keep, int32_t* index, int32_t* count_d
                 void* stream);
 /* dst[r][0..row) = src[index[r]][0..row) for r < m (float64 rows). */
 int mgx_gather(int64_t m, const int32_t* index, int row, const double* src, double* dst, void* stream);
+/* Training targets of the surrogate from exact matrix elements me[n] and the cut flags pass[n]
+ * (may be NULL: all pass): keep[i] = pass[i] && 0 < me[i] < inf, logme[i] = log(me[i]) where kept,
+ * 0 elsewhere.  DEVICE arrays; asynchronous. */
+int mgx_log_targets(int64_t n, const double* me, const uint8_t* pass, double* logme, uint8_t* keep, void* stream);
+/* sums[0] = sum y[i], sums[1] = sum y[i]^2, sums[2] = max y[i] (-inf when n = 0) over n float64
+ * values (DEVICE), in a fixed order (the same bits on every call): MGX_MOMENTS_BLOCKS blocks reduce
+ * contiguous ranges, then one block combines their partials.  sums is a DEVICE array of
+ * MGX_MOMENTS_LEN doubles; entries 3 .. MGX_MOMENTS_LEN - 1 are the partials (scratch).
+ * Asynchronous. */
+#define MGX_MOMENTS_BLOCKS 256
+#define MGX_MOMENTS_LEN (3 * (1 + MGX_MOMENTS_BLOCKS))
+int mgx_moments(int64_t n, const double* y, double* sums, void* stream);
+/* t[i] = float32((y[i] - mean) / sd), sd > 0 (the network's standardised targets).  DEVICE. */
+int mgx_standardize_f32(int64_t n, const double* y, double mean, double sd, float* t, void* stream);
+/* The unweighted events of one batch from the compacted survivors: event j of the output is
+ * idx2[j] of the last stage, or idx1[idx2[j]] with a first stage (idx1 may be NULL); weight[j] =
+ * over1[event] x over2[idx2[j]] (over2 may be NULL: a single stage), index[j] = first + event.
+ * DEVICE arrays (index int64); asynchronous. */
+int mgx_unweighted_out(int64_t m, const int32_t* idx2, const int32_t* idx1, const double* over1, const double* over2,
+                       int64_t first, double* weight, int64_t* index, void* stream);
+/* Reference maxima of the unweighting from n calibration events (exact weights w, surrogate weights
+ * s; DEVICE): maxima[0..2] (HOST) = the q-quantiles (0 < q <= 1; linear interpolation between
+ * order statistics at position q (m - 1); q = 1: the maxima) of w, s and w/s over the m events with
+ * w > 0 and s > 0, computed on the host after copying w and s back (synchronous on stream). */
+int mgx_unweighting_maxima(int64_t n, const double* w, const double* s, double q, double* maxima, void* stream);
 
 /* Measured fused-multiply-add throughput (TFLOP/s, fma = 2 flops) of the float64
  * (precision 64) or float32 (precision 32) pipe of `device`: independent FMA chains, no memory

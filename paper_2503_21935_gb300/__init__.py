@@ -23,6 +23,8 @@ MGX_FLOAT = 4
 MODES = {"fp64": MGX_FP64, "mixed_fp32": MGX_MIXED_FP32, "mixed_tf32": MGX_MIXED_TF32,
          "mixed_bf16x3": MGX_MIXED_BF16X3, "float": MGX_FLOAT}
 MGX_KERNEL_AUTO, MGX_KERNEL_THREAD, MGX_KERNEL_CTA, MGX_KERNEL_THREAD_SMEM = 0, 1, 2, 3
+MGX_MOMENTS_BLOCKS = 256
+MGX_MOMENTS_LEN = 3 * (1 + MGX_MOMENTS_BLOCKS)   # doubles of mgx_moments' output (3 results + partials)
 
 
 class MgxError(RuntimeError):
@@ -84,6 +86,11 @@ def lib():
             "mgx_compact_workspace_bytes": (I, [I64, ctypes.POINTER(SZ)]),
             "mgx_compact": (I, [I64, P, P, P, P, SZ, P]),
             "mgx_gather": (I, [I64, P, I, P, P, P]),
+            "mgx_log_targets": (I, [I64, P, P, P, P, P]),
+            "mgx_moments": (I, [I64, P, P, P]),
+            "mgx_standardize_f32": (I, [I64, P, D, D, P, P]),
+            "mgx_unweighted_out": (I, [I64, P, P, P, P, I64, P, P, P]),
+            "mgx_unweighting_maxima": (I, [I64, P, P, D, P, P]),
             "mgx_batch_create": (I, [P, I, ctypes.POINTER(P)]),
             "mgx_batch_destroy": (None, [P]),
             "mgx_batch_workspace_bytes": (I, [P, ctypes.POINTER(SZ)]),
@@ -103,6 +110,8 @@ def lib():
             "mgx_mlp_gradients": (I, [P, I, P, P, P, P, P, SZ, P]),
             "mgx_mlp_train_step": (I, [P, I, P, P, ctypes.c_float, P, P, SZ, P]),
             "mgx_mlp_adam_step": (I, [P, P, ctypes.c_float, P]),
+            "mgx_mlp_gradients_sampled": (I, [P, I, P, P, I, U64, U64, P, P, P, SZ, P]),
+            "mgx_mlp_train_step_sampled": (I, [P, I, P, P, I, U64, U64, ctypes.c_float, P, P, SZ, P]),
             "mgx_mlp_device_errors": (I, [P, ctypes.POINTER(I), I]),
             "mgx_mlp_set_wait_test": (I, [P, I, D]),
             "mgx_noalloc_scratch_bytes": (SZ, []),
@@ -395,6 +404,27 @@ class Mlp:
         ws = self._workspace(n, True)
         _check(lib().mgx_mlp_train_step(self._h, n, _ptr(xd), _ptr(td), ctypes.c_float(lr), _ptr(loss_out),
                                         _ptr(ws), ws.numel(), _stream(xd.device)), "mgx_mlp_train_step")
+
+    def train_step_sampled(self, x, t, batch, seed, step, lr=1e-3, loss_out=None):
+        """One Adam step on a batch the library draws (Philox, with replacement) from the device
+        training set x [ntotal][24], t [ntotal] (float32): mgx_mlp_train_step_sampled."""
+        import torch
+        x, t = self._dev(x, torch.float32), self._dev(t, torch.float32)
+        ws = self._workspace(batch, True)
+        _check(lib().mgx_mlp_train_step_sampled(self._h, x.shape[0], _ptr(x), _ptr(t), int(batch), int(seed), int(step),
+                                                ctypes.c_float(lr), _ptr(loss_out), _ptr(ws), ws.numel(),
+                                                _stream(x.device)), "mgx_mlp_train_step_sampled")
+
+    def device_gradients_sampled(self, x, t, batch, seed, step, loss_out=None):
+        """Gradient (device float32) on a batch drawn as by train_step_sampled."""
+        import torch
+        x, t = self._dev(x, torch.float32), self._dev(t, torch.float32)
+        g = torch.empty(self.nparams, dtype=torch.float32, device=x.device)
+        ws = self._workspace(batch, True)
+        _check(lib().mgx_mlp_gradients_sampled(self._h, x.shape[0], _ptr(x), _ptr(t), int(batch), int(seed), int(step),
+                                               _ptr(g), _ptr(loss_out), _ptr(ws), ws.numel(), _stream(x.device)),
+               "mgx_mlp_gradients_sampled")
+        return g
 
 
 def builtin_processes():

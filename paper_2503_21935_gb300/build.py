@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmgx.so")
 GENERATED = os.path.join(HERE, "csrc", "generated", "programs.inc")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("mgx.cu", "peaks.cu", "phase_space.cu", "mlp.cu", "unweight.cu")]
-HEADERS = [os.path.join(HERE, "csrc", f) for f in ("mgx_kernel.cuh", "mgx_ops.cuh", "real.cuh", "umma.cuh", "colour_tc.cuh")] + \
+HEADERS = [os.path.join(HERE, "csrc", f) for f in ("mgx_kernel.cuh", "mgx_ops.cuh", "real.cuh", "umma.cuh", "colour_tc.cuh", "philox.cuh")] + \
           [os.path.join(ROOT, "include", "mgx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

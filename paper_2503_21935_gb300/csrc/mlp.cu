@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "mgx.h"
+#include "philox.cuh"
 #include "umma.cuh"
 
 using namespace mgx;
@@ -482,6 +483,23 @@ __global__ void refresh_bf16_kernel(const float* __restrict__ p, ParamLayout L, 
   }
 }
 
+// A training batch drawn with replacement from ntotal examples: batch row r takes example
+// j = floor(u ntotal), u = (first word of the Philox-4x32-10 block with counter (r, step,
+// kSampleStream, 0) under key seed) / 2^32, computed as (word x ntotal) >> 32.
+constexpr uint32_t kSampleStream = 0x4D4C5053u;
+
+__global__ void sample_rows_kernel(int batch, int ntotal, const float* __restrict__ x, const float* __restrict__ t,
+                                   uint64_t seed, uint32_t step, float* __restrict__ xs, float* __restrict__ ts) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= batch) return;
+  uint32_t w[4];
+  philox_block(seed, kSampleStream, (uint64_t)r, step, w);
+  const int j = (int)(((uint64_t)w[0] * (uint64_t)ntotal) >> 32);
+#pragma unroll
+  for (int c = 0; c < kNin; ++c) xs[(size_t)r * kNin + c] = x[(size_t)j * kNin + c];
+  ts[r] = t[j];
+}
+
 // ---------------------------------------------------------------- inference
 // Activations between layers live in HBM as canonical K-major tiles: tile t (128 rows) of a K-wide
 // activation is K/kc chunks (kc = min(K, 64)) of 128 x kc bf16, each chunk contiguous in exactly the
@@ -760,6 +778,7 @@ struct MlpWs {
   __nv_bfloat16 *x, *xT, *h[kDepth], *hT[kDepth], *dz[2], *dzT[2];
   float *z[kDepth], *y, *dy, *loss;
   float* part;            // [kDwSlices][256][256] partial weight gradients
+  float *xs, *ts;         // a sampled training batch: inputs [n][24] and targets [n]
   int* err;
   int ldt;
   size_t bytes;
@@ -790,6 +809,8 @@ MlpWs ws_layout(char* base, int n) {
   w.dy = (float*)take((size_t)ldt * 4);
   w.loss = (float*)take(256);
   w.part = (float*)take((size_t)kDwSlices * kWidth * kWidth * 4);
+  w.xs = (float*)take((size_t)ldt * kNin * 4);
+  w.ts = (float*)take((size_t)ldt * 4);
   w.err = (int*)take(256);
   w.bytes = off;
   return w;
@@ -1079,6 +1100,24 @@ int adam_step(mgx_mlp* net, const float* g, float lr, cudaStream_t st) {
 int mgx_mlp_train_step(mgx_mlp* net, int n, const float* x, const float* t, float lr, float* loss, void* ws, size_t wsb,
                        void* stream) {
   const int rc = mgx_mlp_gradients(net, n, x, t, nullptr, loss, ws, wsb, stream);
+  if (rc != MGX_OK) return rc;
+  return adam_step(net, net->g, lr, (cudaStream_t)stream);
+}
+
+int mgx_mlp_gradients_sampled(mgx_mlp* net, int ntotal, const float* x, const float* t, int batch, uint64_t seed,
+                              uint64_t step, float* grad, float* loss, void* ws, size_t wsb, void* stream) {
+  if (!net || ntotal <= 0 || batch <= 0 || batch > (1 << 24) || !x || !t) return MGX_ERR_INVALID_ARGUMENT;
+  MlpWs w = ws_layout((char*)ws, batch);
+  if (!ws || wsb < w.bytes) return MGX_ERR_WORKSPACE_TOO_SMALL;
+  sample_rows_kernel<<<(batch + 255) / 256, 256, 0, (cudaStream_t)stream>>>(batch, ntotal, x, t, seed, (uint32_t)step,
+                                                                             w.xs, w.ts);
+  if (cudaGetLastError() != cudaSuccess) return MGX_ERR_CUDA;
+  return mgx_mlp_gradients(net, batch, w.xs, w.ts, grad, loss, ws, wsb, stream);
+}
+
+int mgx_mlp_train_step_sampled(mgx_mlp* net, int ntotal, const float* x, const float* t, int batch, uint64_t seed,
+                               uint64_t step, float lr, float* loss, void* ws, size_t wsb, void* stream) {
+  const int rc = mgx_mlp_gradients_sampled(net, ntotal, x, t, batch, seed, step, nullptr, loss, ws, wsb, stream);
   if (rc != MGX_OK) return rc;
   return adam_step(net, net->g, lr, (cudaStream_t)stream);
 }

@@ -10,27 +10,11 @@
 #include <cstdint>
 
 #include "mgx.h"
+#include "philox.cuh"
 
 namespace {
 
 constexpr int kMaxFinal = 8;
-
-__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-    const uint32_t h0 = __umulhi(0xD2511F53u, c[0]), l0 = 0xD2511F53u * c[0];
-    const uint32_t h1 = __umulhi(0xCD9E8D57u, c[2]), l1 = 0xCD9E8D57u * c[2];
-    const uint32_t n0 = h1 ^ c[1] ^ k0, n2 = h0 ^ c[3] ^ k1;
-    c[0] = n0; c[1] = l1; c[2] = n2; c[3] = l0;
-  }
-}
-
-// block `blk` of four words for event e: counter (e lo, blk, stream, e hi), key = seed
-__device__ __forceinline__ void philox_block(uint64_t seed, uint32_t stream, uint64_t e, uint32_t blk, uint32_t w[4]) {
-  w[0] = (uint32_t)e; w[1] = blk; w[2] = stream; w[3] = (uint32_t)(e >> 32);
-  philox10(w, (uint32_t)seed, (uint32_t)(seed >> 32));
-}
 
 __global__ void uniforms_kernel(int64_t n, int64_t first, uint64_t seed, uint32_t stream, double* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

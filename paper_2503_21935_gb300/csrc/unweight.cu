@@ -10,7 +10,10 @@
 // efficiency.  Survivors are compacted deterministically (scan, then scatter in event order).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "mgx.h"
 
@@ -135,7 +138,108 @@ __global__ void gather_kernel(int64_t m, const int32_t* __restrict__ index, int 
   dst[i] = src[(int64_t)index[r] * row + c];
 }
 
+// training targets: keep = pass && 0 < me < inf, logme = log(me) where kept (0 elsewhere)
+__global__ void log_targets_kernel(int64_t n, const double* __restrict__ me, const uint8_t* __restrict__ pass,
+                                   double* __restrict__ logme, uint8_t* __restrict__ keep) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double m = me[i];
+  const bool k = (!pass || pass[i]) && m > 0.0 && m < INFINITY;
+  keep[i] = k ? 1 : 0;
+  logme[i] = k ? log(m) : 0.0;
+}
+
+// (sum y, sum y^2, max y) in float64, in two passes of fixed order (the same bits on every run):
+// block b of MGX_MOMENTS_BLOCKS takes the contiguous range [b c, (b+1) c) of c = ceil(n / blocks)
+// values, its 256 threads stride through it in order and a fixed tree combines them into
+// part[3 b .. 3 b + 2]; then one block combines the blocks' partials by the same tree.
+__device__ void tree3(double& a, double& b, double& c) {
+  __shared__ double s1[256], s2[256], s3[256];
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  s3[threadIdx.x] = c;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      s1[threadIdx.x] += s1[threadIdx.x + h];
+      s2[threadIdx.x] += s2[threadIdx.x + h];
+      s3[threadIdx.x] = fmax(s3[threadIdx.x], s3[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  a = s1[0];
+  b = s2[0];
+  c = s3[0];
+}
+
+__global__ void __launch_bounds__(256) moments_part_kernel(int64_t n, const double* __restrict__ y,
+                                                            double* __restrict__ part) {
+  const int64_t chunk = (n + MGX_MOMENTS_BLOCKS - 1) / MGX_MOMENTS_BLOCKS;
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double a = 0.0, b = 0.0, c = -INFINITY;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += 256) {
+    const double v = y[i];
+    a += v;
+    b = fma(v, v, b);
+    c = fmax(c, v);
+  }
+  tree3(a, b, c);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+  }
+}
+
+__global__ void __launch_bounds__(256) moments_final_kernel(const double* __restrict__ part, double* __restrict__ out) {
+  double a = 0.0, b = 0.0, c = -INFINITY;
+  if (threadIdx.x < MGX_MOMENTS_BLOCKS) {
+    a = part[3 * threadIdx.x];
+    b = part[3 * threadIdx.x + 1];
+    c = part[3 * threadIdx.x + 2];
+  }
+  tree3(a, b, c);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+  }
+}
+
+__global__ void standardize_kernel(int64_t n, const double* __restrict__ y, double mean, double sd,
+                                   float* __restrict__ t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  t[i] = (float)((y[i] - mean) / sd);
+}
+
+// unweighted events: j-th kept event of the last stage is idx2[j]; with a first stage, its event
+// is idx1[idx2[j]] and its weight over1[idx1[idx2[j]]] x over2[idx2[j]]
+__global__ void unweighted_out_kernel(int64_t m, const int32_t* __restrict__ idx2, const int32_t* __restrict__ idx1,
+                                      const double* __restrict__ over1, const double* __restrict__ over2,
+                                      int64_t first, double* __restrict__ weight, int64_t* __restrict__ index) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int32_t i2 = idx2[j];
+  const int32_t i1 = idx1 ? idx1[i2] : i2;
+  weight[j] = over2 ? over1[i1] * over2[i2] : over1[i1];
+  index[j] = first + i1;
+}
+
 unsigned grid(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// q-quantile of v (linear interpolation between order statistics, positions q (n - 1)); v reordered
+double quantile(std::vector<double>& v, double q) {
+  if (v.empty()) return 0.0;
+  if (q >= 1.0) return *std::max_element(v.begin(), v.end());
+  const double pos = q * (double)(v.size() - 1);
+  const size_t lo = (size_t)pos;
+  std::nth_element(v.begin(), v.begin() + lo, v.end());
+  const double a = v[lo];
+  if (lo + 1 >= v.size()) return a;
+  const double b = *std::min_element(v.begin() + lo + 1, v.end());
+  return a + (b - a) * (pos - (double)lo);
+}
 
 }  // namespace
 
@@ -208,6 +312,58 @@ int mgx_gather(int64_t m, const int32_t* index, int row, const double* src, doub
   if (m == 0) return MGX_OK;
   gather_kernel<<<grid(m * row), kBlock, 0, (cudaStream_t)stream>>>(m, index, row, src, dst);
   return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+int mgx_log_targets(int64_t n, const double* me, const uint8_t* pass, double* logme, uint8_t* keep, void* stream) {
+  if (n < 0 || (n > 0 && (!me || !logme || !keep))) return MGX_ERR_INVALID_ARGUMENT;
+  if (n == 0) return MGX_OK;
+  log_targets_kernel<<<grid(n), kBlock, 0, (cudaStream_t)stream>>>(n, me, pass, logme, keep);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+int mgx_moments(int64_t n, const double* y, double* sums, void* stream) {
+  if (n < 0 || !sums || (n > 0 && !y)) return MGX_ERR_INVALID_ARGUMENT;
+  static_assert(MGX_MOMENTS_BLOCKS <= 256, "one thread per partial in the final pass");
+  moments_part_kernel<<<MGX_MOMENTS_BLOCKS, 256, 0, (cudaStream_t)stream>>>(n, y, sums + 3);
+  moments_final_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(sums + 3, sums);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+int mgx_standardize_f32(int64_t n, const double* y, double mean, double sd, float* t, void* stream) {
+  if (n < 0 || !(sd > 0.0) || (n > 0 && (!y || !t))) return MGX_ERR_INVALID_ARGUMENT;
+  if (n == 0) return MGX_OK;
+  standardize_kernel<<<grid(n), kBlock, 0, (cudaStream_t)stream>>>(n, y, mean, sd, t);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+int mgx_unweighted_out(int64_t m, const int32_t* idx2, const int32_t* idx1, const double* over1, const double* over2,
+                       int64_t first, double* weight, int64_t* index, void* stream) {
+  if (m < 0 || first < 0 || (m > 0 && (!idx2 || !over1 || !weight || !index))) return MGX_ERR_INVALID_ARGUMENT;
+  if (m == 0) return MGX_OK;
+  unweighted_out_kernel<<<grid(m), kBlock, 0, (cudaStream_t)stream>>>(m, idx2, idx1, over1, over2, first, weight,
+                                                                     index);
+  return cudaGetLastError() == cudaSuccess ? MGX_OK : MGX_ERR_CUDA;
+}
+
+int mgx_unweighting_maxima(int64_t n, const double* w, const double* s, double q, double* maxima, void* stream) {
+  if (n < 0 || !maxima || !(q > 0.0) || q > 1.0 || (n > 0 && (!w || !s))) return MGX_ERR_INVALID_ARGUMENT;
+  std::vector<double> hw((size_t)n), hs((size_t)n);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0 && (cudaMemcpyAsync(hw.data(), w, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpyAsync(hs.data(), s, n * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess))
+    return MGX_ERR_CUDA;
+  std::vector<double> pw, ps, pr;
+  for (int64_t i = 0; i < n; ++i)
+    if (hw[i] > 0.0 && hs[i] > 0.0) {
+      pw.push_back(hw[i]);
+      ps.push_back(hs[i]);
+      pr.push_back(hw[i] / hs[i]);
+    }
+  maxima[0] = quantile(pw, q);
+  maxima[1] = quantile(ps, q);
+  maxima[2] = quantile(pr, q);
+  return MGX_OK;
 }
 
 }  // extern "C"

@@ -27,7 +27,7 @@ import ctypes
 import numpy as np
 
 from . import (Mlp, MgxError, Process, _check, _ptr, _stream, lib, rambo, rambo_f32, rambo_indexed, cuts, cuts_f32,
-               uniforms, MGX_FP64)
+               uniforms, MGX_FP64, MGX_MOMENTS_LEN)
 from . import dist as _dist
 
 # relative widening of the cut thresholds applied to the float32 proposals: far above float32
@@ -158,33 +158,45 @@ class Unweighter:
         rank, world = _dist.rank_world()
         mom, wps, ok = self.events(ntrain, seed, first=rank * ntrain)
         me = self.exact_me(mom)
-        keep = ok.bool() & (me > 0)
-        x = self.features(mom)[keep].contiguous()
-        y = torch.log(me[keep])
+        n0 = me.shape[0]
+        logme = torch.empty(n0, dtype=torch.float64, device=self.dev)
+        keep = torch.empty(n0, dtype=torch.uint8, device=self.dev)
+        _check(lib().mgx_log_targets(n0, _ptr(me), _ptr(ok), _ptr(logme), _ptr(keep), _stream(self.dev)),
+               "mgx_log_targets")
+        idx = self._compact(keep)
+        x = self.features(self._gather(idx, mom))
+        y = self._gather(idx, logme)
+        n = y.shape[0]
         # standardisation from the moments of all ranks' targets (rank-order sums)
-        s1, s2, cnt = _dist.allreduce_sums([float(y.sum().item()), float((y * y).sum().item()), int(y.numel())],
-                                           device=self.dev)
+        s1, s2, _ = self._moments(y)
+        s1, s2, cnt = _dist.allreduce_sums([s1, s2, n], device=self.dev)
         self.mean = s1 / cnt
         self.sd = float(np.sqrt(max(s2 / cnt - self.mean ** 2, 0.0) * cnt / max(cnt - 1, 1)))
-        t = ((y - self.mean) / self.sd).to(torch.float32).contiguous()
-        n = x.shape[0]
-        g = torch.Generator(device=self.dev)
-        g.manual_seed(seed + 7 * rank)
+        t = torch.empty(n, dtype=torch.float32, device=self.dev)
+        _check(lib().mgx_standardize_f32(n, _ptr(y), self.mean, self.sd, _ptr(t), _stream(self.dev)),
+               "mgx_standardize_f32")
+        # every step's batch is drawn by the library from the replica's own training set
+        key = seed + 7919 * rank
         hist = []
         loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
         for step in range(steps):
-            idx = torch.randint(0, n, (batch,), device=self.dev, generator=g)
-            frac = step / max(1, steps - 1)
-            rate = lr * (lr_decay ** frac)
+            rate = lr * (lr_decay ** (step / max(1, steps - 1)))
             if world == 1:
-                self.net.train_step(x[idx].contiguous(), t[idx].contiguous(), lr=rate, loss_out=loss)
+                self.net.train_step_sampled(x, t, batch, key, step, lr=rate, loss_out=loss)
             else:
-                grad = self.net.device_gradients(x[idx].contiguous(), t[idx].contiguous(), loss_out=loss)
+                grad = self.net.device_gradients_sampled(x, t, batch, key, step, loss_out=loss)
                 _dist.allreduce_gradients(grad, batch)
                 self.net.adam_step(grad, lr=rate)
             if step % max(1, steps // 20) == 0 or step == steps - 1:
                 hist.append((step, float(loss.item())))
         return hist
+
+    def _moments(self, v):
+        """(sum, sum of squares, max) of a device float64 vector, in the library's fixed order."""
+        import torch
+        out = torch.empty(MGX_MOMENTS_LEN, dtype=torch.float64, device=self.dev)
+        _check(lib().mgx_moments(v.shape[0], _ptr(v), _ptr(out), _stream(self.dev)), "mgx_moments")
+        return tuple(out[:3].tolist())
 
     # ------------------------------------------------------------------ calibration
     def calibration_sample(self, n, seed, first=0):
@@ -198,17 +210,11 @@ class Unweighter:
     def set_maxima(self, w, s, q=0.999):
         """Reference maxima from calibration weights: w_max (plain), s_max and r_max (two-stage), the
         q-quantiles of w, s and w/s over the events with w > 0 and s > 0 (q = 1: the maxima)."""
-        sel = (w > 0) & (s > 0)
-        ws, ss = w[sel], s[sel]
-
-        def quant(v):
-            if q >= 1.0:
-                return float(v.max().item())
-            if v.numel() <= 1 << 24:
-                return float(v.quantile(q).item())
-            k = max(0, int(np.ceil(q * v.numel())) - 1)
-            return float(v.kthvalue(k + 1).values.item())
-        self.w_max, self.s_max, self.r_max = quant(ws), quant(ss), quant(ws / ss)
+        out = (ctypes.c_double * 3)()
+        w, s = w.contiguous(), s.contiguous()     # held until the call has copied them back
+        _check(lib().mgx_unweighting_maxima(w.shape[0], _ptr(w), _ptr(s), float(q), ctypes.cast(out, ctypes.c_void_p),
+                                            _stream(self.dev)), "mgx_unweighting_maxima")
+        self.w_max, self.s_max, self.r_max = out[0], out[1], out[2]
         return self.w_max, self.s_max, self.r_max
 
     def calibrate(self, n, seed=202, q=0.999):
@@ -223,8 +229,18 @@ class Unweighter:
     # ------------------------------------------------------------------ unweighting
     def _stats(self, w):
         """Global (max w, sum w, N) of a batch: one collective across ranks."""
-        mx = float(w.max().item()) if w.numel() else 0.0
-        return _dist.allreduce_weight_stats(mx, float(w.sum().item()), int(w.numel()), device=self.dev)
+        sw, _, mx = self._moments(w) if w.numel() else (0.0, 0.0, 0.0)
+        return _dist.allreduce_weight_stats(mx, sw, int(w.numel()), device=self.dev)
+
+    def _unweighted(self, idx2, idx1, over1, over2, first):
+        """Weights and global indices of the unweighted events (mgx_unweighted_out)."""
+        import torch
+        m = idx2.shape[0]
+        weight = torch.empty(m, dtype=torch.float64, device=self.dev)
+        index = torch.empty(m, dtype=torch.int64, device=self.dev)
+        _check(lib().mgx_unweighted_out(m, _ptr(idx2), _ptr(idx1), _ptr(over1), _ptr(over2), int(first),
+                                        _ptr(weight), _ptr(index), _stream(self.dev)), "mgx_unweighted_out")
+        return weight, index
 
     def plain(self, n, seed, first=0):
         """Hit-or-miss on the exact weight of events first .. first+n-1."""
@@ -234,7 +250,8 @@ class Unweighter:
         keep, over = self._accept(w, None, self.w_max, uniforms(n, seed, 11, first=first, device=self.dev.index))
         idx = self._compact(keep)
         mx, sw, nn = self._stats(w)
-        return dict(momenta=self._gather(idx, mom), weight=over[idx.long()], index=first + idx.long(),
+        weight, index = self._unweighted(idx, None, over, None, first)
+        return dict(momenta=self._gather(idx, mom), weight=weight, index=index,
                     exact_calls=self.exact_calls - calls, generated=n, all_weights=w, all_momenta=mom,
                     max_w=mx, sum_w=sw, n_events=nn)
 
@@ -271,9 +288,8 @@ class Unweighter:
         w1 = self._weights(me1, wps1, ok1)
         keep2, over2 = self._accept(w1, s1, self.r_max, r2)
         idx2 = self._compact(keep2)
-        l2 = idx2.long()
-        weight = over1[idx1.long()][l2] * over2[l2]
-        out = dict(momenta=self._gather(idx2, m1), weight=weight, index=first + idx1.long()[l2],
+        weight, index = self._unweighted(idx2, idx1, over1, over2, first)
+        out = dict(momenta=self._gather(idx2, m1), weight=weight, index=index,
                    exact_calls=self.exact_calls - calls, generated=n, stage1=int(idx1.shape[0]))
         mark("stage-2 accept and compaction")
         if profile:

@@ -48,3 +48,12 @@ def test_host_only_calls(libpath):
     h = ctypes.c_void_p()
     assert pkg.lib().mgx_process_create(None, None, 0, 0, ctypes.byref(h)) == -1
     assert pkg.lib().mgx_compute(None, 10, None, None, None, None, None, None, None, 0, None, 0, None) == -1
+
+
+def test_binding_constants_match_header():
+    """Constants the binding repeats from include/mgx.h (sizes and enum values) equal the header's."""
+    import paper_2503_21935_gb300 as pkg
+    src = open(os.path.join(ROOT, "include", "mgx.h")).read()
+    assert int(re.search(r"#define MGX_MOMENTS_BLOCKS (\d+)", src).group(1)) == pkg.MGX_MOMENTS_BLOCKS
+    assert pkg.MGX_MOMENTS_LEN == 3 * (1 + pkg.MGX_MOMENTS_BLOCKS)
+    assert re.search(r"MGX_KERNEL_HELICITY = 4, MGX_KERNEL_SPLIT = 5", src)

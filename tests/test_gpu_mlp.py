@@ -103,3 +103,27 @@ def test_inference_from_momenta_and_across_passes():
     tail = net.forward(x[(1 << 22) - 100:].contiguous())
     assert torch.equal(tail, y_x[(1 << 22) - 100:])
     assert torch.isfinite(y_x).all()
+
+
+def test_sampled_training_step_draws_the_documented_rows():
+    """mgx_mlp_train_step_sampled is mgx_mlp_train_step on the rows its header documents: batch row
+    r takes example floor(w0 ntotal / 2^32), w0 the first word of Philox-4x32-10 with counter
+    (r, step, 0x4D4C5053, 0) under the seed (computed here by the host generator), bit for bit."""
+    import torch
+    from phasespace.philox import philox4x32_10
+    rng = np.random.default_rng(4)
+    ntotal, batch, seed, step = 5000, 1024, 0x123456789ABC, 7
+    x = rng.normal(size=(ntotal, 24)).astype(np.float32)
+    t = rng.normal(size=ntotal).astype(np.float32)
+    r = np.arange(batch, dtype=np.uint64)
+    ctr = np.stack([r & np.uint64(0xFFFFFFFF), np.full(batch, step, np.uint64), np.full(batch, 0x4D4C5053, np.uint64),
+                    r >> np.uint64(32)], axis=-1).astype(np.uint32)
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+    w0 = philox4x32_10(ctr, key)[:, 0].astype(np.uint64)
+    idx = ((w0 * np.uint64(ntotal)) >> np.uint64(32)).astype(np.int64)
+    assert len(np.unique(idx)) > 0.8 * batch
+    a, b = _net(seed=5), _net(seed=5)
+    a.train_step_sampled(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), batch, seed, step, lr=1e-3)
+    b.train_step(x[idx], t[idx], lr=1e-3)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.get_params(), b.get_params())
