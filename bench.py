@@ -18,6 +18,7 @@ collective); rank 0 prints one JSON line.  --impl reference times the float64
 CPU oracle on the host cores instead (bounded sample of the same workload).
 """
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -462,10 +463,11 @@ def extra_surrogate(pkg, dev):
     for name, fn, target, nbatch in legs:
         fn(1 << 10, False)                         # warm-up (batch index far from the timed ones)
         torch.cuda.synchronize()
-        n_unw = gen = calls = over = 0
+        n_unw = gen = calls = 0
         b = 0
         phases = {}
         batch_s = []
+        weights = []                                 # for the overweight count after the timed region
         t0 = time.perf_counter()
         while (target is not None and n_unw < target) or (nbatch is not None and b < nbatch):
             tb = time.perf_counter()
@@ -474,7 +476,7 @@ def extra_surrogate(pkg, dev):
             n_unw += int(r["weight"].shape[0])
             gen += r["generated"]
             calls += r["exact_calls"]
-            over += int((r["weight"] > 1).sum().item())
+            weights.append(r["weight"])
             if name == "surrogate" and U.timing:
                 for k, v in U.timing.items():
                     phases[k] = phases.get(k, 0.0) + v
@@ -482,6 +484,7 @@ def extra_surrogate(pkg, dev):
             batch_s.append(time.perf_counter() - tb)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        over = sum(int((w > 1).sum().item()) for w in weights)
         res[name] = {"value": n_unw / dt, "unit": "unweighted events/s", "generated": gen,
                      "unweighted": n_unw, "exact_me_calls": calls, "seconds": dt, "batches": b,
                      "overweight_fraction": over / n_unw if n_unw else None,
@@ -629,6 +632,10 @@ def run_gpu(args):
                             ("batched", lambda: extra_batched(pkg, dev, stream)),
                             ("surrogate_unweighting", lambda: extra_surrogate(pkg, dev)),
                             ("phase_space", lambda: extra_phase_space(pkg, dev))):
+                # each workload starts from an empty allocator cache (the previous ones' workspaces,
+                # up to 60 GB for g g > t t~ g g g, would otherwise stay reserved)
+                gc.collect()
+                torch.cuda.empty_cache()
                 t0 = time.perf_counter()
                 try:
                     extras[key] = fn()
