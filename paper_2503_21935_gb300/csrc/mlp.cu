@@ -268,15 +268,21 @@ __global__ void __launch_bounds__(kRows) gemm_bf16_kernel(const GemmArgs g) {
   }
 }
 
+constexpr int kMaxDevices = 64;
+
+int current_device() {
+  int dev = 0;
+  return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices ? dev : -1;
+}
+
+// SM count of the current device (cached per device)
 int sm_count_cached() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      n = 0;
-    if (n <= 0) n = 148;
-  }
-  return n;
+  static int n[kMaxDevices] = {};
+  const int dev = current_device();
+  if (dev < 0) return 148;
+  if (n[dev] <= 0 && (cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n[dev] <= 0))
+    n[dev] = 148;
+  return n[dev];
 }
 
 size_t gemm_smem(const GemmArgs& g) {
@@ -295,11 +301,12 @@ int gemm(GemmArgs g, cudaStream_t st) {
   g.nt = std::min(g.N, kWidth);
   while (g.nt > 64 && g.N % (g.nt / 2) == 0 && mtiles * ((g.N + g.nt - 1) / g.nt) < 3 * sm_count_cached()) g.nt /= 2;
   const size_t smem = gemm_smem(g);
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[kMaxDevices] = {};   // the attribute is set once per device
+  const int dev = current_device();
+  if (dev < 0 || !attr[dev]) {
     if (cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024) != cudaSuccess)
       return MGX_ERR_CUDA;
-    attr = true;
+    if (dev >= 0) attr[dev] = true;
   }
   dim3 grid((g.M + kRows - 1) / kRows, (g.N + g.nt - 1) / g.nt, zs);
   gemm_bf16_kernel<<<grid, kRows, smem, st>>>(g);
