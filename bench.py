@@ -517,7 +517,7 @@ def run_gpu(args):
             dist.barrier()
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:     # the oracle baseline at N = 1 only
         cores = _host_cores()
         per_core = 8 * ORACLE_CHUNK        # about 10 s of oracle work per host process
         rate, n, busy, wall = cpu_oracle_rate(args.workload, per_core, cores)

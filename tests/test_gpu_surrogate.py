@@ -108,3 +108,26 @@ def test_data_parallel_training_step_equals_full_batch():
     # gradient changes that only where the gradient is tiny against its own rounding
     assert np.median(np.abs(pa - pb)) <= 1e-9 and np.quantile(np.abs(pa - pb), 0.99) <= 2e-5
     assert np.median(step) > 5e-4
+
+
+def test_tiny_batches_and_empty_stages():
+    """Batches of 1 to 64 events, and maxima so large that a stage keeps nothing: every call of the
+    chain (indexed RAMBO, cuts, exact |M|^2, accept, compaction, outputs) runs on the empty case and
+    the outputs stay consistent."""
+    from paper_2503_21935_gb300.surrogate import Unweighter
+    U = Unweighter("g g > t t~ g g", 1500.0, [173.0, 173.0, 0.0, 0.0], cut_particles=[4, 5], seed=5)
+    U.train(1 << 12, steps=20, batch=512, lr=2e-3)
+    U.calibrate(1 << 12)
+    for n in (1, 8, 64):
+        for fn in (U.plain, U.two_stage):
+            r = fn(n, seed=77, first=1000)
+            m = r["weight"].shape[0]
+            assert r["index"].shape[0] == m and r["momenta"].shape == (m, 6, 4)
+            if m:
+                assert bool((r["weight"] >= 1).all())
+                assert bool((r["index"] >= 1000).all()) and bool((r["index"] < 1000 + n).all())
+    U.w_max = U.s_max = U.r_max = 1e300
+    for fn in (U.plain, U.two_stage):
+        r = fn(256, seed=78)
+        assert r["weight"].shape[0] == 0 and r["momenta"].shape == (0, 6, 4)
+    assert U.two_stage(256, seed=78)["stage1"] == 0
