@@ -390,7 +390,10 @@ int mgx_features(int64_t n, int ncomp, const double* momenta, double scale, floa
 /* s = exp(mean + sd y) * wps * pass (wps, pass may be NULL). */
 int mgx_surrogate_weight(int64_t n, const float* y, double mean, double sd, const double* wps,
                          const uint8_t* pass, double* s, void* stream);
-/* The same with a float32 phase-space weight wps (from mgx_rambo_f32). */
+/* The same with a float32 phase-space weight wps (from mgx_rambo_f32), computed in float32
+ * (fast-math exponential, a few ulp; s = float(exp(float(mean) + float(sd) y) wps)) when the
+ * exponent's magnitude is below 80 and in float64 otherwise: a proposal weight only has to be
+ * positive wherever the exact weight is. */
 int mgx_surrogate_weight_f32(int64_t n, const float* y, double mean, double sd, const float* wps,
                              const uint8_t* pass, double* s, void* stream);
 /* w = me * wps * pass (wps, pass may be NULL). */

@@ -511,7 +511,9 @@ __global__ void sample_rows_kernel(int batch, int ntotal, const float* __restric
 // Activations between layers live in HBM as canonical K-major tiles: tile t (128 rows) of a K-wide
 // activation is K/kc chunks (kc = min(K, 64)) of 128 x kc bf16, each chunk contiguous in exactly the
 // layout tcgen05 reads from shared memory, so every operand load is one bulk copy.
-constexpr int kInfThreads = 192;   // warps 0-3: epilogue (tensor-memory lanes 0-127); 4: loads; 5: MMAs
+constexpr int kInfThreads = 320;   // warps 0-7: epilogue (warp w: tensor-memory lanes 32 (w % 4) .. +31,
+                                   // columns 128 (w / 4) .. +127); 8: loads; 9: MMAs
+constexpr int kInfEpi = 256;       // epilogue threads
 constexpr int kInfStages = 4;      // operand chunks in flight
 constexpr int64_t kInferRows = 1 << 22;   // rows per pass of the layer kernels (workspace ~1.1 KB / row)
 
@@ -555,14 +557,17 @@ struct InferArgs {
 
 size_t infer_smem(int K) {
   const int kc = K < 64 ? K : 64;
-  return (size_t)kWidth * K * 2 + (size_t)kInfStages * kRows * kc * 2 + 2 * kWidth * 4 + 16 * 8 + 16;
+  return (size_t)kWidth * K * 2 + (size_t)kInfStages * kRows * kc * 2 + 2 * kWidth * 4 + 2 * 2 * kRows * 4 + 16 * 8 +
+         16;
 }
 
 // One hidden layer (+ the output layer when h == nullptr) over all tiles: a persistent block keeps
 // the layer's weights in shared memory, streams the input tiles through a ring of kInfStages chunk
-// buffers (bulk copies, warp 4), accumulates each tile's 128 x 256 product into one of two
-// tensor-memory accumulators (tcgen05.mma issued by warp 5), and its four epilogue warps apply bias
-// and SiLU to the other accumulator meanwhile and write the bf16 activations (or the scalar output).
+// buffers (bulk copies, warp 8), accumulates each tile's 128 x 256 product into one of two
+// tensor-memory accumulators (tcgen05.mma issued by warp 9), and its eight epilogue warps (two per
+// tensor-memory lane quarter, one per half of the columns) apply bias and SiLU to the other
+// accumulator meanwhile and write the bf16 activations; in the last layer each half forms its part
+// of the 256 -> 1 output, and the two parts are added in shared memory (one named barrier per tile).
 // Every wait is bounded; a wait that runs out sets the block's abort flag, the remaining outputs of
 // the block become NaN and the error is counted.
 __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferArgs g) {
@@ -573,7 +578,8 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
   unsigned char* sa = sm + wbytes;
   float* sbias = reinterpret_cast<float*>(sa + kInfStages * cbytes);
   float* sw4 = sbias + kWidth;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sw4 + kWidth);
+  float* ypart = sw4 + kWidth;   // [tile parity][column half][row] partial outputs of the last layer
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ypart + 2 * 2 * kRows);
   uint64_t *full = bar, *empty = bar + kInfStages, *accf = bar + 2 * kInfStages, *acce = accf + 2;
   uint64_t *wfull = acce + 2, *drain = wfull + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
@@ -586,7 +592,7 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
     }
     for (int i = 0; i < 2; ++i) {
       umma::mbar_init(accf + i, 1);
-      umma::mbar_init(acce + i, 4 * 32);
+      umma::mbar_init(acce + i, kInfEpi);
     }
     umma::mbar_init(wfull, 1);
     umma::mbar_init(drain, 1);
@@ -601,7 +607,7 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tslot;
-  if (warp == 4) {
+  if (warp == 8) {
     if (lane == 0) {
       // the layer's weights once, then the input tiles' chunks through the ring
       umma::mbar_arrive_expect_tx(wfull, wbytes);
@@ -627,7 +633,7 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
         umma::mbar_wait(full + j % kInfStages, (j / kInfStages) & 1, g.wait_ns);
       umma::mbar_wait(wfull, 0, g.wait_ns);
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     if (lane == 0) {
       bool ok = umma::mbar_wait(wfull, 0, g.wait_ns);
       if (!ok) *abort_flag = 1;
@@ -668,9 +674,12 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
       }
     }
   } else {
-    // epilogue: thread t owns row t of each tile (tensor-memory lane t)
+    // epilogue: warp w owns rows 32 (w % 4) .. +31 of each tile (its tensor-memory lane quarter) and
+    // columns 128 (w / 4) .. +127
     const float nan = __int_as_float(0x7fc00000);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int quarter = warp & 3, half = warp >> 2, r = quarter * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const int c_lo = half * (kWidth / 2);
     bool ok = true;
     uint32_t lt = 0;
     for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++lt) {
@@ -684,10 +693,10 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
         }
       }
       umma::fence_after_sync();
-      const int64_t row = tile * kRows + t;
+      const int64_t row = tile * kRows + r;
       float y = 0.0f;
       unsigned char* out = g.h ? reinterpret_cast<unsigned char*>(g.h) + (size_t)tile * kRows * kWidth * 2 : nullptr;
-      for (int n0 = 0; n0 < kWidth; n0 += 32) {
+      for (int n0 = c_lo; n0 < c_lo + kWidth / 2; n0 += 32) {
         float v[32];
         if (ok) {
           umma::tmem_ld32(tmem + b * kWidth + lane_base + (uint32_t)n0, v);
@@ -696,29 +705,47 @@ __global__ void __launch_bounds__(kInfThreads, 1) mlp_infer_kernel(const InferAr
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = nan;
         }
+        float bv[32];   // this chunk's bias (shared memory, 16-byte loads)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 f = reinterpret_cast<const float4*>(sbias + n0)[q];
+          bv[4 * q] = f.x; bv[4 * q + 1] = f.y; bv[4 * q + 2] = f.z; bv[4 * q + 3] = f.w;
+        }
         if (out) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             __align__(16) __nv_bfloat16 hv[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const float z = v[8 * j + q] + sbias[n0 + 8 * j + q];
+              const float z = v[8 * j + q] + bv[8 * j + q];
               hv[q] = __float2bfloat16_rn(z * __fdividef(1.0f, 1.0f + __expf(-z)));
             }
             const int n = n0 + 8 * j;
-            *reinterpret_cast<uint4*>(out + (n / 64) * (kRows * 64 * 2) + umma::kmajor_offset(t, n % 64, 64, 2)) =
+            *reinterpret_cast<uint4*>(out + (n / 64) * (kRows * 64 * 2) + umma::kmajor_offset(r, n % 64, 64, 2)) =
                 *reinterpret_cast<const uint4*>(hv);
           }
         } else {
+          float wv[32];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 f = reinterpret_cast<const float4*>(sw4 + n0)[q];
+            wv[4 * q] = f.x; wv[4 * q + 1] = f.y; wv[4 * q + 2] = f.z; wv[4 * q + 3] = f.w;
+          }
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
-            const float z = v[q] + sbias[n0 + q];
+            const float z = v[q] + bv[q];
             const float h = __bfloat162float(__float2bfloat16_rn(z * __fdividef(1.0f, 1.0f + __expf(-z))));
-            y = fmaf(h, sw4[n0 + q], y);
+            y = fmaf(h, wv[q], y);
           }
         }
       }
-      if (!out && row < g.nrows) g.y[row] = ok ? y + g.b4[0] : nan;
+      if (!out) {
+        // y = (columns 0..127 part) + (columns 128..255 part) + b4, the same order for every row
+        float* yp = ypart + (lt & 1) * 2 * kRows;
+        yp[half * kRows + r] = y;
+        asm volatile("bar.sync 1, %0;" ::"n"(kInfEpi) : "memory");
+        if (half == 0 && row < g.nrows) g.y[row] = ok ? (yp[r] + yp[kRows + r]) + g.b4[0] : nan;
+      }
       umma::fence_before_sync();
       if (ok) umma::mbar_arrive(acce + b);
     }

@@ -46,7 +46,13 @@ __global__ void surrogate_weight_f32_kernel(int64_t n, const float* __restrict__
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool ok = pass == nullptr || pass[i];
-  s[i] = ok ? exp(mean + sd * (double)y[i]) * (wps ? (double)wps[i] : 1.0) : 0.0;
+  // a proposal weight only has to be a positive function of the event (stage 2 divides it out), so
+  // the exponential runs in float32 (one MUFU op instead of a float64 polynomial on GB300's slow
+  // float64 pipe) wherever float32 holds it
+  const float af = fmaf((float)sd, y[i], (float)mean);
+  const float w = wps ? wps[i] : 1.0f;
+  const double v = fabsf(af) < 80.0f ? (double)(__expf(af) * w) : exp(mean + sd * (double)y[i]) * (double)w;
+  s[i] = ok ? v : 0.0;
 }
 
 // exact weight w = me * wps * pass
