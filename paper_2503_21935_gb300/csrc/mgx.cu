@@ -370,28 +370,40 @@ __global__ void __launch_bounds__(kThreads, 4)
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
-  const uint32_t tmem = *tslot;
-  uint32_t phase = 0;
+  // Nothing but the loop position stays live across the op table (the tensor-memory address is read
+  // back from shared memory and the mbarrier phase restarts at 0 every pass: a pass completes an even
+  // number of phases, two parts per helicity and chunk), so the op table keeps the registers of the
+  // plain thread kernel.
+  int64_t base = (int64_t)blockIdx.x * blockDim.x;
   bool healthy = true;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nevt; base += nthreads) {
+  uint32_t fail_phase = 0;
+  for (; base < nevt; base += nthreads) {
     const int64_t e = base + threadIdx.x;
     const bool valid = e < nevt;
-    if (healthy) {
-      stage_momenta(mom, base, min((int64_t)blockDim.x, nevt - base), npar4, smem);
-      if (valid) eval_amplitudes<double>(P, smem + threadIdx.x * npar4, W);
-      const double scale = valid ? coupling_scale(P, alphas[e]) : 0.0;
-      __syncthreads();                      // the staged momenta are dead: the stage reuses them
-      healthy = tc_colour_sums<F>(P, A, W, valid, e, scale, mh_out, raw, mbar, tmem, phase);
-      if (healthy && valid) finish_from_workspace<double>(P, e, W, scale, rhel, rcol, me, selhel, selcol, colw_out);
-      if (!healthy && threadIdx.x == 0 && A.status) atomicAdd(A.status, 1);
+    stage_momenta(mom, base, min((int64_t)blockDim.x, nevt - base), npar4, smem);
+    if (valid) eval_amplitudes<double>(P, smem + threadIdx.x * npar4, W);
+    const double scale = valid ? coupling_scale(P, alphas[e]) : 0.0;
+    __syncthreads();                      // the staged momenta are dead: the stage reuses them
+    uint32_t phase = 0;
+    if (!tc_colour_sums<F>(P, A, W, valid, e, scale, mh_out, raw, mbar, *tslot, phase)) {
+      healthy = false;
+      fail_phase = phase;
+      break;
     }
-    if (!healthy && valid) {
+    if (valid) finish_from_workspace<double>(P, e, W, scale, rhel, rcol, me, selhel, selcol, colw_out);
+  }
+  if (!healthy) {
+    if (threadIdx.x == 0 && A.status) atomicAdd(A.status, 1);
+    for (; base < nevt; base += nthreads) {   // this pass and every later one: NaN and -1
+      const int64_t e = base + threadIdx.x;
+      if (e >= nevt) continue;
       me[e] = __longlong_as_double(0x7ff8000000000000ll);
       if (selhel) selhel[e] = -1;
       if (selcol) selcol[e] = -1;
     }
+    umma::mbar_wait(mbar, fail_phase ^ 1, A.wait_ns);   // bounded wait for MMAs still in flight
   }
-  if (!healthy) umma::mbar_wait(mbar, phase ^ 1, A.wait_ns);   // bounded wait for MMAs still in flight
+  const uint32_t tmem = *tslot;
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -1413,8 +1425,9 @@ int mgx_process_create(const char* process, const mgx_params* params, int device
     pr->tc_kpad = (n + 7) / 8 * 8;
     pr->tc_kpad16 = (n + 15) / 16 * 16;
     pr->tc_npad = (n + 15) / 16 * 16;
-    pr->tc_cols = 32;
-    while (pr->tc_cols < pr->tc_npad) pr->tc_cols *= 2;
+    pr->tc_cols = 32;   // one accumulator, or two (Re and Im) when the contraction is one stage
+    const int tc_need = pr->tc_kpad16 <= kTcKc ? 2 * pr->tc_npad : pr->tc_npad;
+    while (pr->tc_cols < tc_need) pr->tc_cols *= 2;
     const int np = pr->tc_npad;
     std::vector<float> b32;
     std::vector<uint16_t> b16;
