@@ -14,7 +14,9 @@ Q.V or row R.psi, chosen by an exact minimum vertex cover); terms with one colou
 vector up to a phase form a group; terms of a group sharing a bilinear form a run
 whose other operands are summed by a SUM op (once per helicity state of their legs).
 AMP ops take one product per run and good helicity and add the group amplitude,
-times a phase in {1, i, -1, -i}, to the group's colour flows.
+times a phase in {1, i, -1, -i}, to the group's colour flows.  Where it is cheaper, the
+single-run groups of one bilinear are closed flow-major instead: one summed current per colour
+flow they reach and one AMP op per flow (see _flow_major_bilinears).
 """
 import itertools
 import math
@@ -377,6 +379,32 @@ def _closure(D, ti):
     return out
 
 
+def _flow_major_bilinears(B, groups, gruns):
+    """Bilinears whose single-run groups are cheaper closed flow by flow.  Group-major (the default)
+    costs, per good helicity, one product X . Y_g per group plus a jamp add per (group, flow);
+    flow-major costs one product and one jamp add per colour flow the groups reach and helicity,
+    plus, per helicity state of the other legs, a 4-vector add per further (group, flow) entry to
+    form the flow's summed current.  A bilinear shared by many groups that reach few flows
+    (a row bilinear over the root and one gluon: 15 groups on 6 flows in g g > t t~ g g) gains.
+    Costs are float64 instructions of the kernels with 2^npar helicities.  Returns {(X, kind):
+    [group indices]} for the bilinears to close flow-major."""
+    nhel = 1 << B.npar
+    byx = {}
+    for gi, eff in enumerate(gruns):
+        if len(eff) == 1 and len(eff[0][2]) == 1:
+            byx.setdefault(eff[0][:2], []).append(gi)
+    out = {}
+    for key, gis in byx.items():
+        nvar_y = B.nvar(gruns[gis[0]][0][2][0][0])
+        entries = sum(len(groups[g][2]) for g in gis)
+        nflows = len({f for g in gis for f, _ in groups[g][2]})
+        group_major = nhel * (16 * len(gis) + 2 * entries)
+        flow_major = nhel * 18 * nflows + 8 * nvar_y * (entries - nflows)
+        if flow_major < group_major:
+            out[key] = gis
+    return out
+
+
 def _dfs_schedule(B):
     """Thread-per-event schedule: ops in depth-first order, blocks freed after last use."""
     D = B.D
@@ -393,35 +421,67 @@ def _dfs_schedule(B):
         done.add(i)
         order.append(("C", i))
     groups = _term_groups(D)
+
+    def sum_node(items):
+        mask = cur[items[0][0]].mask
+        if any(cur[y].mask != mask for y, _ in items):
+            raise ValueError("summands cover different legs")
+        node = Current(len(cur), mask, cur[items[0][0]].flav, "SUM", children=tuple(y for y, _ in items))
+        node.phases = [ph for _, ph in items]
+        cur.append(node)
+        return node.id
     # a run of several terms closing on one bilinear gets a sum current: the phased sum of its
     # other operands (all over the same legs), computed once per helicity state of those legs
     # instead of once per full helicity inside the amplitude row
     gruns = []
+    for g in groups:
+        gruns.append([(x, kind, [(sum_node(items), 0)] if len(items) > 1 else items)
+                      for x, kind, items in _runs(D, g)])
+    flow_major = _flow_major_bilinears(B, groups, gruns)
+    amps = []                       # (runs, flows) of each AMP row
+    handled = set()
     for gi, g in enumerate(groups):
-        eff = []
-        for x, kind, items in _runs(D, g):
-            if len(items) > 1:
-                mask = cur[items[0][0]].mask
-                if any(cur[y].mask != mask for y, _ in items):
-                    raise ValueError("terms of one bilinear cover different legs")
-                node = Current(len(cur), mask, cur[items[0][0]].flav, "SUM", children=tuple(y for y, _ in items))
-                node.phases = [ph for _, ph in items]
-                cur.append(node)
-                items = [(node.id, 0)]
-            eff.append((x, kind, items))
-        gruns.append(eff)
+        if gi in handled:
+            continue
+        eff = gruns[gi]
+        key = eff[0][:2] if len(eff) == 1 else None
+        if key in flow_major:
+            # flow-major closure of every single-run group on this bilinear X: per colour flow f,
+            # T_f = sum over the groups g entering f of (flow phase x term phase) Y_g, a current
+            # over the legs X does not cover (once per helicity state of those legs), then one
+            # product X . T_f per good helicity into flow f alone
+            # the Y_g are made first, then every T_f (one sum op per flow), then the products
+            x, kind = key
+            gis = flow_major[key]
+            handled.update(gis)
+            emit(x)
+            per_flow = {}
+            for gj in gis:
+                ((_, _, ((y, ph),)),) = gruns[gj]
+                emit(y)
+                for f, fph in groups[gj][2]:
+                    per_flow.setdefault(f, []).append((y, (ph + fph) % 4))
+            for f, items in per_flow.items():
+                if len(items) > 1:
+                    t = sum_node(items)
+                    emit(t)
+                    items = [(t, 0)]
+                amps.append(([(x, kind, items)], [(f, 0)]))
+                order.append(("A", len(amps) - 1))
+            continue
         for x, _, items in eff:
             emit(x)
             for y, _ in items:
                 emit(y)
-        order.append(("A", gi))
+        amps.append((eff, g[2]))
+        order.append(("A", len(amps) - 1))
 
     def uses(item):
         kind, x = item
         if kind == "C":
             return list(cur[x].children)
         out = []
-        for b, _, items in gruns[x]:
+        for b, _, items in amps[x][0]:
             out += [b] + [y for y, _ in items]
         return out
     last = {}
@@ -437,7 +497,7 @@ def _dfs_schedule(B):
             offset[x] = A.alloc(B.blocksize(x))
             ops.append(B.current_row(x, offset, terms))
         else:
-            ops.append(B.amp_row(gruns[x], groups[x][2], offset, flows, terms))
+            ops.append(B.amp_row(amps[x][0], amps[x][1], offset, flows, terms))
         for u in set(uses(item)):
             if last[u] == pos:
                 A.release(offset[u], B.blocksize(u))
