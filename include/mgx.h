@@ -269,9 +269,9 @@ int mgx_kernel_launches(const mgx_process* proc, int64_t nevt, int mode);
  * module-scope device array of mgx_noalloc_scratch_bytes() = 128 MiB, which every GPU that
  * loads the library holds until the process exits; the grid is sized so the workspace fits, i.e.
  * floor(128 MiB / (128 x per-event workspace)) blocks of 128 threads, at most the usual persistent
- * grid: g g > t t~ g g gets 16 blocks (2048 events in flight instead of 77824), g g > t t~ g g g
+ * grid: g g > t t~ g g gets 12 blocks (1536 events in flight instead of 77824), g g > t t~ g g g
  * a single block (128 events in flight), so their throughput through this entry point is
- * about 1/38 and 1/600 of mgx_compute's on a full batch; the small processes get the full grid.
+ * about 1/50 and 1/600 of mgx_compute's on a full batch; the small processes get the full grid.
  * The call itself allocates nothing (no cudaMalloc/cudaFree, no allocating library call); the
  * process handle must have been created beforehand.  Set-up: the first call on a device looks
  * up the array's device address with that device current, so make that first call before any
