@@ -204,7 +204,7 @@ def _workload_config(nevt, mode, workload=WORKLOAD, ws_bytes=None):
     cfg = {"workload": f"{wl.process}, {nevt} flat RAMBO events/GPU, sqrt(s)=1500 GeV, mt=173, alpha_s=0.118",
            "process": wl.process, "nevt_per_gpu": nevt, "mode": mode}
     if ws_bytes is None:
-        cfg["l2"] = "inputs larger than L2 (192 MiB momenta, 5.0 GB workspace)"
+        cfg["l2"] = "inputs larger than L2 (192 MiB momenta, 6.3 GB workspace)"
     else:
         cfg["l2"] = (f"workspace {ws_bytes / 2**30:.1f} GiB, "
                      + ("larger than L2" if ws_bytes > (129 << 20) else "smaller than L2 (a profiling case)"))
@@ -633,7 +633,7 @@ def run_gpu(args):
                             ("surrogate_unweighting", lambda: extra_surrogate(pkg, dev)),
                             ("phase_space", lambda: extra_phase_space(pkg, dev))):
                 # each workload starts from an empty allocator cache (the previous ones' workspaces,
-                # up to 60 GB for g g > t t~ g g g, would otherwise stay reserved)
+                # up to 81 GB for g g > t t~ g g g, would otherwise stay reserved)
                 gc.collect()
                 torch.cuda.empty_cache()
                 t0 = time.perf_counter()

@@ -69,3 +69,39 @@ def test_op_table_invariants(programs):
                 for t in _terms(P, op[11], op[12]):
                     assert t[1] == op[5], proc
         assert P.jamp_zero == (0 if len(seen_first) == P.ncol else 1)
+
+
+def _fp64_work(P, ngood):
+    """Float64 instructions per event of a program under the kernels' per-op counts (the model the
+    library's roofline uses; colour sum and weights left out, they do not depend on the closure)."""
+    c = P.flop_counts
+    per_var = (64 * (c["var_ffv_f"] + c["var_ffv_fb"]) + 72 * c["var_ffv_v"] + 56 * c["var_vvv"]
+               + 32 * c["var_vvvv"] + 56 * c["var_bil"] + 32 * c["var_rbil"])
+    amp = ngood * (16 * c["amp_runs"] + 8 * (c["amp_terms"] - c["amp_runs"]) + 2 * (c["amp_runs"] - c["amp"])
+                   + 2 * (c["amp_flows"] - P.ncol))
+    hdr = 8 * c["sum_adds"] + 8 * c["vvv_hdr"] + 18 * c["vvvv_hdr"] + 8 * c["slash_hdr"] + 16 * c["slash_pref_hdr"]
+    return per_var + amp + hdr
+
+
+@pytest.mark.parametrize("proc", BUILTIN)
+def test_flow_major_closure_only_where_it_saves_work(proc, programs, monkeypatch):
+    """The flow-major closure changes the amplitude stage only: every current op of the group-major
+    program is still there, and the modelled float64 work per event never grows.  For
+    g g > t t~ g g it closes exactly the four row bilinears whose 15 groups reach 6 flows each
+    (105 -> 69 products per helicity)."""
+    P = programs[proc]
+    monkeypatch.setattr(pg, "_flow_major_bilinears", lambda B, groups, gruns: {})
+    G = pg.build_program(proc)
+    key = lambda op: (op[0], op[5], op[6], op[7], op[8], op[9], op[10])
+    cur_ops = lambda Q: sorted(key(op) for op in Q.ops if op[0] not in (pg.OP_AMP, pg.OP_SUM))
+    assert cur_ops(P) == cur_ops(G)
+    ngood = 1 << P.npar
+    assert _fp64_work(P, ngood) <= _fp64_work(G, ngood)
+    if proc == "g g > t t~ g g":
+        assert (G.flop_counts["amp"], P.flop_counts["amp"]) == (105, 69)
+        assert (G.flop_counts["amp_flows"], P.flop_counts["amp_flows"]) == (336, 240)
+        single = [op for op in P.ops if op[0] == pg.OP_AMP and op[10] == 1 and op[12] == 1]
+        assert len(single) == 24                      # 4 bilinears x 6 flows
+        assert _fp64_work(P, ngood) < 0.9 * _fp64_work(G, ngood)
+    if proc in ("e+ e- > mu+ mu-", "g g > t t~"):
+        assert P.ops == G.ops and P.flows == G.flows and P.terms == G.terms
