@@ -228,10 +228,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRICS[args.workload], "value": value, "unit": "events/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(b for _, _, b in rates),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(_workload_config(args.nevt, args.mode, args.workload),
-                           sample=f"each step evaluates {n} events of this workload on the host cores"),
+            "config": _workload_config(args.nevt, args.mode, args.workload),
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per_core} events per core x {cores} spawn processes per step"},
+                             "sample": f"each step evaluates {n} events of this workload on the host cores "
+                                       f"({per_core} events per core x {cores} spawn processes)"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -604,10 +604,11 @@ def run_gpu(args):
                 "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed_fp32": "f64+f32", "mixed_tf32": "f64+tf32", "mixed_bf16x3": "f64+bf16",
                           "float": "f32"}[args.mode], "data": "synthetic",
+                # the reference arm prints the same config for the same arguments
                 "config": dict(_workload_config(nevt, args.mode, args.workload,
                                                 None if default_case else proc.workspace_bytes(nevt, mode)),
-                               **({} if args.kernel == "auto" else {"kernel": args.kernel}), ngood=proc.ngood, ndiagrams=proc.ndiagrams,
-                               ncol=proc.ncol),
+                               **({} if args.kernel == "auto" else {"kernel": args.kernel})),
+                "process": {"ngood": proc.ngood, "ndiagrams": proc.ndiagrams, "ncol": proc.ncol},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak,
                              "traffic": None if per_evt is None else per_evt * nevt,

@@ -42,3 +42,5 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"].startswith("g g > t t~ g g")
+    # the GPU arm's default line carries exactly this config, so the two arms compare like for like
+    assert line["config"] == bench._workload_config(bench.NEVT, "fp64", "ggttgg")
