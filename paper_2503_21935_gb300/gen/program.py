@@ -449,8 +449,8 @@ def _dfs_schedule(B):
             # flow-major closure of every single-run group on this bilinear X: per colour flow f,
             # T_f = sum over the groups g entering f of (flow phase x term phase) Y_g, a current
             # over the legs X does not cover (once per helicity state of those legs), then one
-            # product X . T_f per good helicity into flow f alone
-            # the Y_g are made first, then every T_f (one sum op per flow), then the products
+            # product X . T_f per good helicity into flow f alone.  The Y_g are made first, then
+            # every T_f (one sum op per flow), then the products.
             x, kind = key
             gis = flow_major[key]
             handled.update(gis)
