@@ -152,6 +152,18 @@ def test_berends_giele_equals_interpreter_jamps():
         assert np.abs(Jbg - J).max() / np.abs(J).max() < 1e-13, proc
 
 
+def test_berends_giele_equals_interpreter_jamps_five_gluons():
+    """g g > t t~ g g g, the 1240-diagram process of the large workload: every jamp of all 128
+    helicities from the diagram interpreter equals the colour-ordered recursion's (one event; the
+    recursion sums gluon currents over splittings and never forms a diagram)."""
+    me = get("g g > t t~ g g g")
+    p, a, _, _ = make_inputs(WORKLOADS["ggttggg"], 1)
+    J = me.jamps(p, a)
+    perms, Jbg = jamps_ggttng(p, a)
+    assert perms == me.perms and J.shape == (1, 128, 120)
+    assert np.abs(Jbg - J).max() / np.abs(J).max() < 1e-13
+
+
 def test_lorentz_invariance():
     # a boost changes the polarisation vectors by terms proportional to k, so the
     # helicity sum is frame independent only where the Ward identity holds: zero width
