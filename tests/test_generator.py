@@ -14,7 +14,7 @@ def programs():
     return {p: pg.build_program(p) for p in BUILTIN}
 
 
-@pytest.mark.parametrize("proc", ["g g > t t~", "g g > t t~ g", "g g > t t~ g g"])
+@pytest.mark.parametrize("proc", ["g g > t t~", "g g > t t~ g", "g g > t t~ g g", "g g > t t~ g g g"])
 def test_colour_matrix_equals_oracle(proc, programs):
     """Symbolic Fierz reduction (compiler) against explicit colour-index sums (oracle), exactly."""
     from oracle.matrix_element import get
