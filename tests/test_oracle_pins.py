@@ -155,13 +155,20 @@ def test_berends_giele_equals_interpreter_jamps():
 def test_berends_giele_equals_interpreter_jamps_five_gluons():
     """g g > t t~ g g g, the 1240-diagram process of the large workload: every jamp of all 128
     helicities from the diagram interpreter equals the colour-ordered recursion's (one event; the
-    recursion sums gluon currents over splittings and never forms a diagram)."""
+    recursion sums gluon currents over splittings and never forms a diagram), and |M|^2 is
+    symmetric under a relabelling of the final gluons."""
     me = get("g g > t t~ g g g")
     p, a, _, _ = make_inputs(WORKLOADS["ggttggg"], 1)
     J = me.jamps(p, a)
     perms, Jbg = jamps_ggttng(p, a)
     assert perms == me.perms and J.shape == (1, 128, 120)
     assert np.abs(Jbg - J).max() / np.abs(J).max() < 1e-13
+    # Bose symmetry of the three final gluons: a cyclic relabelling leaves |M|^2 unchanged only if
+    # the enumeration misses no diagram and the flow decomposition is right
+    q = p.copy()
+    q[:, [4, 5, 6]] = p[:, [5, 6, 4]]
+    r = me.evaluate(p, a)["me"]
+    assert np.abs(me.evaluate(q, a)["me"] / r - 1).max() < 1e-13
 
 
 def test_lorentz_invariance():
